@@ -1,0 +1,250 @@
+/*
+ * motif.h — C ABI of the GB300 Skip-Brute-Force planted (l,d) motif search library.
+ *
+ * The method (Perera & Ragel, "Accelerating Motif Finding in DNA Sequences with Multicore
+ * CPUs", Sec. III.A): enumerate every l-mer over {A,C,G,T}; compare it with every length-l
+ * window of each input sequence by Hamming distance; an l-mer matches a sequence when some
+ * window lies within distance d; an l-mer that fails to match a sequence is discarded at once
+ * and the remaining sequences are skipped.  The l-mers that match every sequence form the
+ * result set (Sec. I.A defines the planted (l,d) problem whose consensus is one member).
+ *
+ * Conventions shared by every entry point below:
+ *  - Every call returns an int status (motif_status); nothing throws across the ABI.
+ *  - Sequences are n rows of t characters from "ACGTacgt" (Sec. I.A: n sequences of length t).
+ *    A window is a substring of length l; each sequence has W = t - l + 1 windows (Sec. III.A;
+ *    the paper writes (n - l) + 1 with n standing for the sequence length there).
+ *  - A candidate l-mer c = c_0 c_1 ... c_{l-1} is identified by its 2l-bit code:
+ *    A=0, C=1, G=2, T=3, base c_i stored in bits [2(l-1-i), 2(l-1-i)+1].  The candidate index
+ *    space [0, 4^l) is exactly the code space (Sec. IV.A: l-mers are generated from their
+ *    index, never stored), so ascending codes are lexicographic order of the strings.
+ *  - Results are always ascending, duplicate-free codes.
+ *  - Argument rules: n >= 1, t >= 1, 1 <= l <= 31 (4^l fits in 64 bits), d >= 0.
+ *    d >= l accepts every candidate; t < l yields an empty result (no windows).
+ *  - The library owns each plan and every device buffer it allocates; the caller owns every
+ *    buffer it passes in.  A plan is not thread-safe; motif_submit and motif_poll are.
+ *  - Device work of a plan runs on its stream (motif_opts.stream, a cudaStream_t; NULL = the
+ *    legacy default stream).  Pointer arguments named d_* are device pointers, all others host.
+ */
+#ifndef MOTIF_H_
+#define MOTIF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MOTIF_OK = 0,
+  MOTIF_PENDING = 1,         /* motif_poll: the job has not finished yet */
+  MOTIF_ERR_ARG = -1,        /* an argument breaks the rules above */
+  MOTIF_ERR_ALPHABET = -2,   /* a sequence character outside ACGTacgt */
+  MOTIF_ERR_CAPACITY = -3,   /* more results than the output capacity; *out_count = required */
+  MOTIF_ERR_OOM = -4,        /* a device or host allocation failed */
+  MOTIF_ERR_CUDA = -5,       /* a CUDA runtime call failed (or no CUDA device is present) */
+  MOTIF_ERR_TIMEOUT = -6,    /* a bounded wait ran out (host poll or a device-side wait) */
+  MOTIF_ERR_BUSY = -7,       /* the serving queue refused the job (queue full) */
+  MOTIF_ERR_STATE = -8,      /* wrong call order, e.g. a search before sequences were loaded */
+  MOTIF_ERR_NOTFOUND = -9    /* unknown job id */
+} motif_status;
+
+/* Search kernel selection. */
+typedef enum {
+  MOTIF_KERNEL_AUTO = 0,  /* the plan's tuned choice */
+  MOTIF_KERNEL_CAND = 1,  /* one candidate per lane: XOR, pair-fold, POPC, running min */
+  MOTIF_KERNEL_GROUP = 2  /* one (l-k)-base prefix per lane, its 4^k suffixes as a bit mask */
+} motif_kernel;
+
+typedef struct motif_plan_s* motif_plan;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a device
+ * pointer of at least `bytes` bytes, usable on `stream`, or NULL on failure. */
+typedef void* (*motif_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*motif_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+  void* stream;             /* cudaStream_t for all device work of the plan; NULL = default */
+  int32_t kernel;           /* motif_kernel */
+  int32_t block;            /* threads per CTA; 0 = tuned */
+  int32_t ctas_per_sm;      /* resident CTAs per SM of the persistent grid; 0 = tuned */
+  int32_t cands_per_thread; /* CAND kernel: candidates a lane carries per fresh tile; 0 = tuned */
+  int32_t compact_levels;   /* CAND kernel: sequences with a survivor queue; 0 = tuned */
+  int32_t suffix_bases;     /* GROUP kernel: k, suffix bases enumerated in one lane; 0 = tuned */
+  int32_t timeout_ms;       /* bound on every device-side and host-side wait; 0 = 60000 */
+  motif_alloc_fn alloc;     /* NULL = cudaMallocAsync / cudaFreeAsync on the plan's stream */
+  motif_free_fn free;
+  void* alloc_ctx;
+  uint64_t range_lo;        /* candidate sub-range [range_lo, range_hi) of [0, 4^l), the */
+  uint64_t range_hi;        /* per-worker index range of Sec. IV.A; range_hi == 0: all */
+} motif_opts;
+
+typedef struct {
+  uint64_t candidates;           /* candidates in the searched range */
+  uint64_t survivors;            /* codes accepted by the last search */
+  uint64_t algorithmic_compares; /* canonical window-compare count (motif_count_compares) */
+  double search_ms;              /* device time of the search kernel, last search */
+  double sort_ms;                /* device time of sort/dedup, last search */
+  double total_ms;               /* host wall time of the last motif_search or served job */
+  double queue_ms;               /* served job: submit -> admission */
+  int64_t device_bytes;          /* device memory held by the plan */
+  int32_t smem_bytes;            /* dynamic shared memory per CTA of the search kernel */
+  int32_t kernel;                /* kernel that ran (motif_kernel) */
+  int32_t grid;                  /* CTAs launched */
+  int32_t block;                 /* threads per CTA */
+} motif_stats_t;
+
+/* ---- plans ------------------------------------------------------------------------------ */
+
+/* Fills *o with defaults: every field zero / NULL (tuned or library defaults). */
+void motif_opts_default(motif_opts* o);
+
+/* Creates a plan for an (l,d) search over n sequences of length t (Sec. I.A; the inputs of
+ * Sec. IV.A: the sequences, the pattern length l and the allowed mutations d).  Validates the
+ * argument rules, reserves the device buffers and fixes the kernel configuration.  opts may be
+ * NULL.  *out receives the plan, released by motif_plan_destroy.
+ * Errors: MOTIF_ERR_ARG, MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
+int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_opts* opts,
+                      motif_plan* out);
+
+/* Releases the plan and its device memory (after its stream has drained).  NULL is a no-op. */
+void motif_plan_destroy(motif_plan p);
+
+/* ---- input: window extraction (Sec. IV.A "all the windows are first extracted") -------- */
+
+/* Copies n rows of t characters (row r at seqs + r*stride, stride >= t) to the device and
+ * packs every window into a 2l-bit word (32-bit for l <= 16, 64-bit above).  Blocking; the
+ * characters are validated and a character outside ACGTacgt returns MOTIF_ERR_ALPHABET
+ * (the plan then holds no sequences).  Errors: MOTIF_ERR_ARG, MOTIF_ERR_ALPHABET,
+ * MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
+int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride);
+
+/* Same as motif_load_seqs for characters already in device memory (d_seqs, row stride
+ * `stride` bytes).  Asynchronous on the plan's stream; an invalid character is recorded on
+ * the device and reported as MOTIF_ERR_ALPHABET by the next motif_search (for
+ * motif_search_device, through *d_out_count = -1). */
+int motif_load_seqs_device(motif_plan p, const char* d_seqs, int64_t stride);
+
+/* ---- search (Sec. III.A skip-BF; Sec. IV.A range split) -------------------------------- */
+
+/* Blocking search over the plan's candidate range.  Writes the accepted codes, ascending and
+ * duplicate-free, to out_codes[0 .. *out_count).  If more than `capacity` codes are accepted
+ * it returns MOTIF_ERR_CAPACITY with *out_count = the required capacity and promises nothing
+ * about out_codes; call again with a larger buffer.  out_codes may be NULL when capacity == 0.
+ * Errors: MOTIF_ERR_ARG, MOTIF_ERR_STATE (no sequences), MOTIF_ERR_ALPHABET,
+ * MOTIF_ERR_CAPACITY, MOTIF_ERR_OOM, MOTIF_ERR_CUDA, MOTIF_ERR_TIMEOUT. */
+int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* out_count);
+
+/* Asynchronous search on the plan's stream with device-resident output: the search kernel
+ * appends accepted codes into d_out_codes (capacity entries), the sort/dedup kernels order
+ * them in place, and *d_out_count (one int64 in device memory) receives the number of
+ * accepted codes.  If that number exceeds capacity, only the count is meaningful (retry with
+ * more room); -1 means an invalid character was loaded.  No host synchronisation. */
+int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
+                        int64_t* d_out_count);
+
+/* Runs the counting form of the search over the plan's range and returns in *out the
+ * canonical algorithmic window-compare count: per candidate, sequences in input order, each
+ * scanned left to right up to and including its first window within distance d, all W
+ * windows of the first sequence with none, and no sequence after it.  Blocking. */
+int motif_count_compares(motif_plan p, uint64_t* out);
+
+/* Statistics of the last search / served job of the plan. */
+int motif_stats(motif_plan p, motif_stats_t* s);
+
+/* ---- batching: many uneven jobs in one persistent launch -------------------------------- */
+
+/* Runs `njobs` loaded plans together in one persistent launch of the batched kernel, which
+ * pulls candidate tiles of every job from one device tile queue; use_graph != 0 captures the
+ * launch sequence in a CUDA graph and replays it.  Per job j the results follow motif_search's
+ * rules on out_codes[j] / capacities[j] / out_counts[j]; statuses[j] receives job j's status.
+ * Returns MOTIF_OK when every job succeeded, else the first failing status.  Blocking; the
+ * work runs on the first plan's stream. */
+int motif_batch_search(int32_t njobs, const motif_plan* plans, uint64_t* const* out_codes,
+                       const int64_t* capacities, int64_t* out_counts, int32_t* statuses,
+                       int32_t use_graph);
+
+/* Autotuner: times each candidate configuration (kernel, block, CTAs per SM, candidates per
+ * lane, queue levels, suffix bases) on a sub-range of the plan's candidates, keeps the
+ * fastest in the plan and in the process-wide cache keyed by (word width, l, d, n, W, SMs),
+ * and copies it into *best when best != NULL.  budget_ms bounds the tuning time. */
+int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best);
+
+/* Saves / loads the process-wide tuning cache as JSON. */
+int motif_tune_cache_save(const char* path);
+int motif_tune_cache_load(const char* path);
+
+/* ---- serving: continuous batching -------------------------------------------------------- */
+
+typedef struct {
+  int32_t max_active;      /* jobs resident on the device at once; 0 = 64 */
+  int32_t max_queued;      /* jobs waiting for admission before submit returns BUSY; 0 = 4096 */
+  int64_t device_budget;   /* bytes of device memory the admitted jobs may hold; 0 = 4 GiB */
+  int32_t step_tiles;      /* candidate tiles per device step between admissions; 0 = tuned */
+  int32_t use_graph;       /* != 0: replay the step launch from a CUDA graph */
+  int32_t timeout_ms;      /* bound on each device step; 0 = 60000 */
+} motif_server_opts;
+
+/* Starts the process-wide serving loop (a scheduler thread with its own stream).  opts may be
+ * NULL.  MOTIF_ERR_STATE if it is already running. */
+int motif_server_start(const motif_server_opts* opts);
+
+/* Stops the serving loop after the jobs in flight finish; pending unfinished jobs fail with
+ * MOTIF_ERR_STATE at their next poll. */
+int motif_server_stop(void);
+
+/* Submits the loaded plan as a job (starting the loop with defaults if needed).  The plan's
+ * packed windows are copied, so the plan may be reused or destroyed after this returns.
+ * *job_id receives the job id.  Errors: MOTIF_ERR_STATE (no sequences), MOTIF_ERR_BUSY. */
+int motif_submit(motif_plan p, int64_t* job_id);
+
+/* Waits up to timeout_ms (0 = do not wait) for the job.  Returns MOTIF_PENDING while it runs;
+ * on completion writes the codes by motif_search's rules and releases the job (on
+ * MOTIF_ERR_CAPACITY the job stays so that it can be polled again).  stats may be NULL. */
+int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity, int64_t* out_count,
+               int32_t timeout_ms, motif_stats_t* stats);
+
+/* ---- sharding over several workers (Sec. IV.A: per-worker first/last l-mer index) -------- */
+
+/* Splits the candidate space [0, total) into `world` contiguous ranges with sizes in
+ * proportion to weights[0..world) (NULL = equal) and returns rank's [*lo, *hi).  Concatenating
+ * the per-rank ascending results in rank order gives the global ascending result. */
+int motif_shard_range(uint64_t total, int32_t rank, int32_t world, const double* weights,
+                      uint64_t* lo, uint64_t* hi);
+
+/* ---- helpers ------------------------------------------------------------------------------ */
+
+const char* motif_strerror(int status);
+
+/* Encodes the first l characters of s (ACGTacgt) into a 2l-bit code (layout above). */
+int motif_encode(const char* s, int32_t l, uint64_t* code);
+
+/* Decodes a 2l-bit code into l characters (no terminator written). */
+int motif_decode(uint64_t code, int32_t l, char* out);
+
+/* K4 issue-rate probes: operations per SM per clock of one instruction class, measured with
+ * one 1024-thread CTA per SM on the current device. */
+typedef enum {
+  MOTIF_PROBE_POPC = 0,
+  MOTIF_PROBE_LOP3 = 1,
+  MOTIF_PROBE_IMNMX = 2,
+  MOTIF_PROBE_SHF = 3,
+  MOTIF_PROBE_IADD = 4,
+  MOTIF_PROBE_IMAD = 5,
+  MOTIF_PROBE_POPC_LOP3 = 6,   /* 1 POPC + 3 LOP3 on independent chains; rate in POPC+LOP3 ops */
+  MOTIF_PROBE_CMP_SPLIT = 7,   /* split-plane window compares */
+  MOTIF_PROBE_CMP_FOLD = 8,    /* folded window compares */
+  MOTIF_PROBE_LDS64_DIV = 9,   /* 64-bit shared loads at distinct conflict-free addresses */
+  MOTIF_PROBE_COUNT = 10
+} motif_probe_kind;
+
+int motif_probe_rate(int32_t kind, int32_t iters, double* ops_per_sm_clk, double* sm_cycles);
+
+/* Library version string. */
+const char* motif_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOTIF_H_ */

@@ -1,0 +1,570 @@
+// C ABI: plans, window loading (K0), the search (K1 steps + K2 sort/dedup), the compare
+// counter, statistics and small helpers.  Everything device-side runs on the plan's stream.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "plan.h"
+
+using motif::JobDesc;
+using motif::JobState;
+using motif::StepCtl;
+
+namespace motif {
+
+int status_from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return MOTIF_OK;
+  if (e == cudaErrorMemoryAllocation) return MOTIF_ERR_OOM;
+  return MOTIF_ERR_CUDA;
+}
+
+void* plan_alloc(motif_plan_s* p, size_t bytes) {
+  if (bytes == 0) return nullptr;
+  void* ptr = nullptr;
+  if (p->opts.alloc) {
+    ptr = p->opts.alloc(bytes, p->stream, p->opts.alloc_ctx);
+  } else if (cudaMallocAsync(&ptr, bytes, p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) p->device_bytes += (int64_t)bytes;
+  return ptr;
+}
+
+void plan_free(motif_plan_s* p, void* ptr, size_t bytes) {
+  if (!ptr) return;
+  if (p->opts.free) p->opts.free(ptr, p->stream, p->opts.alloc_ctx);
+  else cudaFreeAsync(ptr, p->stream);
+  p->device_bytes -= (int64_t)bytes;
+}
+
+namespace {
+std::mutex g_ball_mu;
+uint64_t* g_ball[64][kMaxKs + 1] = {};
+std::mutex g_attr_mu;
+size_t g_attr_smem[3][kMaxKs + 1] = {};
+}  // namespace
+
+const uint64_t* ball_table(int device, int ks, cudaStream_t s) {
+  if (device < 0 || device >= 64 || ks < 1 || ks > kMaxKs) return nullptr;
+  std::lock_guard<std::mutex> g(g_ball_mu);
+  if (!g_ball[device][ks]) {
+    uint64_t* t = nullptr;
+    if (cudaMalloc(&t, (size_t)ball_table_words(ks) * 8) != cudaSuccess) return nullptr;
+    if (launch_ball_table(t, ks, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaFree(t);
+      return nullptr;
+    }
+    g_ball[device][ks] = t;
+  }
+  return g_ball[device][ks];
+}
+
+void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_cap) {
+  memset(jd, 0, sizeof(*jd));
+  jd->n = p->n; jd->t = p->t; jd->l = p->l; jd->d = p->d;
+  jd->W = p->W; jd->wstride = p->wstride;
+  jd->planes = p->d_planes; jd->codes = p->d_codes;
+  jd->kind = p->kind;
+  jd->ks = p->kind == MOTIF_KERNEL_GROUP ? p->p : 0;
+  jd->cpt = p->kind == MOTIF_KERNEL_CAND ? p->p : 1;
+  jd->span0 = p->span0;
+  jd->lo = p->lo; jd->hi = p->hi;
+  jd->unit_lo = p->unit_lo; jd->unit_hi = p->unit_hi;
+  jd->chunk_units = p->chunk_units; jd->nchunks = p->nchunks;
+  jd->rest_threshold = p->rest_threshold;
+  jd->qidx[0] = p->d_qidx[0]; jd->qidx[1] = p->d_qidx[1];
+  jd->qmask[0] = p->d_qmask[0]; jd->qmask[1] = p->d_qmask[1];
+  jd->qcap = p->qcap;
+  jd->out = out; jd->out_cap = out_cap;
+  jd->ball = p->kind == MOTIF_KERNEL_GROUP ? ball_table(p->device, p->p, p->stream) : nullptr;
+}
+
+static void free_queues(motif_plan_s* p) {
+  for (int i = 0; i < 2; ++i) {
+    plan_free(p, p->d_qidx[i], p->qcap * 4);
+    plan_free(p, p->d_qmask[i], p->qcap * 8 * (size_t)p->qmask_words);
+    p->d_qidx[i] = nullptr;
+    p->d_qmask[i] = nullptr;
+  }
+  p->qcap = 0;
+  p->qmask_words = 0;
+}
+
+int plan_configure(motif_plan_s* p) {
+  const motif_opts& o = p->opts;
+  // Kernel variant.
+  int kind = o.kernel == MOTIF_KERNEL_CAND ? MOTIF_KERNEL_CAND : MOTIF_KERNEL_GROUP;
+  int pv;
+  if (kind == MOTIF_KERNEL_CAND) {
+    pv = o.cands_per_thread > 0 ? o.cands_per_thread : 2;
+    if (pv != 1 && pv != 2 && pv != 4) return MOTIF_ERR_ARG;
+  } else {
+    pv = o.suffix_bases > 0 ? o.suffix_bases : 4;
+    if (pv > kMaxKs) return MOTIF_ERR_ARG;
+    if (pv > p->l) pv = p->l;
+  }
+  const int span0 = o.compact_levels > 0 ? std::min(o.compact_levels, 2)
+                                         : (kind == MOTIF_KERNEL_GROUP && pv >= 3 ? 2 : 1);
+  const int block = o.block > 0 ? o.block : 256;
+  if (block % 32 != 0 || block > 256) return MOTIF_ERR_ARG;
+  const size_t smem = step_smem_bytes(kind, pv, std::max(p->wstride, kWinAlign));
+  {
+    std::lock_guard<std::mutex> g(g_attr_mu);
+    size_t& cur = g_attr_smem[kind][pv];
+    if (smem > cur) {
+      cudaError_t e = step_kernel_attrs(kind, pv, smem);
+      if (e != cudaSuccess) return status_from_cuda(e);
+      cur = smem;
+    }
+  }
+  int per_sm = step_max_ctas_per_sm(kind, pv, block, smem);
+  if (per_sm <= 0) return MOTIF_ERR_ARG;
+  if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
+  // Units and chunking.
+  const int shift = kind == MOTIF_KERNEL_GROUP ? 2 * pv : 0;
+  const uint64_t unit_lo = p->lo >> shift;
+  const uint64_t unit_hi = p->hi > p->lo ? ((p->hi - 1) >> shift) + 1 : unit_lo;
+  const uint64_t units = unit_hi - unit_lo;
+  const uint64_t max_chunk = kind == MOTIF_KERNEL_GROUP ? (1ull << 22) : (1ull << 28);
+  const uint64_t chunk = std::max<uint64_t>(1, std::min(units, max_chunk));
+  const int words = kind == MOTIF_KERNEL_GROUP ? mask_words(pv) : 0;
+  if (chunk != p->qcap || words != p->qmask_words) {
+    free_queues(p);
+    for (int i = 0; i < 2; ++i) {
+      p->d_qidx[i] = (uint32_t*)plan_alloc(p, chunk * 4);
+      if (!p->d_qidx[i]) return MOTIF_ERR_OOM;
+      if (words) {
+        p->d_qmask[i] = (uint64_t*)plan_alloc(p, chunk * 8 * (size_t)words);
+        if (!p->d_qmask[i]) return MOTIF_ERR_OOM;
+      }
+    }
+    p->qcap = chunk;
+    p->qmask_words = words;
+  }
+  p->kind = kind;
+  p->p = pv;
+  p->span0 = span0;
+  p->block = block;
+  p->grid = per_sm * p->sms;
+  p->smem = smem;
+  p->unit_lo = unit_lo;
+  p->unit_hi = unit_hi;
+  p->chunk_units = chunk;
+  p->nchunks = units == 0 ? 0 : (units + chunk - 1) / chunk;
+  p->rest_threshold = (uint64_t)8 * 32 * p->sms;
+  if (kind == MOTIF_KERNEL_GROUP && !ball_table(p->device, pv, p->stream)) return MOTIF_ERR_CUDA;
+  return MOTIF_OK;
+}
+
+int run_steps(int kind, int pv, const JobDesc* d_jobs, JobState* d_states, int njobs,
+              StepCtl* d_ctl, int grid, int block, size_t smem, int max_steps, bool poll,
+              int timeout_ms, cudaStream_t s, int* steps_run) {
+  const double t0 = now_ms();
+  int launched = 0;
+  const int group = 8;
+  while (launched < max_steps) {
+    const int todo = poll ? std::min(group, max_steps - launched) : max_steps - launched;
+    for (int i = 0; i < todo; ++i) {
+      cudaError_t e = launch_step(kind, pv, d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+      if (e != cudaSuccess) return status_from_cuda(e);
+    }
+    launched += todo;
+    if (!poll) break;
+    unsigned active = 0;
+    cudaError_t e = cudaMemcpyAsync(&active, &d_ctl->active_jobs, sizeof(unsigned),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (active == 0) break;
+    if (timeout_ms > 0 && now_ms() - t0 > timeout_ms) {
+      if (steps_run) *steps_run = launched;
+      return MOTIF_ERR_TIMEOUT;
+    }
+  }
+  if (steps_run) *steps_run = launched;
+  return MOTIF_OK;
+}
+
+}  // namespace motif
+
+using namespace motif;
+
+namespace motif_api {
+
+constexpr const char* kVersion = "motif-gb300 0.1 (sm_103a)";
+
+int validate_args(int32_t n, int32_t t, int32_t l, int32_t d) {
+  if (n < 1 || t < 1 || l < 1 || l > kMaxL || d < 0) return MOTIF_ERR_ARG;
+  return MOTIF_OK;
+}
+
+int timeout_of(const motif_plan_s* p) { return p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 60000; }
+
+// Upper bound on steps for one job: every chunk needs at most n passes.
+int max_steps_of(const motif_plan_s* p) {
+  const uint64_t s = p->nchunks * (uint64_t)p->n + 2;
+  return s > (uint64_t)(1 << 30) ? (1 << 30) : (int)s;
+}
+
+int ensure_out(motif_plan_s* p, int64_t need) {
+  if (need <= p->out_cap) return MOTIF_OK;
+  plan_free(p, p->d_out, (size_t)p->out_cap * 8);
+  p->d_out = (uint64_t*)plan_alloc(p, (size_t)need * 8);
+  p->out_cap = p->d_out ? need : 0;
+  return p->d_out ? MOTIF_OK : MOTIF_ERR_OOM;
+}
+
+int ensure_sort(motif_plan_s* p, int64_t cap) {
+  const size_t need = sort_scratch_bytes(cap, p->sms);
+  if (need <= p->sort_bytes) return MOTIF_OK;
+  plan_free(p, p->d_sort, p->sort_bytes);
+  p->d_sort = plan_alloc(p, need);
+  p->sort_bytes = p->d_sort ? need : 0;
+  return p->d_sort ? MOTIF_OK : MOTIF_ERR_OOM;
+}
+
+int check_alphabet(motif_plan_s* p) {
+  if (!p->check_alpha) return MOTIF_OK;
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  p->check_alpha = false;
+  if (err) {
+    p->loaded = false;
+    return MOTIF_ERR_ALPHABET;
+  }
+  return MOTIF_OK;
+}
+
+// Enqueues one search of the plan writing into (out, cap): descriptor, state reset, steps.
+int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll, int* steps) {
+  JobDesc jd;
+  fill_desc(p, &jd, out, cap);
+  if (p->kind == MOTIF_KERNEL_GROUP && !jd.ball) return MOTIF_ERR_CUDA;
+  cudaError_t e = cudaMemcpyAsync(p->d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ctl, 0, sizeof(StepCtl), p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  if (p->nchunks == 0) {
+    if (steps) *steps = 0;
+    return MOTIF_OK;
+  }
+  return run_steps(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
+                   max_steps_of(p), poll, timeout_of(p), p->stream, steps);
+}
+
+__global__ void finalize_count_kernel(const int* err, const unsigned long long* count,
+                                      int64_t* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = *err ? -1 : (int64_t)*count;
+}
+
+}  // namespace motif_api
+
+using namespace motif_api;
+
+extern "C" {
+
+const char* motif_version(void) { return kVersion; }
+
+const char* motif_strerror(int status) {
+  switch (status) {
+    case MOTIF_OK: return "ok";
+    case MOTIF_PENDING: return "pending";
+    case MOTIF_ERR_ARG: return "invalid argument";
+    case MOTIF_ERR_ALPHABET: return "character outside ACGTacgt";
+    case MOTIF_ERR_CAPACITY: return "output capacity too small";
+    case MOTIF_ERR_OOM: return "out of memory";
+    case MOTIF_ERR_CUDA: return "CUDA error";
+    case MOTIF_ERR_TIMEOUT: return "timed out";
+    case MOTIF_ERR_BUSY: return "queue full";
+    case MOTIF_ERR_STATE: return "invalid state for this call";
+    case MOTIF_ERR_NOTFOUND: return "unknown job";
+    default: return "unknown status";
+  }
+}
+
+void motif_opts_default(motif_opts* o) {
+  if (o) memset(o, 0, sizeof(*o));
+}
+
+int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_opts* opts,
+                      motif_plan* out) {
+  if (!out) return MOTIF_ERR_ARG;
+  *out = nullptr;
+  int rc = validate_args(n, t, l, d);
+  if (rc) return rc;
+  motif_plan_s* p = new (std::nothrow) motif_plan_s();
+  if (!p) return MOTIF_ERR_OOM;
+  if (opts) p->opts = *opts;
+  p->n = n; p->t = t; p->l = l; p->d = d;
+  p->W = t - l + 1;
+  p->wstride = p->W > 0 ? (p->W + kWinAlign - 1) / kWinAlign * kWinAlign : 0;
+  const uint64_t space = 1ull << (2 * l);
+  p->lo = p->opts.range_lo;
+  p->hi = p->opts.range_hi ? p->opts.range_hi : space;
+  if (p->hi > space || p->lo > p->hi) { delete p; return MOTIF_ERR_ARG; }
+  p->stream = (cudaStream_t)p->opts.stream;
+  cudaError_t e = cudaGetDevice(&p->device);
+  cudaDeviceProp prop;
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, p->device);
+  if (e != cudaSuccess) { cudaGetLastError(); delete p; return MOTIF_ERR_CUDA; }
+  p->sms = prop.multiProcessorCount;
+  for (auto& ev : p->ev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) { motif_plan_destroy(p); return MOTIF_ERR_CUDA; }
+  }
+  const size_t chars = (size_t)n * t;
+  const size_t wins = (size_t)n * std::max(p->wstride, 0);
+  p->d_chars = (char*)plan_alloc(p, chars);
+  p->chars_bytes = chars;
+  p->d_planes = wins ? (uint2*)plan_alloc(p, wins * 8) : nullptr;
+  p->d_codes = wins ? (uint64_t*)plan_alloc(p, wins * 8) : nullptr;
+  p->d_err = (int*)plan_alloc(p, sizeof(int));
+  p->d_job = (JobDesc*)plan_alloc(p, sizeof(JobDesc));
+  p->d_state = (JobState*)plan_alloc(p, sizeof(JobState));
+  p->d_ctl = (StepCtl*)plan_alloc(p, sizeof(StepCtl));
+  p->d_total = (unsigned long long*)plan_alloc(p, sizeof(unsigned long long));
+  if (!p->d_chars || (wins && (!p->d_planes || !p->d_codes)) || !p->d_err || !p->d_job ||
+      !p->d_state || !p->d_ctl || !p->d_total) {
+    motif_plan_destroy(p);
+    return MOTIF_ERR_OOM;
+  }
+  if (p->opts.kernel == MOTIF_KERNEL_AUTO) tune_lookup(p, &p->opts);
+  rc = plan_configure(p);
+  if (rc == MOTIF_OK) rc = ensure_out(p, 1 << 16);
+  if (rc) { motif_plan_destroy(p); return rc; }
+  *out = p;
+  return MOTIF_OK;
+}
+
+void motif_plan_destroy(motif_plan p) {
+  if (!p) return;
+  DeviceGuard g(p->device);
+  cudaStreamSynchronize(p->stream);
+  free_queues(p);
+  plan_free(p, p->d_chars, p->chars_bytes);
+  const size_t wins = (size_t)p->n * std::max(p->wstride, 0);
+  plan_free(p, p->d_planes, wins * 8);
+  plan_free(p, p->d_codes, wins * 8);
+  plan_free(p, p->d_err, sizeof(int));
+  plan_free(p, p->d_job, sizeof(JobDesc));
+  plan_free(p, p->d_state, sizeof(JobState));
+  plan_free(p, p->d_ctl, sizeof(StepCtl));
+  plan_free(p, p->d_total, sizeof(unsigned long long));
+  plan_free(p, p->d_out, (size_t)p->out_cap * 8);
+  plan_free(p, p->d_sort, p->sort_bytes);
+  cudaStreamSynchronize(p->stream);
+  for (auto& ev : p->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete p;
+}
+
+static int load_common(motif_plan p, bool sync_check) {
+  cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  e = launch_pack(p->d_chars, p->t, p->n, p->t, p->l, p->wstride, p->d_planes, p->d_codes,
+                  p->d_err, p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  p->loaded = true;
+  p->check_alpha = true;
+  return sync_check ? check_alphabet(p) : MOTIF_OK;
+}
+
+int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride) {
+  if (!p || !seqs || stride < p->t) return MOTIF_ERR_ARG;
+  DeviceGuard g(p->device);
+  p->loaded = false;
+  cudaError_t e = cudaMemcpy2DAsync(p->d_chars, p->t, seqs, (size_t)stride, p->t, p->n,
+                                    cudaMemcpyHostToDevice, p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return load_common(p, true);
+}
+
+int motif_load_seqs_device(motif_plan p, const char* d_seqs, int64_t stride) {
+  if (!p || !d_seqs || stride < p->t) return MOTIF_ERR_ARG;
+  DeviceGuard g(p->device);
+  p->loaded = false;
+  cudaError_t e = cudaMemcpy2DAsync(p->d_chars, p->t, d_seqs, (size_t)stride, p->t, p->n,
+                                    cudaMemcpyDeviceToDevice, p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return load_common(p, false);
+}
+
+int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* out_count) {
+  if (!p || !out_count || capacity < 0 || (capacity > 0 && !out_codes)) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  const double t0 = now_ms();
+  int rc = check_alphabet(p);
+  if (rc) return rc;
+  p->stats.candidates = p->hi - p->lo;
+  p->stats.kernel = p->kind;
+  p->stats.grid = p->grid;
+  p->stats.block = p->block;
+  p->stats.smem_bytes = (int32_t)p->smem;
+  *out_count = 0;
+  if (p->W <= 0 || p->hi <= p->lo) {  // no windows or an empty range: nothing survives
+    p->stats.survivors = 0;
+    p->stats.search_ms = p->stats.sort_ms = 0;
+    p->stats.total_ms = now_ms() - t0;
+    return MOTIF_OK;
+  }
+  unsigned long long found = 0;
+  for (;;) {
+    cudaEventRecord(p->ev[0], p->stream);
+    int steps = 0;
+    rc = enqueue_search(p, p->d_out, (uint64_t)p->out_cap, true, &steps);
+    if (rc) return rc;
+    cudaEventRecord(p->ev[1], p->stream);
+    cudaError_t e = cudaMemcpyAsync(&found, &p->d_state->out_count, sizeof(found),
+                                    cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (found <= (unsigned long long)p->out_cap) break;
+    rc = ensure_out(p, (int64_t)std::max<unsigned long long>(found, 2 * (unsigned long long)p->out_cap));
+    if (rc) return rc;
+  }
+  if (found > 4096) {
+    rc = ensure_sort(p, p->out_cap);
+    if (rc) return rc;
+  }
+  cudaEventRecord(p->ev[2], p->stream);
+  cudaError_t e = launch_sort_unique(p->d_out, &p->d_state->out_count, p->out_cap, 2 * p->l,
+                                     p->d_sort, p->sms, (long long)found, p->stream);
+  cudaEventRecord(p->ev[3], p->stream);
+  unsigned long long final_count = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&final_count, &p->d_state->out_count, sizeof(final_count),
+                        cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  *out_count = (int64_t)final_count;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]);
+  p->stats.search_ms = ms;
+  cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]);
+  p->stats.sort_ms = ms;
+  p->stats.survivors = final_count;
+  if ((int64_t)final_count > capacity) {
+    p->stats.total_ms = now_ms() - t0;
+    return MOTIF_ERR_CAPACITY;
+  }
+  if (final_count) {
+    e = cudaMemcpyAsync(out_codes, p->d_out, final_count * 8, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  p->stats.total_ms = now_ms() - t0;
+  return MOTIF_OK;
+}
+
+int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
+                        int64_t* d_out_count) {
+  if (!p || !d_out_count || capacity < 0 || (capacity > 0 && !d_out_codes)) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  int rc = MOTIF_OK;
+  if (capacity > 4096) {
+    rc = ensure_sort(p, capacity);
+    if (rc) return rc;
+  }
+  if (p->W <= 0 || p->hi <= p->lo) {
+    cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  } else {
+    rc = enqueue_search(p, d_out_codes, (uint64_t)capacity, false, nullptr);
+    if (rc) return rc;
+    cudaError_t e = launch_sort_unique(d_out_codes, &p->d_state->out_count, capacity, 2 * p->l,
+                                       p->d_sort, p->sms, -1, p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  finalize_count_kernel<<<1, 32, 0, p->stream>>>(p->d_err, &p->d_state->out_count, d_out_count);
+  return status_from_cuda(cudaGetLastError());
+}
+
+int motif_count_compares(motif_plan p, uint64_t* out) {
+  if (!p || !out) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  int rc = check_alphabet(p);
+  if (rc) return rc;
+  *out = 0;
+  if (p->W <= 0 || p->hi <= p->lo) return MOTIF_OK;
+  JobDesc jd;
+  fill_desc(p, &jd, p->d_out, p->out_cap);
+  unsigned long long total = 0;
+  cudaError_t e = cudaMemcpyAsync(p->d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_total, 0, sizeof(unsigned long long), p->stream);
+  if (e == cudaSuccess) e = launch_count(p->d_job, p->d_total, p->sms * 8, 256, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, p->d_total, sizeof(total), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  *out = total;
+  p->stats.algorithmic_compares = total;
+  return MOTIF_OK;
+}
+
+int motif_stats(motif_plan p, motif_stats_t* s) {
+  if (!p || !s) return MOTIF_ERR_ARG;
+  *s = p->stats;
+  s->device_bytes = p->device_bytes;
+  return MOTIF_OK;
+}
+
+int motif_shard_range(uint64_t total, int32_t rank, int32_t world, const double* weights,
+                      uint64_t* lo, uint64_t* hi) {
+  if (world < 1 || rank < 0 || rank >= world || !lo || !hi) return MOTIF_ERR_ARG;
+  double sum = 0;
+  for (int r = 0; r < world; ++r) {
+    const double w = weights ? weights[r] : 1.0;
+    if (!(w >= 0)) return MOTIF_ERR_ARG;
+    sum += w;
+  }
+  if (!(sum > 0)) return MOTIF_ERR_ARG;
+  // Boundaries at floor(total * cumulative_weight / sum), computed in long double; the last
+  // boundary is exactly total.
+  auto cut = [&](int r) -> uint64_t {
+    if (r >= world) return total;
+    long double acc = 0;
+    for (int i = 0; i < r; ++i) acc += weights ? weights[i] : 1.0;
+    long double v = (long double)total * acc / (long double)sum;
+    uint64_t c = (uint64_t)v;
+    return c > total ? total : c;
+  };
+  *lo = cut(rank);
+  *hi = cut(rank + 1);
+  if (*hi < *lo) *hi = *lo;
+  return MOTIF_OK;
+}
+
+int motif_encode(const char* s, int32_t l, uint64_t* code) {
+  if (!s || !code || l < 1 || l > kMaxL) return MOTIF_ERR_ARG;
+  uint64_t c = 0;
+  for (int i = 0; i < l; ++i) {
+    int v;
+    switch (s[i]) {
+      case 'A': case 'a': v = 0; break;
+      case 'C': case 'c': v = 1; break;
+      case 'G': case 'g': v = 2; break;
+      case 'T': case 't': v = 3; break;
+      default: return MOTIF_ERR_ALPHABET;
+    }
+    c = (c << 2) | (uint64_t)v;
+  }
+  *code = c;
+  return MOTIF_OK;
+}
+
+int motif_decode(uint64_t code, int32_t l, char* out) {
+  if (!out || l < 1 || l > kMaxL) return MOTIF_ERR_ARG;
+  if (l < 32 && (code >> (2 * l)) != 0) return MOTIF_ERR_ARG;
+  static const char kB[4] = {'A', 'C', 'G', 'T'};
+  for (int i = 0; i < l; ++i) out[i] = kB[(code >> (2 * (l - 1 - i))) & 3u];
+  return MOTIF_OK;
+}
+
+}  // extern "C"

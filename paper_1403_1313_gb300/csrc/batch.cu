@@ -1,0 +1,375 @@
+// Batching and tuning.
+//
+// motif_batch_search runs many uneven jobs in one job table: every step launch walks all jobs
+// and pulls tiles of whichever passes still have work, so small jobs fill the SMs that a large
+// job's tail leaves idle and no job pays its own launch-and-drain cost.  The launch sequence can
+// be captured once in a CUDA graph and replayed until every job is done.
+//
+// motif_autotune times candidate configurations on a sub-range of the plan's candidates and
+// keeps the fastest, in the plan and in a process-wide cache keyed by the job's shape.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+using namespace motif;
+
+namespace motif_batch {
+
+// Per-device stream and job-table buffers reused across batch calls.
+struct BatchCtx {
+  cudaStream_t stream = nullptr;
+  JobDesc* d_jobs = nullptr;
+  JobState* d_states = nullptr;
+  StepCtl* d_ctl = nullptr;
+  int cap = 0;
+};
+std::mutex g_mu;
+BatchCtx g_ctx[64];
+
+int ensure_ctx(int dev, int njobs, BatchCtx** out) {
+  if (dev < 0 || dev >= 64) return MOTIF_ERR_ARG;
+  BatchCtx& c = g_ctx[dev];
+  if (!c.stream && cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess)
+    return MOTIF_ERR_CUDA;
+  if (njobs > c.cap) {
+    if (c.d_jobs) cudaFree(c.d_jobs);
+    if (c.d_states) cudaFree(c.d_states);
+    if (!c.d_ctl && cudaMalloc(&c.d_ctl, sizeof(StepCtl)) != cudaSuccess) return MOTIF_ERR_OOM;
+    const int cap = std::max(njobs, 64);
+    if (cudaMalloc(&c.d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
+        cudaMalloc(&c.d_states, sizeof(JobState) * cap) != cudaSuccess) {
+      c.cap = 0;
+      return MOTIF_ERR_OOM;
+    }
+    c.cap = cap;
+  }
+  *out = &c;
+  return MOTIF_OK;
+}
+
+// Runs the job table [0, njobs) of one kernel variant to completion on ctx->stream.
+int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, size_t smem,
+              int max_steps, bool use_graph, int timeout_ms) {
+  cudaStream_t s = c->stream;
+  if (!use_graph) {
+    return run_steps(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem,
+                     max_steps, true, timeout_ms, s, nullptr);
+  }
+  const int group = 4;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  for (int i = 0; i < group && e == cudaSuccess; ++i)
+    e = launch_step(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem, s);
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  const double t0 = now_ms();
+  int launched = 0, rc = MOTIF_OK;
+  while (e == cudaSuccess && launched < max_steps) {
+    e = cudaGraphLaunch(exec, s);
+    launched += group;
+    unsigned active = 0;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&active, &c->d_ctl->active_jobs, sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || active == 0) break;
+    if (timeout_ms > 0 && now_ms() - t0 > timeout_ms) {
+      rc = MOTIF_ERR_TIMEOUT;
+      break;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return rc;
+}
+
+}  // namespace motif_batch
+
+using namespace motif_batch;
+
+extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
+                                  uint64_t* const* out_codes, const int64_t* capacities,
+                                  int64_t* out_counts, int32_t* statuses, int32_t use_graph) {
+  if (njobs < 1 || !plans || !out_codes || !capacities || !out_counts || !statuses)
+    return MOTIF_ERR_ARG;
+  for (int j = 0; j < njobs; ++j) {
+    if (!plans[j] || capacities[j] < 0 || (capacities[j] > 0 && !out_codes[j])) return MOTIF_ERR_ARG;
+    if (plans[j]->device != plans[0]->device) return MOTIF_ERR_ARG;
+    statuses[j] = plans[j]->loaded ? MOTIF_OK : MOTIF_ERR_STATE;
+    out_counts[j] = 0;
+  }
+  DeviceGuard g(plans[0]->device);
+  std::lock_guard<std::mutex> lk(g_mu);
+  BatchCtx* c = nullptr;
+  int rc = ensure_ctx(plans[0]->device, njobs, &c);
+  if (rc) return rc;
+  // Every plan's pending work (loads) must finish before the batch stream reads its windows.
+  for (int j = 0; j < njobs; ++j) {
+    if (cudaStreamSynchronize(plans[j]->stream) != cudaSuccess) return MOTIF_ERR_CUDA;
+    if (plans[j]->check_alpha) {
+      int err = 0;
+      cudaMemcpy(&err, plans[j]->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+      plans[j]->check_alpha = false;
+      if (err) { plans[j]->loaded = false; statuses[j] = MOTIF_ERR_ALPHABET; }
+    }
+  }
+  const double t0 = now_ms();
+  // Group the device jobs by kernel variant; each group runs as one table.
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int j = 0; j < njobs; ++j) {
+    motif_plan_s* p = plans[j];
+    if (statuses[j] != MOTIF_OK || p->W <= 0 || p->hi <= p->lo || p->nchunks == 0) continue;
+    groups[{p->kind, p->p}].push_back(j);
+  }
+  std::vector<char> redo(njobs, 0);
+  for (auto& kv : groups) {
+    const int kind = kv.first.first, pv = kv.first.second;
+    const std::vector<int>& ids = kv.second;
+    std::vector<JobDesc> descs(ids.size());
+    size_t smem = 0;
+    int max_steps = 0, grid = 0, block = 256, timeout = 0;
+    for (size_t i = 0; i < ids.size(); ++i) {
+      motif_plan_s* p = plans[ids[i]];
+      fill_desc(p, &descs[i], p->d_out, (uint64_t)p->out_cap);
+      smem = std::max(smem, p->smem);
+      max_steps = std::max<int>(max_steps, (int)std::min<uint64_t>(p->nchunks * p->n + 2, 1 << 30));
+      block = p->block;
+      timeout = std::max(timeout, p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 60000);
+    }
+    if (step_kernel_attrs(kind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
+    grid = step_max_ctas_per_sm(kind, pv, block, smem) * plans[ids[0]]->sms;
+    if (grid <= 0) return MOTIF_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(c->d_jobs, descs.data(), sizeof(JobDesc) * ids.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_states, 0, sizeof(JobState) * ids.size(), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctl, 0, sizeof(StepCtl), c->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    rc = run_table(c, kind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
+                   timeout);
+    if (rc) return rc;
+    std::vector<JobState> st(ids.size());
+    e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    for (size_t i = 0; i < ids.size(); ++i) {
+      const int j = ids[i];
+      motif_plan_s* p = plans[j];
+      const unsigned long long found = st[i].out_count;
+      if (found > (unsigned long long)p->out_cap) {
+        redo[j] = 1;  // the plan's own buffer was too small: rerun this job alone below
+        continue;
+      }
+      // Sort/dedup this job's codes in its own buffer (count in the batch state array).
+      if (found > 4096) {
+        const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
+        if (need > p->sort_bytes) {
+          plan_free(p, p->d_sort, p->sort_bytes);
+          cudaStreamSynchronize(p->stream);
+          p->d_sort = plan_alloc(p, need);
+          cudaStreamSynchronize(p->stream);
+          p->sort_bytes = p->d_sort ? need : 0;
+          if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
+        }
+      }
+      e = launch_sort_unique(p->d_out, &c->d_states[i].out_count, p->out_cap, 2 * p->l,
+                             p->d_sort, p->sms, (long long)found, c->stream);
+      unsigned long long fc = 0;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&fc, &c->d_states[i].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
+                            c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return status_from_cuda(e);
+      out_counts[j] = (int64_t)fc;
+      p->stats.survivors = fc;
+      p->stats.candidates = p->hi - p->lo;
+      if ((int64_t)fc > capacities[j]) {
+        statuses[j] = MOTIF_ERR_CAPACITY;
+        continue;
+      }
+      if (fc) {
+        e = cudaMemcpyAsync(out_codes[j], p->d_out, fc * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return status_from_cuda(e);
+      }
+    }
+  }
+  for (int j = 0; j < njobs; ++j) {
+    if (!redo[j]) continue;
+    int64_t cnt = 0;
+    statuses[j] = motif_search(plans[j], out_codes[j], capacities[j], &cnt);
+    out_counts[j] = cnt;
+  }
+  const double ms = now_ms() - t0;
+  for (int j = 0; j < njobs; ++j) plans[j]->stats.total_ms = ms;
+  for (int j = 0; j < njobs; ++j)
+    if (statuses[j] != MOTIF_OK) return statuses[j];
+  return MOTIF_OK;
+}
+
+// ---- autotuner ---------------------------------------------------------------------------------
+
+namespace motif_tune {
+
+struct Choice {
+  int kernel, block, ctas_per_sm, cands_per_thread, compact_levels, suffix_bases;
+  double cand_per_s;
+};
+std::mutex g_tmu;
+std::map<std::string, Choice> g_cache;
+
+std::string key_of(const motif_plan_s* p) {
+  char buf[128];
+  snprintf(buf, sizeof(buf), "w%d_l%d_d%d_n%d_W%d_sm%d", p->l <= 16 ? 32 : 64, p->l, p->d, p->n,
+           p->W, p->sms);
+  return buf;
+}
+
+void apply(motif_opts* o, const Choice& c) {
+  o->kernel = c.kernel;
+  o->block = c.block;
+  o->ctas_per_sm = c.ctas_per_sm;
+  o->cands_per_thread = c.cands_per_thread;
+  o->compact_levels = c.compact_levels;
+  o->suffix_bases = c.suffix_bases;
+}
+
+}  // namespace motif_tune
+
+using namespace motif_tune;
+
+extern "C" int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best) {
+  if (!p) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  const std::string key = key_of(p);
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      apply(&p->opts, it->second);
+      int rc = plan_configure(p);
+      if (best) *best = p->opts;
+      return rc;
+    }
+  }
+  std::vector<Choice> cands;
+  for (int ks = 2; ks <= kMaxKs; ++ks) {
+    if (ks > p->l) break;
+    for (int span : {1, 2})
+      for (int cps : {0, 2})
+        cands.push_back({MOTIF_KERNEL_GROUP, 256, cps, 0, span, ks, 0});
+  }
+  for (int cpt : {1, 2, 4}) cands.push_back({MOTIF_KERNEL_CAND, 256, 0, cpt, 1, 0, 0});
+  const motif_opts saved = p->opts;
+  const uint64_t full_lo = p->lo, full_hi = p->hi;
+  const uint64_t span_c = full_hi - full_lo;
+  const double t_start = now_ms();
+  Choice win{};
+  win.cand_per_s = -1;
+  for (const Choice& c : cands) {
+    if (budget_ms > 0 && now_ms() - t_start > budget_ms && win.cand_per_s > 0) break;
+    motif_opts o = saved;
+    apply(&o, c);
+    // Sub-range sized for the kernel's speed: the per-candidate kernel is ~50x slower.
+    const uint64_t want = c.kernel == MOTIF_KERNEL_CAND ? (1ull << 22) : (1ull << 26);
+    o.range_lo = full_lo;
+    o.range_hi = full_lo + std::min<uint64_t>(span_c, want);
+    p->opts = o;
+    p->lo = o.range_lo;
+    p->hi = o.range_hi;
+    if (plan_configure(p) != MOTIF_OK) continue;
+    int64_t cnt = 0;
+    std::vector<uint64_t> tmp(1 << 16);
+    double best_ms = 1e30;
+    for (int rep = 0; rep < 2; ++rep) {
+      const int st = motif_search(p, tmp.data(), (int64_t)tmp.size(), &cnt);
+      if (st != MOTIF_OK && st != MOTIF_ERR_CAPACITY) { best_ms = 1e30; break; }
+      best_ms = std::min(best_ms, p->stats.search_ms + p->stats.sort_ms);
+    }
+    if (best_ms >= 1e30) continue;
+    Choice r = c;
+    r.cand_per_s = (double)(p->hi - p->lo) / (best_ms * 1e-3);
+    if (r.cand_per_s > win.cand_per_s) win = r;
+  }
+  p->opts = saved;
+  p->lo = full_lo;
+  p->hi = full_hi;
+  if (win.cand_per_s <= 0) {
+    plan_configure(p);
+    return MOTIF_ERR_CUDA;
+  }
+  apply(&p->opts, win);
+  p->opts.range_lo = saved.range_lo;
+  p->opts.range_hi = saved.range_hi;
+  int rc = plan_configure(p);
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_cache[key] = win;
+  }
+  if (best) *best = p->opts;
+  return rc;
+}
+
+extern "C" int motif_tune_cache_save(const char* path) {
+  if (!path) return MOTIF_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  FILE* f = fopen(path, "w");
+  if (!f) return MOTIF_ERR_ARG;
+  fprintf(f, "{\n");
+  size_t i = 0;
+  for (auto& kv : g_cache) {
+    const Choice& c = kv.second;
+    fprintf(f,
+            "  \"%s\": {\"kernel\": %d, \"block\": %d, \"ctas_per_sm\": %d, "
+            "\"cands_per_thread\": %d, \"compact_levels\": %d, \"suffix_bases\": %d, "
+            "\"cand_per_s\": %.6g}%s\n",
+            kv.first.c_str(), c.kernel, c.block, c.ctas_per_sm, c.cands_per_thread,
+            c.compact_levels, c.suffix_bases, c.cand_per_s, ++i < g_cache.size() ? "," : "");
+  }
+  fprintf(f, "}\n");
+  fclose(f);
+  return MOTIF_OK;
+}
+
+extern "C" int motif_tune_cache_load(const char* path) {
+  if (!path) return MOTIF_ERR_ARG;
+  FILE* f = fopen(path, "r");
+  if (!f) return MOTIF_ERR_ARG;
+  char line[512];
+  std::lock_guard<std::mutex> lk(g_tmu);
+  while (fgets(line, sizeof(line), f)) {
+    char key[128];
+    Choice c{};
+    if (sscanf(line,
+               " \"%127[^\"]\": {\"kernel\": %d, \"block\": %d, \"ctas_per_sm\": %d, "
+               "\"cands_per_thread\": %d, \"compact_levels\": %d, \"suffix_bases\": %d, "
+               "\"cand_per_s\": %lf",
+               key, &c.kernel, &c.block, &c.ctas_per_sm, &c.cands_per_thread, &c.compact_levels,
+               &c.suffix_bases, &c.cand_per_s) == 8)
+      g_cache[key] = c;
+  }
+  fclose(f);
+  return MOTIF_OK;
+}
+
+namespace motif {
+// Applies a cached tuning choice to fresh plans created with MOTIF_KERNEL_AUTO.
+bool tune_lookup(const motif_plan_s* p, motif_opts* o) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  auto it = g_cache.find(key_of(p));
+  if (it == g_cache.end()) return false;
+  apply(o, it->second);
+  return true;
+}
+}  // namespace motif

@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/motif.h"
+
+namespace motif {
+
+constexpr int kMaxL = 31;            // 4^l must fit in 64 bits
+constexpr int kWinAlign = 8;         // window rows padded to a multiple of 8 (four 128-bit loads)
+constexpr int kMaxKs = 4;            // GROUP kernel: at most 4 suffix bases (256-bit masks)
+constexpr int kPassNone = -1;
+
+// Per-job descriptor, written by the host before a job's first step and read-only on the device.
+struct JobDesc {
+  int32_t n, t, l, d;
+  int32_t W;                 // windows per sequence, t - l + 1 (> 0 for every device job)
+  int32_t wstride;           // row stride of planes / codes in windows (multiple of kWinAlign)
+  const uint2* planes;       // [n][wstride] compressed bit planes (E, O) of each window
+  const uint64_t* codes;     // [n][wstride] packed 2l-bit code of each window
+  int32_t kind;              // MOTIF_KERNEL_CAND or MOTIF_KERNEL_GROUP
+  int32_t ks;                // GROUP: suffix bases per group (1..kMaxKs); CAND: 0
+  int32_t cpt;               // CAND: candidates per lane in a fresh pass (1, 2 or 4)
+  int32_t span0;             // sequences a fresh pass scans before the first compaction
+  uint64_t lo, hi;           // candidate range [lo, hi)
+  uint64_t unit_lo, unit_hi; // work units of the range: candidates (CAND) or groups (GROUP)
+  uint64_t chunk_units;      // units per chunk (bounds the queues)
+  uint64_t nchunks;
+  uint64_t rest_threshold;   // a queue pass with <= this many entries finishes every sequence
+  uint32_t* qidx[2];         // ping-pong survivor queues: unit offset within the chunk
+  uint64_t* qmask[2];        // GROUP: alive masks, mask_words(ks) words per entry
+  uint64_t qcap;             // entries per queue (>= chunk_units)
+  uint64_t* out;             // accepted codes, appended
+  uint64_t out_cap;
+  const uint64_t* ball;      // GROUP: Hamming-ball table for ks (see ball_table_words)
+};
+
+// Per-job device state, advanced by the last CTA of every step.
+struct JobState {
+  unsigned long long cursor;     // next work item of the current pass
+  unsigned long long qcount[2];  // entries in each queue
+  unsigned long long out_count;  // accepted codes (may exceed out_cap)
+  unsigned long long chunk;      // current chunk
+  int32_t pass_seq;              // first sequence of the current pass (0 = fresh chunk)
+  int32_t qsel;                  // input queue of a queue pass
+  int32_t done;
+  int32_t error;
+  unsigned long long steps;      // steps in which the job had work
+  unsigned long long pad[2];
+};
+
+// Step control block (one per launch sequence).
+struct StepCtl {
+  unsigned int ctas_done;        // CTAs finished in the current step
+  unsigned int tiles_per_warp;   // 0 = unlimited; else each warp grabs at most this many tiles
+  unsigned int active_jobs;      // written by the last CTA: jobs not yet done
+  unsigned int steps;            // steps executed
+};
+
+__host__ __device__ inline int mask_words(int ks) { return ks <= 3 ? 1 : (1 << (2 * ks - 6)); }
+// Ball table for ks: for every suffix value v in [0, 4^ks) and radius r in [0, ks], the
+// 4^ks-bit mask of suffixes within Hamming distance r of v; mask_words(ks) words per entry.
+__host__ __device__ inline int ball_table_words(int ks) {
+  return (1 << (2 * ks)) * (ks + 1) * mask_words(ks);
+}
+
+// ---- launchers (stream-ordered, no host synchronisation) ---------------------------------
+cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l, int wstride,
+                        uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s);
+// Fills the Hamming-ball table for ks (ball_table_words(ks) words).
+cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s);
+// Step kernel variants: kind = MOTIF_KERNEL_CAND with p = candidates per lane (1, 2, 4), or
+// MOTIF_KERNEL_GROUP with p = ks (1..4).  Every job of one launch must use the same variant.
+bool step_variant_ok(int kind, int p);
+size_t step_smem_bytes(int kind, int p, int wstride);
+cudaError_t step_kernel_attrs(int kind, int p, size_t smem);
+int step_max_ctas_per_sm(int kind, int p, int block, size_t smem);
+cudaError_t launch_step(int kind, int p, const JobDesc* d_jobs, JobState* d_states, int njobs,
+                        StepCtl* d_ctl, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
+                         cudaStream_t s);
+// Sorts d_codes[0 .. *d_count) ascending and removes repeats in place (count updated) when
+// *d_count <= cap.  known_count >= 0 lets the host skip the path that cannot apply.
+size_t sort_scratch_bytes(int64_t cap, int sms);
+cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, int64_t cap,
+                               int key_bits, void* scratch, int sms, long long known_count,
+                               cudaStream_t s);
+
+}  // namespace motif

@@ -1,0 +1,80 @@
+// K0: window extraction (Sec. IV.A: every window is extracted before the search starts).
+//
+// Each thread turns one length-l window of one sequence into
+//   - its packed 2l-bit code: base i (0 = leftmost) in bits [2(l-1-i), 2(l-1-i)+1], A=0 C=1 G=2
+//     T=3, so the code of a window equals the index of the identical candidate l-mer;
+//   - its two compressed bit planes: E holds the low bit of every base, O the high bit, base i
+//     at plane bit (l-1-i).  Two l-mers differ at base i exactly when E or O differs at bit
+//     l-1-i, so their Hamming distance is popc((E1 ^ E2) | (O1 ^ O2)) for every l <= 32.
+// Rows are padded to `wstride` windows by repeating the last window: a repeated window
+// matches exactly when the original does, so scans may run over the padding unguarded.
+#include "motif_internal.h"
+
+namespace motif {
+namespace {
+
+__device__ __forceinline__ int base_code(char ch) {
+  switch (ch) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    default: return -1;
+  }
+}
+
+__global__ void validate_kernel(const char* __restrict__ chars, int64_t stride, int n, int t,
+                                int* err) {
+  const int64_t total = (int64_t)n * t;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / t, c = i - r * t;
+    if (base_code(chars[r * stride + c]) < 0) atomicOr(err, 1);
+  }
+}
+
+__global__ void pack_kernel(const char* __restrict__ chars, int64_t stride, int n, int t, int l,
+                            int wstride, uint2* __restrict__ planes,
+                            uint64_t* __restrict__ codes) {
+  const int W = t - l + 1;
+  const int64_t total = (int64_t)n * wstride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / wstride);
+    int j = (int)(i - (int64_t)s * wstride);
+    if (j >= W) j = W - 1;  // padding repeats the last window
+    const char* p = chars + (int64_t)s * stride + j;
+    uint64_t code = 0;
+    uint32_t E = 0, O = 0;
+    for (int b = 0; b < l; ++b) {
+      int v = base_code(p[b]);
+      v = v < 0 ? 0 : v;  // invalid characters are reported by validate_kernel
+      code = (code << 2) | (uint64_t)v;
+      E = (E << 1) | (uint32_t)(v & 1);
+      O = (O << 1) | (uint32_t)(v >> 1);
+    }
+    planes[i] = make_uint2(E, O);
+    codes[i] = code;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l, int wstride,
+                        uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s) {
+  const int block = 256;
+  const int64_t chars = (int64_t)n * t;
+  int grid = (int)((chars + block - 1) / block);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  validate_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, d_err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || t < l) return e;
+  const int64_t wins = (int64_t)n * wstride;
+  grid = (int)((wins + block - 1) / block);
+  if (grid > 4096) grid = 4096;
+  pack_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, l, wstride, planes, codes);
+  return cudaGetLastError();
+}
+
+}  // namespace motif

@@ -1,0 +1,98 @@
+// Host-side plan object and the helpers shared by the ABI, batching, tuning and serving code.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <chrono>
+#include <vector>
+
+#include "motif_internal.h"
+
+struct motif_plan_s {
+  // problem (Sec. I.A: n sequences of length t; pattern length l; d allowed mismatches)
+  int n = 0, t = 0, l = 0, d = 0;
+  int W = 0;                 // windows per sequence, t - l + 1 (may be <= 0)
+  int wstride = 0;           // padded windows per row
+  motif_opts opts{};
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+
+  // kernel configuration
+  int kind = MOTIF_KERNEL_GROUP;
+  int p = 4;                 // candidates per lane (CAND) or suffix bases ks (GROUP)
+  int span0 = 2;
+  int block = 256, grid = 0;
+  size_t smem = 0;
+  uint64_t lo = 0, hi = 0;   // candidate range
+  uint64_t unit_lo = 0, unit_hi = 0, chunk_units = 0, nchunks = 0, rest_threshold = 0;
+
+  // device memory owned by the plan
+  char* d_chars = nullptr;
+  size_t chars_bytes = 0;
+  uint2* d_planes = nullptr;
+  uint64_t* d_codes = nullptr;
+  int* d_err = nullptr;
+  uint32_t* d_qidx[2] = {nullptr, nullptr};
+  uint64_t* d_qmask[2] = {nullptr, nullptr};
+  uint64_t qcap = 0;
+  int qmask_words = 0;
+  uint64_t* d_out = nullptr;
+  int64_t out_cap = 0;
+  void* d_sort = nullptr;
+  size_t sort_bytes = 0;
+  motif::JobDesc* d_job = nullptr;
+  motif::JobState* d_state = nullptr;
+  motif::StepCtl* d_ctl = nullptr;
+  unsigned long long* d_total = nullptr;
+  int64_t device_bytes = 0;
+
+  bool loaded = false;
+  bool check_alpha = false;  // device-loaded characters not yet validated on the host
+  motif_stats_t stats{};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace motif {
+
+// Device memory through the plan's allocator (or stream-ordered cudaMallocAsync).
+void* plan_alloc(motif_plan_s* p, size_t bytes);
+void plan_free(motif_plan_s* p, void* ptr, size_t bytes);
+
+// Ball table of ks on the plan's device (built once per device and ks).
+const uint64_t* ball_table(int device, int ks, cudaStream_t s);
+
+// Fills the device descriptor of the plan's job (host copy).
+void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_cap);
+
+// (Re)applies the kernel configuration: variant, grid, shared memory, chunking and queues.
+int plan_configure(motif_plan_s* p);
+
+// Launches steps for a job table until no job is active (polling every `group` steps), or
+// blindly `max_steps` steps when poll == false.  Returns a motif_status.
+int run_steps(int kind, int pv, const JobDesc* d_jobs, JobState* d_states, int njobs,
+              StepCtl* d_ctl, int grid, int block, size_t smem, int max_steps, bool poll,
+              int timeout_ms, cudaStream_t s, int* steps_run);
+
+int status_from_cuda(cudaError_t e);
+
+// Copies a cached tuning choice for the plan's shape into *o; false when none is cached.
+bool tune_lookup(const motif_plan_s* p, motif_opts* o);
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+inline double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace motif

@@ -1,0 +1,674 @@
+// K1: the skip-BF search (Sec. III.A) as a multi-job, pass-structured CUDA kernel.
+//
+// Work is organised in *passes*.  A pass takes a list of live work units of one job and scans
+// one or a few consecutive sequences for each of them, lane by lane:
+//   - a fresh pass takes its units straight from the candidate index range of the current chunk
+//     (Sec. IV.A: l-mers are produced from their index, never stored) and scans sequences
+//     [0, span0);
+//   - a queue pass takes the survivors that the previous pass compacted into a ping-pong queue
+//     and scans the next sequence, or every remaining sequence once few survivors are left;
+//   - units that fail a sequence are dropped on the spot and never look at the remaining
+//     sequences (the skip of Sec. III.A); units that pass every sequence are accepted.
+// Survivors are compacted with a warp ballot / prefix sum and one atomic per warp, so that the
+// next pass runs full warps instead of lanes idling behind the skip.
+//
+// Two unit kinds share this structure:
+//   CAND  — one candidate l-mer per lane (cpt per lane in a fresh pass).  Per window:
+//           m = (E_c ^ E_w) | (O_c ^ O_w) over the compressed bit planes (the pair-fold of the
+//           XOR of the packed codes), dist = popc(m), running min, early break once the
+//           minimum is <= d (Sec. III.A: "the Hamming distance ... less than or equal to d").
+//   GROUP — one group of 4^ks candidates sharing their first l-ks bases per lane.  Per window
+//           one POPC gives the prefix distance h; when h <= d the suffixes within d-h of the
+//           window's last ks bases (a precomputed Hamming-ball mask) are marked as matched.
+//           Hamming distance is additive over positions, so each candidate of the group is
+//           matched by exactly the windows the per-candidate test would accept.
+//
+// A launch of the step kernel advances every job in the table by one pass (or part of one,
+// under a tile budget).  CTAs are persistent: each walks the jobs in table order, stages the
+// windows of the pass into shared memory and pulls 32-unit tiles per warp from the job's pass
+// cursor.  The last CTA to finish advances each job's state for the next launch; no CTA ever
+// waits for another.
+#include "motif_internal.h"
+
+namespace motif {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxStageSeqs = 2;  // sequences of one pass staged in shared memory
+
+__device__ __forceinline__ uint32_t compress_even(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
+// Compressed planes of a packed code: E = low bit of each base, O = high bit.
+__device__ __forceinline__ void code_planes(uint64_t k, uint32_t& E, uint32_t& O) {
+  E = compress_even(k);
+  O = compress_even(k >> 1);
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ int ld_volatile(const int32_t* p) {
+  return *reinterpret_cast<const volatile int32_t*>(p);
+}
+
+// Reserves `cnt` slots per lane at `counter` with one atomic per warp; returns this lane's
+// first slot.  Must be called by all 32 lanes.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter,
+                                                           unsigned cnt) {
+  const int lane = threadIdx.x & 31;
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned total = __shfl_sync(kFull, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(counter, (unsigned long long)total);
+  base = __shfl_sync(kFull, base, 31);
+  return base + (incl - cnt);
+}
+
+// Shape of the pass a job is in; identical in every CTA of a step.
+struct Pass {
+  unsigned long long work;  // items of the pass
+  uint64_t chunk_base;      // first unit of the chunk
+  uint64_t chunk_units;     // units in the chunk
+  int s0, s1;               // sequences [s0, s1) scanned in-lane
+  int fresh;                // items are chunk units (1) or queue entries (0)
+  int qin, qout;
+  int staged;               // windows of [s0, s1) come from shared memory
+};
+
+__device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
+  Pass p;
+  const unsigned long long chunk = ld_volatile(&st->chunk);
+  const int pass_seq = ld_volatile(&st->pass_seq);
+  p.chunk_base = jd.unit_lo + chunk * jd.chunk_units;
+  const uint64_t left = jd.unit_hi > p.chunk_base ? jd.unit_hi - p.chunk_base : 0;
+  p.chunk_units = left < jd.chunk_units ? left : jd.chunk_units;
+  if (pass_seq == 0) {
+    p.fresh = 1;
+    p.work = p.chunk_units;
+    p.s0 = 0;
+    p.s1 = jd.span0 < jd.n ? jd.span0 : jd.n;
+    p.qin = 0;
+    p.qout = 0;
+  } else {
+    p.fresh = 0;
+    p.qin = ld_volatile(&st->qsel);
+    p.qout = 1 - p.qin;
+    p.work = ld_volatile(&st->qcount[p.qin]);
+    p.s0 = pass_seq;
+    p.s1 = p.work <= jd.rest_threshold ? jd.n : (pass_seq + 1 < jd.n ? pass_seq + 1 : jd.n);
+  }
+  p.staged = (p.s1 - p.s0) <= kMaxStageSeqs;
+  return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// CAND: one candidate per lane slot.
+
+// Scans one sequence's windows for up to CPT candidates; returns the subset of `alive` that
+// has a window within distance d.  `w4` holds two windows (E0,O0,E1,O1) per uint4 and the row
+// is padded to a multiple of 8 windows.
+template <int CPT, bool GLOBAL>
+__device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int wpad, int d,
+                                              const uint32_t (&E)[CPT], const uint32_t (&O)[CPT],
+                                              unsigned alive) {
+  uint32_t mn[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) mn[c] = 64u;
+  const int n4 = wpad >> 1;  // uint4 count
+  for (int q = 0; q < n4; q += 4) {
+    uint4 a, b, e, f;
+    if (GLOBAL) {
+      a = __ldg(w4 + q); b = __ldg(w4 + q + 1); e = __ldg(w4 + q + 2); f = __ldg(w4 + q + 3);
+    } else {
+      a = w4[q]; b = w4[q + 1]; e = w4[q + 2]; f = w4[q + 3];
+    }
+    unsigned hit = 0;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      uint32_t m = mn[c];
+      m = min(m, (uint32_t)__popc((E[c] ^ a.x) | (O[c] ^ a.y)));
+      m = min(m, (uint32_t)__popc((E[c] ^ a.z) | (O[c] ^ a.w)));
+      m = min(m, (uint32_t)__popc((E[c] ^ b.x) | (O[c] ^ b.y)));
+      m = min(m, (uint32_t)__popc((E[c] ^ b.z) | (O[c] ^ b.w)));
+      m = min(m, (uint32_t)__popc((E[c] ^ e.x) | (O[c] ^ e.y)));
+      m = min(m, (uint32_t)__popc((E[c] ^ e.z) | (O[c] ^ e.w)));
+      m = min(m, (uint32_t)__popc((E[c] ^ f.x) | (O[c] ^ f.y)));
+      m = min(m, (uint32_t)__popc((E[c] ^ f.z) | (O[c] ^ f.w)));
+      mn[c] = m;
+      hit |= (m <= (uint32_t)d ? 1u : 0u) << c;
+    }
+    if ((hit & alive) == alive) break;  // every live candidate has matched this sequence
+  }
+  unsigned matched = 0;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) matched |= (mn[c] <= (uint32_t)d ? 1u : 0u) << c;
+  return matched & alive;
+}
+
+template <int CPT>
+__device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
+                          unsigned long long base, const uint4* stage) {
+  const int lane = threadIdx.x & 31;
+  uint32_t E[CPT], O[CPT], off[CPT];
+  unsigned alive = 0;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    const unsigned long long item = base + (unsigned long long)c * 32 + lane;
+    off[c] = 0;
+    E[c] = O[c] = 0;
+    if (item < p.work) {
+      off[c] = p.fresh ? (uint32_t)item : jd.qidx[p.qin][item];
+      code_planes(p.chunk_base + off[c], E[c], O[c]);
+      alive |= 1u << c;
+    }
+  }
+  const int wpad = jd.wstride;
+  for (int s = p.s0; s < p.s1 && alive; ++s) {
+    if (p.staged) {
+      alive = scan_cand<CPT, false>(stage + (size_t)(s - p.s0) * (wpad >> 1), wpad, jd.d, E, O,
+                                    alive);
+    } else {
+      const uint4* g = reinterpret_cast<const uint4*>(jd.planes + (size_t)s * wpad);
+      alive = scan_cand<CPT, true>(g, wpad, jd.d, E, O, alive);
+    }
+  }
+  __syncwarp();
+  const unsigned cnt = __popc(alive);
+  if (p.s1 >= jd.n) {
+    unsigned long long slot = warp_reserve(&st->out_count, cnt);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (alive & (1u << c)) {
+        if (slot < jd.out_cap) jd.out[slot] = p.chunk_base + off[c];
+        ++slot;
+      }
+  } else {
+    unsigned long long slot = warp_reserve(&st->qcount[p.qout], cnt);
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (alive & (1u << c)) jd.qidx[p.qout][slot++] = off[c];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// GROUP: 4^KS candidates sharing their first l-KS bases per lane.
+
+template <int KS>
+struct GroupMask {
+  static constexpr int NW = (KS <= 3) ? 1 : (1 << (2 * KS - 6));
+  uint64_t w[NW];
+};
+
+// Marks, in `matched`, the suffixes within r of suffix value v (ball table row).
+template <int KS, bool GLOBAL>
+__device__ __forceinline__ void or_ball(GroupMask<KS>& matched, const uint64_t* ball, int v,
+                                        int r) {
+  constexpr int NW = GroupMask<KS>::NW;
+  const uint64_t* row = ball + ((size_t)v * (KS + 1) + r) * NW;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) matched.w[i] |= GLOBAL ? __ldg(row + i) : row[i];
+}
+
+template <int KS>
+__device__ __forceinline__ bool covers(const GroupMask<KS>& matched, const GroupMask<KS>& alive) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < GroupMask<KS>::NW; ++i) ok &= (matched.w[i] & alive.w[i]) == alive.w[i];
+  return ok;
+}
+
+template <int KS>
+__device__ __forceinline__ bool any_set(const GroupMask<KS>& m) {
+  uint64_t o = 0;
+#pragma unroll
+  for (int i = 0; i < GroupMask<KS>::NW; ++i) o |= m.w[i];
+  return o != 0;
+}
+
+// One window with prefix distance h (already known <= d): or in the ball of its suffix.
+template <int KS, bool GLOBAL>
+__device__ __forceinline__ void group_hit(GroupMask<KS>& matched, const uint64_t* ball, int d,
+                                          int h, int v) {
+  int r = d - h;
+  r = r < KS ? r : KS;
+  or_ball<KS, GLOBAL>(matched, ball, v, r);
+}
+
+// Staged form: wp4 holds two prefix-plane windows per uint4, sfx the suffix value per window.
+template <int KS>
+__device__ __forceinline__ void scan_group_staged(const uint4* __restrict__ wp4,
+                                                  const uint16_t* __restrict__ sfx, int wpad,
+                                                  int d, uint32_t Ep, uint32_t Op,
+                                                  const uint64_t* ball, GroupMask<KS>& alive) {
+  GroupMask<KS> matched;
+#pragma unroll
+  for (int i = 0; i < GroupMask<KS>::NW; ++i) matched.w[i] = 0;
+  const int n4 = wpad >> 1;
+  for (int q = 0; q < n4; q += 2) {
+    const uint4 a = wp4[q], b = wp4[q + 1];
+    const int h0 = __popc((Ep ^ a.x) | (Op ^ a.y));
+    const int h1 = __popc((Ep ^ a.z) | (Op ^ a.w));
+    const int h2 = __popc((Ep ^ b.x) | (Op ^ b.y));
+    const int h3 = __popc((Ep ^ b.z) | (Op ^ b.w));
+    if (min(min(h0, h1), min(h2, h3)) <= d) {
+      const int j = q * 2;
+      if (h0 <= d) group_hit<KS, false>(matched, ball, d, h0, sfx[j]);
+      if (h1 <= d) group_hit<KS, false>(matched, ball, d, h1, sfx[j + 1]);
+      if (h2 <= d) group_hit<KS, false>(matched, ball, d, h2, sfx[j + 2]);
+      if (h3 <= d) group_hit<KS, false>(matched, ball, d, h3, sfx[j + 3]);
+      if (covers<KS>(matched, alive)) break;  // every live candidate matched this sequence
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < GroupMask<KS>::NW; ++i) alive.w[i] &= matched.w[i];
+}
+
+// Global form (few survivors left): planes and codes read through the read-only path.
+template <int KS>
+__device__ __forceinline__ void scan_group_global(const uint2* __restrict__ planes,
+                                                  const uint64_t* __restrict__ codes, int wpad,
+                                                  int d, uint32_t Ep, uint32_t Op,
+                                                  const uint64_t* ball, GroupMask<KS>& alive) {
+  GroupMask<KS> matched;
+#pragma unroll
+  for (int i = 0; i < GroupMask<KS>::NW; ++i) matched.w[i] = 0;
+  const uint4* p4 = reinterpret_cast<const uint4*>(planes);
+  const uint64_t smask = (1ull << (2 * KS)) - 1;
+  for (int q = 0; q < (wpad >> 1); ++q) {
+    const uint4 a = __ldg(p4 + q);
+    const int h0 = __popc((Ep ^ (a.x >> KS)) | (Op ^ (a.y >> KS)));
+    const int h1 = __popc((Ep ^ (a.z >> KS)) | (Op ^ (a.w >> KS)));
+    if (min(h0, h1) <= d) {
+      if (h0 <= d) group_hit<KS, true>(matched, ball, d, h0, (int)(__ldg(codes + 2 * q) & smask));
+      if (h1 <= d)
+        group_hit<KS, true>(matched, ball, d, h1, (int)(__ldg(codes + 2 * q + 1) & smask));
+      if (covers<KS>(matched, alive)) break;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < GroupMask<KS>::NW; ++i) alive.w[i] &= matched.w[i];
+}
+
+// Initial alive mask of group g: the suffixes s with lo <= (g << 2KS) + s < hi.
+template <int KS>
+__device__ __forceinline__ void range_mask(uint64_t g, uint64_t lo, uint64_t hi,
+                                           GroupMask<KS>& m) {
+  constexpr int NW = GroupMask<KS>::NW;
+  constexpr int BITS = 1 << (2 * KS);
+  const uint64_t first = g << (2 * KS);
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    const int wbits = BITS < 64 ? BITS : 64;
+    uint64_t word = wbits == 64 ? ~0ull : ((1ull << wbits) - 1);
+    const uint64_t wlo = first + (uint64_t)i * 64;  // code of bit 0 of this word
+    // clear bits below lo
+    if (lo > wlo) {
+      const uint64_t k = lo - wlo;
+      word = k >= 64 ? 0 : (word & (~0ull << k));
+    }
+    // clear bits at or above hi
+    if (hi < wlo + (uint64_t)wbits) {
+      const uint64_t k = hi > wlo ? hi - wlo : 0;
+      word = k == 0 ? 0 : (word & (~0ull >> (64 - k)));
+    }
+    m.w[i] = word;
+  }
+}
+
+template <int KS>
+__device__ void group_tile(const JobDesc& jd, JobState* st, const Pass& p,
+                           unsigned long long base, const uint4* stage_wp,
+                           const uint16_t* stage_sfx, const uint64_t* stage_ball) {
+  constexpr int NW = GroupMask<KS>::NW;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long item = base + lane;
+  GroupMask<KS> alive;
+  uint32_t off = 0, Ep = 0, Op = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) alive.w[i] = 0;
+  if (item < p.work) {
+    if (p.fresh) {
+      off = (uint32_t)item;
+      range_mask<KS>(p.chunk_base + off, jd.lo, jd.hi, alive);
+    } else {
+      off = jd.qidx[p.qin][item];
+      const uint64_t* src = jd.qmask[p.qin] + item * NW;
+#pragma unroll
+      for (int i = 0; i < NW; ++i) alive.w[i] = src[i];
+    }
+    code_planes(p.chunk_base + off, Ep, Op);  // prefix planes of the group (l-KS bases)
+  }
+  const int wpad = jd.wstride;
+  for (int s = p.s0; s < p.s1 && any_set<KS>(alive); ++s) {
+    if (p.staged) {
+      const int r = s - p.s0;
+      scan_group_staged<KS>(stage_wp + (size_t)r * (wpad >> 1), stage_sfx + (size_t)r * wpad, wpad,
+                            jd.d, Ep, Op, stage_ball, alive);
+    } else {
+      scan_group_global<KS>(jd.planes + (size_t)s * wpad, jd.codes + (size_t)s * wpad, wpad, jd.d,
+                            Ep, Op, jd.ball, alive);
+    }
+  }
+  __syncwarp();
+  if (p.s1 >= jd.n) {
+    unsigned cnt = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) cnt += __popcll(alive.w[i]);
+    unsigned long long slot = warp_reserve(&st->out_count, cnt);
+    const uint64_t first = (p.chunk_base + off) << (2 * KS);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      uint64_t w = alive.w[i];
+      while (w) {
+        const int b = __ffsll((long long)w) - 1;
+        w &= w - 1;
+        if (slot < jd.out_cap) jd.out[slot] = first + (uint64_t)i * 64 + b;
+        ++slot;
+      }
+    }
+  } else {
+    const unsigned cnt = any_set<KS>(alive) ? 1u : 0u;
+    const unsigned long long slot = warp_reserve(&st->qcount[p.qout], cnt);
+    if (cnt) {
+      jd.qidx[p.qout][slot] = off;
+      uint64_t* dst = jd.qmask[p.qout] + slot * NW;
+#pragma unroll
+      for (int i = 0; i < NW; ++i) dst[i] = alive.w[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The step kernel.
+
+// KIND = MOTIF_KERNEL_CAND with P = candidates per lane, or MOTIF_KERNEL_GROUP with P = ks.
+template <int KIND, int P>
+__global__ void __launch_bounds__(256) step_kernel(const JobDesc* __restrict__ jobs,
+                                                   JobState* states, int njobs, StepCtl* ctl) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ JobDesc s_jd;
+  __shared__ Pass s_pass;
+  __shared__ int s_skip;
+  __shared__ unsigned s_tiles;
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const unsigned budget = ctl->tiles_per_warp * (blockDim.x >> 5);
+  if (tid == 0) s_tiles = 0;
+
+  for (int j = 0; j < njobs; ++j) {
+    __syncthreads();
+    if (tid == 0) {
+      int skip = 1;
+      if (!ld_volatile(&states[j].done) && (budget == 0 || s_tiles < budget)) {
+        s_jd = jobs[j];
+        s_pass = make_pass(s_jd, &states[j]);
+        skip = ld_volatile(&states[j].cursor) >= s_pass.work;
+      }
+      s_skip = skip;
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    const JobDesc& jd = s_jd;
+    const Pass p = s_pass;
+    JobState* st = &states[j];
+    const int wpad = jd.wstride;
+    const int nst = p.staged ? p.s1 - p.s0 : 0;
+
+    // Stage the windows of the pass (and the ball table) in shared memory.
+    const uint4* stage4 = reinterpret_cast<const uint4*>(smem);
+    const uint16_t* stage_sfx = nullptr;
+    const uint64_t* stage_ball = nullptr;
+    if (KIND == MOTIF_KERNEL_CAND) {
+      uint4* dst = reinterpret_cast<uint4*>(smem);
+      const uint4* src = reinterpret_cast<const uint4*>(jd.planes + (size_t)p.s0 * wpad);
+      for (int i = tid; i < nst * (wpad >> 1); i += blockDim.x) dst[i] = src[i];
+    } else {
+      uint2* dwp = reinterpret_cast<uint2*>(smem);
+      uint16_t* dsfx = reinterpret_cast<uint16_t*>(smem + (size_t)kMaxStageSeqs * wpad * 8);
+      uint64_t* dball =
+          reinterpret_cast<uint64_t*>(smem + (size_t)kMaxStageSeqs * wpad * 10 + 16 -
+                                      ((size_t)kMaxStageSeqs * wpad * 10) % 16);
+      const uint64_t smask = (1ull << (2 * P)) - 1;
+      for (int i = tid; i < nst * wpad; i += blockDim.x) {
+        const uint2 pl = jd.planes[(size_t)p.s0 * wpad + i];
+        dwp[i] = make_uint2(pl.x >> P, pl.y >> P);
+        dsfx[i] = (uint16_t)(jd.codes[(size_t)p.s0 * wpad + i] & smask);
+      }
+      const int bw = ball_table_words(P);
+      for (int i = tid; i < bw; i += blockDim.x) dball[i] = jd.ball[i];
+      stage_sfx = dsfx;
+      stage_ball = dball;
+    }
+    __syncthreads();
+
+    // Pull 32-unit tiles (32*cpt candidates for a fresh CAND pass) until the pass is exhausted.
+    const unsigned long long tile =
+        (KIND == MOTIF_KERNEL_CAND && p.fresh) ? 32ull * P : 32ull;
+    for (;;) {
+      unsigned long long base = 0;
+      int stop = 0;
+      if (lane == 0) {
+        if (budget != 0 && atomicAdd(&s_tiles, 1u) >= budget) {
+          stop = 1;
+        } else {
+          base = atomicAdd(&st->cursor, tile);
+          stop = base >= p.work;
+        }
+      }
+      stop = __shfl_sync(kFull, stop, 0);
+      if (stop) break;
+      base = __shfl_sync(kFull, base, 0);
+      if (KIND == MOTIF_KERNEL_CAND) {
+        if (p.fresh) cand_tile<P>(jd, st, p, base, stage4);
+        else cand_tile<1>(jd, st, p, base, stage4);
+      } else {
+        group_tile<P>(jd, st, p, base, stage4, stage_sfx, stage_ball);
+      }
+    }
+  }
+
+  // The last CTA to finish advances every job to its next pass.
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->ctas_done, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  unsigned active = 0;
+  for (int j = tid; j < njobs; j += blockDim.x) {
+    JobState* st = &states[j];
+    if (ld_volatile(&st->done)) continue;
+    const JobDesc jd = jobs[j];
+    const Pass p = make_pass(jd, st);
+    const unsigned long long cur = ld_volatile(&st->cursor);
+    if (cur > 0 || p.work == 0) st->steps += 1;
+    if (cur >= p.work) {  // the pass is complete
+      st->cursor = 0;
+      const bool chunk_done = p.s1 >= jd.n || ld_volatile(&st->qcount[p.qout]) == 0;
+      if (chunk_done) {
+        const unsigned long long next = ld_volatile(&st->chunk) + 1;
+        st->chunk = next;
+        st->pass_seq = 0;
+        st->qcount[0] = 0;
+        if (next >= jd.nchunks) st->done = 1;
+      } else {
+        st->pass_seq = p.s1;
+        st->qsel = p.qout;
+        st->qcount[1 - p.qout] = 0;
+      }
+    }
+    if (!ld_volatile(&st->done)) ++active;
+  }
+  // Block-wide sum of `active`.
+  for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(kFull, active, o);
+  __shared__ unsigned s_act[32];
+  if (lane == 0) s_act[tid >> 5] = active;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_act[w];
+    ctl->active_jobs = tot;
+    ctl->steps += 1;
+    __threadfence();
+    ctl->ctas_done = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Counting kernel: the canonical algorithmic window-compare tally (per candidate, sequences in
+// input order, windows left to right up to the first match, W for a sequence without one, and
+// nothing after it).
+
+__global__ void __launch_bounds__(256) count_kernel(const JobDesc* __restrict__ job,
+                                                    unsigned long long* total) {
+  const JobDesc jd = *job;
+  unsigned long long local = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = jd.lo + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < jd.hi;
+       k += stride) {
+    uint32_t E, O;
+    code_planes(k, E, O);
+    for (int s = 0; s < jd.n; ++s) {
+      const uint2* row = jd.planes + (size_t)s * jd.wstride;
+      int j = 0;
+      for (; j < jd.W; ++j) {
+        const uint2 w = __ldg(row + j);
+        if (__popc((E ^ w.x) | (O ^ w.y)) <= jd.d) break;
+      }
+      if (j < jd.W) {
+        local += (unsigned long long)(j + 1);
+      } else {
+        local += (unsigned long long)jd.W;
+        break;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(kFull, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
+}
+
+// Ball tables for ks = 1..kMaxKs: entry (v, r) = suffixes within distance r of v.
+__global__ void ball_kernel(uint64_t* table, int ks) {
+  const int nv = 1 << (2 * ks);
+  const int nw = mask_words(ks);
+  const int entries = nv * (ks + 1) * nw;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < entries; e += gridDim.x * blockDim.x) {
+    const int w = e % nw;
+    const int r = (e / nw) % (ks + 1);
+    const int v = e / (nw * (ks + 1));
+    uint64_t word = 0;
+    for (int b = 0; b < 64; ++b) {
+      const int s = w * 64 + b;
+      if (s >= nv) break;
+      const uint32_t x = (uint32_t)(s ^ v);
+      const int dist = __popc((x | (x >> 1)) & 0x55555555u);
+      if (dist <= r) word |= 1ull << b;
+    }
+    table[e] = word;
+  }
+}
+
+template <int KIND, int P>
+cudaError_t step_launch_t(const JobDesc* d_jobs, JobState* d_states, int njobs, StepCtl* d_ctl,
+                          int grid, int block, size_t smem, cudaStream_t s) {
+  step_kernel<KIND, P><<<grid, block, smem, s>>>(d_jobs, d_states, njobs, d_ctl);
+  return cudaGetLastError();
+}
+
+template <int KIND, int P>
+const void* step_fn() {
+  return reinterpret_cast<const void*>(&step_kernel<KIND, P>);
+}
+
+const void* step_function(int kind, int p) {
+  if (kind == MOTIF_KERNEL_CAND) {
+    switch (p) {
+      case 1: return step_fn<MOTIF_KERNEL_CAND, 1>();
+      case 2: return step_fn<MOTIF_KERNEL_CAND, 2>();
+      case 4: return step_fn<MOTIF_KERNEL_CAND, 4>();
+    }
+  } else if (kind == MOTIF_KERNEL_GROUP) {
+    switch (p) {
+      case 1: return step_fn<MOTIF_KERNEL_GROUP, 1>();
+      case 2: return step_fn<MOTIF_KERNEL_GROUP, 2>();
+      case 3: return step_fn<MOTIF_KERNEL_GROUP, 3>();
+      case 4: return step_fn<MOTIF_KERNEL_GROUP, 4>();
+    }
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+bool step_variant_ok(int kind, int p) { return step_function(kind, p) != nullptr; }
+
+size_t step_smem_bytes(int kind, int p, int wstride) {
+  if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
+  size_t b = (size_t)kMaxStageSeqs * wstride * 10;
+  b += 16 - b % 16;
+  return b + (size_t)ball_table_words(p) * 8;
+}
+
+cudaError_t step_kernel_attrs(int kind, int p, size_t smem) {
+  const void* f = step_function(kind, p);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int step_max_ctas_per_sm(int kind, int p, int block, size_t smem) {
+  const void* f = step_function(kind, p);
+  int n = 0;
+  if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+cudaError_t launch_step(int kind, int p, const JobDesc* d_jobs, JobState* d_states, int njobs,
+                        StepCtl* d_ctl, int grid, int block, size_t smem, cudaStream_t s) {
+  if (kind == MOTIF_KERNEL_CAND) {
+    switch (p) {
+      case 1: return step_launch_t<MOTIF_KERNEL_CAND, 1>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+      case 2: return step_launch_t<MOTIF_KERNEL_CAND, 2>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+      case 4: return step_launch_t<MOTIF_KERNEL_CAND, 4>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+    }
+  } else if (kind == MOTIF_KERNEL_GROUP) {
+    switch (p) {
+      case 1: return step_launch_t<MOTIF_KERNEL_GROUP, 1>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+      case 2: return step_launch_t<MOTIF_KERNEL_GROUP, 2>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+      case 3: return step_launch_t<MOTIF_KERNEL_GROUP, 3>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+      case 4: return step_launch_t<MOTIF_KERNEL_GROUP, 4>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
+                         cudaStream_t s) {
+  count_kernel<<<grid, block, 0, s>>>(d_job, d_total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s) {
+  const int entries = ball_table_words(ks);
+  ball_kernel<<<(entries + 255) / 256, 256, 0, s>>>(table, ks);
+  return cudaGetLastError();
+}
+
+}  // namespace motif

@@ -1,0 +1,541 @@
+// Serving: continuous batching of motif-search jobs.
+//
+// Clients submit loaded plans; a scheduler thread owns one device job table.  Between device
+// steps it admits queued jobs (first come, first served) while table slots and the device
+// memory budget allow, launches one step of the multi-job step kernel (every active job advances
+// by up to a bounded number of tiles, so new arrivals never wait behind a long job), reads back
+// the job states, and retires finished jobs: their codes are sorted/de-duplicated on the device,
+// copied to the host and handed to motif_poll.  A job's result does not depend on which other
+// jobs shared its steps: each job only reads its own windows and writes its own queues/output.
+#include <string.h>
+
+#include <algorithm>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "plan.h"
+
+using namespace motif;
+
+namespace motif_serve {
+
+constexpr uint64_t kServeChunkGroups = 1ull << 20;
+
+struct Job {
+  int64_t id = 0;
+  int n = 0, t = 0, l = 0, d = 0, W = 0, wstride = 0;
+  int kind = MOTIF_KERNEL_GROUP, pv = 4, span0 = 2, sms = 0;
+  size_t smem = 0;
+  uint64_t lo = 0, hi = 0, unit_lo = 0, unit_hi = 0, chunk_units = 0, nchunks = 0, rest = 0;
+  uint2* planes = nullptr;
+  uint64_t* codes = nullptr;
+  size_t win_bytes = 0;
+  uint32_t* qidx[2] = {nullptr, nullptr};
+  uint64_t* qmask[2] = {nullptr, nullptr};
+  uint64_t qcap = 0;
+  int words = 0;
+  uint64_t* out = nullptr;
+  int64_t out_cap = 0;
+  void* sort = nullptr;
+  size_t sort_bytes = 0;
+  int64_t footprint = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0, gpu_ms = 0;
+  int status = MOTIF_OK;
+  bool done = false;
+  std::vector<uint64_t> result;
+};
+
+struct Server {
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::thread th;
+  bool running = false, stopping = false;
+  motif_server_opts o{};
+  int device = 0, sms = 0;
+  cudaStream_t stream = nullptr;
+  std::deque<Job*> queue;
+  std::vector<Job*> active;       // table order = admission order
+  std::map<int64_t, Job*> jobs;   // every job not yet released by motif_poll
+  int64_t next_id = 1;
+  int64_t budget_used = 0;
+  JobDesc* d_jobs = nullptr;
+  JobState* d_states = nullptr;
+  StepCtl* d_ctl = nullptr;
+  int kind = -1, pv = -1, grid = 0, block = 256;
+  size_t smem = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+std::mutex g_life;  // guards g_srv creation / destruction
+Server* g_srv = nullptr;
+
+void* salloc(Server* S, size_t b) {
+  void* p = nullptr;
+  if (b == 0) return nullptr;
+  if (cudaMallocAsync(&p, b, S->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void sfree(Server* S, void* p) {
+  if (p) cudaFreeAsync(p, S->stream);
+}
+
+void release_buffers(Server* S, Job* j) {
+  for (int i = 0; i < 2; ++i) {
+    sfree(S, j->qidx[i]);
+    sfree(S, j->qmask[i]);
+    j->qidx[i] = nullptr;
+    j->qmask[i] = nullptr;
+  }
+  sfree(S, j->out);
+  sfree(S, j->sort);
+  sfree(S, j->planes);
+  sfree(S, j->codes);
+  j->out = nullptr;
+  j->sort = nullptr;
+  j->planes = nullptr;
+  j->codes = nullptr;
+}
+
+int64_t footprint_of(const Job* j) {
+  return (int64_t)(2 * j->qcap * (4 + 8 * (uint64_t)j->words) + 8 * (uint64_t)(1 << 16));
+}
+
+bool allocate_job(Server* S, Job* j) {
+  for (int i = 0; i < 2; ++i) {
+    j->qidx[i] = (uint32_t*)salloc(S, j->qcap * 4);
+    j->qmask[i] = (uint64_t*)salloc(S, j->qcap * 8 * (uint64_t)j->words);
+    if (!j->qidx[i] || !j->qmask[i]) return false;
+  }
+  j->out_cap = 1 << 16;
+  j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
+  return j->out != nullptr;
+}
+
+void fill_job_desc(const Job* j, JobDesc* jd) {
+  memset(jd, 0, sizeof(*jd));
+  jd->n = j->n; jd->t = j->t; jd->l = j->l; jd->d = j->d;
+  jd->W = j->W; jd->wstride = j->wstride;
+  jd->planes = j->planes; jd->codes = j->codes;
+  jd->kind = j->kind; jd->ks = j->pv; jd->cpt = 1; jd->span0 = j->span0;
+  jd->lo = j->lo; jd->hi = j->hi; jd->unit_lo = j->unit_lo; jd->unit_hi = j->unit_hi;
+  jd->chunk_units = j->chunk_units; jd->nchunks = j->nchunks; jd->rest_threshold = j->rest;
+  jd->qidx[0] = j->qidx[0]; jd->qidx[1] = j->qidx[1];
+  jd->qmask[0] = j->qmask[0]; jd->qmask[1] = j->qmask[1];
+  jd->qcap = j->qcap;
+  jd->out = j->out; jd->out_cap = (uint64_t)j->out_cap;
+}
+
+int max_active(const Server* S) { return S->o.max_active > 0 ? S->o.max_active : 64; }
+
+// (Re)builds the graph that replays one step launch over the table.
+int prepare_launch(Server* S, int kind, int pv, size_t smem) {
+  if (S->kind == kind && S->pv == pv && S->smem >= smem && (S->exec || !S->o.use_graph))
+    return MOTIF_OK;
+  smem = std::max(smem, S->smem);
+  if (step_kernel_attrs(kind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
+  const int per_sm = step_max_ctas_per_sm(kind, pv, S->block, smem);
+  if (per_sm <= 0) return MOTIF_ERR_ARG;
+  S->kind = kind;
+  S->pv = pv;
+  S->smem = smem;
+  S->grid = per_sm * S->sms;
+  if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
+  if (S->graph) { cudaGraphDestroy(S->graph); S->graph = nullptr; }
+  if (S->o.use_graph) {
+    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess)
+      e = launch_step(kind, pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl, S->grid,
+                      S->block, S->smem, S->stream);
+    cudaError_t e2 = cudaStreamEndCapture(S->stream, &S->graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->exec, S->graph, 0);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  return MOTIF_OK;
+}
+
+// Tile budget per warp and step: bounds the length of one step.
+unsigned tiles_per_warp(const Server* S) {
+  const unsigned warps = (unsigned)S->grid * (unsigned)(S->block / 32);
+  if (S->o.step_tiles > 0) return std::max(1u, (unsigned)S->o.step_tiles / std::max(1u, warps));
+  return 48;
+}
+
+// Uploads descriptors of the active jobs; states of jobs that moved down are copied, states of
+// newly admitted jobs zeroed, and unused slots marked done.
+int upload_table(Server* S, const std::vector<int>& old_slot) {
+  const int cap = max_active(S);
+  std::vector<JobDesc> descs(cap);
+  memset(descs.data(), 0, sizeof(JobDesc) * cap);
+  for (size_t i = 0; i < S->active.size(); ++i) fill_job_desc(S->active[i], &descs[i]);
+  cudaError_t e = cudaMemcpyAsync(S->d_jobs, descs.data(), sizeof(JobDesc) * cap,
+                                  cudaMemcpyHostToDevice, S->stream);
+  for (size_t i = 0; i < S->active.size() && e == cudaSuccess; ++i) {
+    if (old_slot[i] < 0)
+      e = cudaMemsetAsync(&S->d_states[i], 0, sizeof(JobState), S->stream);
+    else if (old_slot[i] != (int)i)
+      e = cudaMemcpyAsync(&S->d_states[i], &S->d_states[old_slot[i]], sizeof(JobState),
+                          cudaMemcpyDeviceToDevice, S->stream);
+  }
+  if (e == cudaSuccess && (int)S->active.size() < cap) {
+    std::vector<JobState> idle(cap - S->active.size());
+    memset(idle.data(), 0, sizeof(JobState) * idle.size());
+    for (auto& st : idle) st.done = 1;
+    e = cudaMemcpyAsync(&S->d_states[S->active.size()], idle.data(), sizeof(JobState) * idle.size(),
+                        cudaMemcpyHostToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);  // `idle` goes out of scope
+  }
+  return status_from_cuda(e);
+}
+
+// Sorts a finished job's codes and copies them to the host.
+int finish_job(Server* S, Job* j, int slot, unsigned long long found) {
+  if (found > 4096) {
+    const size_t need = sort_scratch_bytes(j->out_cap, S->sms);
+    j->sort = salloc(S, need);
+    j->sort_bytes = need;
+    if (!j->sort) return MOTIF_ERR_OOM;
+  }
+  cudaError_t e = launch_sort_unique(j->out, &S->d_states[slot].out_count, j->out_cap, 2 * j->l,
+                                     j->sort, S->sms, (long long)found, S->stream);
+  unsigned long long fc = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&fc, &S->d_states[slot].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
+                        S->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  if (e == cudaSuccess) {
+    j->result.resize(fc);
+    if (fc) e = cudaMemcpyAsync(j->result.data(), j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  }
+  return status_from_cuda(e);
+}
+
+void scheduler(Server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  bool dirty = true;
+  std::vector<int> old_slot;
+  for (;;) {
+    // Admission: first come, first served, while slots and the memory budget allow.
+    const int64_t budget = S->o.device_budget > 0 ? S->o.device_budget : (8ll << 30);
+    old_slot.assign(S->active.size(), 0);
+    for (size_t i = 0; i < S->active.size(); ++i) old_slot[i] = (int)i;
+    while (!S->queue.empty() && (int)S->active.size() < max_active(S)) {
+      Job* j = S->queue.front();
+      if (!S->active.empty() && (j->kind != S->kind || j->pv != S->pv)) break;
+      j->footprint = footprint_of(j);
+      if (!S->active.empty() && S->budget_used + j->footprint > budget) break;
+      if (!allocate_job(S, j)) {
+        release_buffers(S, j);
+        if (S->active.empty()) {  // cannot ever fit: fail the job
+          S->queue.pop_front();
+          j->status = MOTIF_ERR_OOM;
+          j->done = true;
+          j->t_done = now_ms();
+          S->cv_done.notify_all();
+          continue;
+        }
+        break;
+      }
+      S->queue.pop_front();
+      if (prepare_launch(S, j->kind, j->pv, j->smem) != MOTIF_OK) {
+        release_buffers(S, j);
+        j->status = MOTIF_ERR_CUDA;
+        j->done = true;
+        S->cv_done.notify_all();
+        continue;
+      }
+      j->t_admit = now_ms();
+      S->budget_used += j->footprint;
+      S->active.push_back(j);
+      old_slot.push_back(-1);
+      dirty = true;
+    }
+    if (S->active.empty()) {
+      if (S->stopping) break;
+      S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+      continue;
+    }
+    if (dirty) {
+      if (upload_table(S, old_slot) != MOTIF_OK) {
+        for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
+        S->active.clear();
+        S->cv_done.notify_all();
+        continue;
+      }
+      dirty = false;
+    }
+    const int nact = (int)S->active.size();
+    lk.unlock();
+    // One device step over the whole table.
+    StepCtl ctl{};
+    ctl.tiles_per_warp = tiles_per_warp(S);
+    cudaError_t e = cudaMemcpyAsync(S->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, S->stream);
+    cudaEventRecord(S->ev0, S->stream);
+    if (e == cudaSuccess) {
+      if (S->exec) e = cudaGraphLaunch(S->exec, S->stream);
+      else e = launch_step(S->kind, S->pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl,
+                           S->grid, S->block, S->smem, S->stream);
+    }
+    cudaEventRecord(S->ev1, S->stream);
+    std::vector<JobState> st(nact);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(st.data(), S->d_states, sizeof(JobState) * nact, cudaMemcpyDeviceToHost,
+                          S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    float step_ms = 0;
+    cudaEventElapsedTime(&step_ms, S->ev0, S->ev1);
+    lk.lock();
+    if (e != cudaSuccess) {
+      for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
+      S->active.clear();
+      S->cv_done.notify_all();
+      continue;
+    }
+    // Retire finished jobs (keeping table order for the rest).
+    std::vector<Job*> keep;
+    std::vector<int> moved;
+    for (int i = 0; i < nact; ++i) {
+      Job* j = S->active[i];
+      j->gpu_ms += step_ms;
+      if (!st[i].done) { keep.push_back(j); moved.push_back(i); continue; }
+      const unsigned long long found = st[i].out_count;
+      if (found > (unsigned long long)j->out_cap) {
+        // Output overflow: grow the buffer and restart the job in place.
+        sfree(S, j->out);
+        j->out_cap = (int64_t)found;
+        j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
+        if (!j->out) { j->status = MOTIF_ERR_OOM; }
+        else {
+          cudaMemsetAsync(&S->d_states[i], 0, sizeof(JobState), S->stream);
+          keep.push_back(j);
+          moved.push_back(i);
+          dirty = true;  // descriptor changed
+          continue;
+        }
+      } else {
+        j->status = finish_job(S, j, i, found);
+      }
+      j->t_done = now_ms();
+      j->done = true;
+      S->budget_used -= j->footprint;
+      release_buffers(S, j);
+      dirty = true;
+    }
+    if (dirty) {
+      S->active = keep;
+      old_slot = moved;
+      // States move down to their new slots before the next step (upload_table at loop top).
+      if (upload_table(S, old_slot) != MOTIF_OK) {
+        for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
+        S->active.clear();
+      }
+      dirty = false;
+      S->cv_done.notify_all();
+    }
+  }
+  // Shutdown: fail whatever is still queued.
+  for (Job* j : S->queue) {
+    j->status = MOTIF_ERR_STATE;
+    j->done = true;
+  }
+  S->queue.clear();
+  S->cv_done.notify_all();
+}
+
+int start_locked(const motif_server_opts* opts) {
+  if (g_srv) return MOTIF_ERR_STATE;
+  Server* S = new Server();
+  if (opts) S->o = *opts;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&S->device) != cudaSuccess ||
+      cudaGetDeviceProperties(&prop, S->device) != cudaSuccess) {
+    delete S;
+    return MOTIF_ERR_CUDA;
+  }
+  S->sms = prop.multiProcessorCount;
+  const int cap = max_active(S);
+  if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&S->d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
+      cudaMalloc(&S->d_states, sizeof(JobState) * cap) != cudaSuccess ||
+      cudaMalloc(&S->d_ctl, sizeof(StepCtl)) != cudaSuccess ||
+      cudaEventCreate(&S->ev0) != cudaSuccess || cudaEventCreate(&S->ev1) != cudaSuccess) {
+    delete S;
+    return MOTIF_ERR_CUDA;
+  }
+  S->running = true;
+  g_srv = S;
+  S->th = std::thread(scheduler, S);
+  return MOTIF_OK;
+}
+
+}  // namespace motif_serve
+
+using namespace motif_serve;
+
+extern "C" int motif_server_start(const motif_server_opts* opts) {
+  std::lock_guard<std::mutex> g(g_life);
+  return start_locked(opts);
+}
+
+extern "C" int motif_server_stop(void) {
+  Server* S;
+  {
+    std::lock_guard<std::mutex> g(g_life);
+    S = g_srv;
+    if (!S) return MOTIF_ERR_STATE;
+    g_srv = nullptr;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stopping = true;
+  }
+  S->cv_work.notify_all();
+  S->th.join();
+  cudaStreamSynchronize(S->stream);
+  for (auto& kv : S->jobs) {
+    release_buffers(S, kv.second);
+    delete kv.second;
+  }
+  cudaStreamSynchronize(S->stream);
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->graph) cudaGraphDestroy(S->graph);
+  cudaFree(S->d_jobs);
+  cudaFree(S->d_states);
+  cudaFree(S->d_ctl);
+  cudaEventDestroy(S->ev0);
+  cudaEventDestroy(S->ev1);
+  cudaStreamDestroy(S->stream);
+  delete S;
+  return MOTIF_OK;
+}
+
+extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
+  if (!p || !job_id) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  // Validate device-loaded characters before accepting the job.
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MOTIF_ERR_CUDA;
+  if (p->check_alpha) {
+    int err = 0;
+    if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return MOTIF_ERR_CUDA;
+    p->check_alpha = false;
+    if (err) { p->loaded = false; return MOTIF_ERR_ALPHABET; }
+  }
+  Server* S;
+  {
+    std::lock_guard<std::mutex> lg(g_life);
+    if (!g_srv) {
+      int rc = start_locked(nullptr);
+      if (rc) return rc;
+    }
+    S = g_srv;
+  }
+  if (S->device != p->device) return MOTIF_ERR_ARG;
+  Job* j = new Job();
+  j->t_submit = now_ms();
+  j->n = p->n; j->t = p->t; j->l = p->l; j->d = p->d; j->W = p->W; j->wstride = p->wstride;
+  j->sms = S->sms;
+  j->kind = MOTIF_KERNEL_GROUP;
+  j->pv = std::min(kMaxKs, p->l);
+  j->span0 = j->pv >= 3 ? 2 : 1;
+  j->smem = step_smem_bytes(j->kind, j->pv, std::max(j->wstride, kWinAlign));
+  j->lo = p->lo; j->hi = p->hi;
+  const int shift = 2 * j->pv;
+  j->unit_lo = j->lo >> shift;
+  j->unit_hi = j->hi > j->lo ? ((j->hi - 1) >> shift) + 1 : j->unit_lo;
+  const uint64_t units = j->unit_hi - j->unit_lo;
+  j->chunk_units = std::max<uint64_t>(1, std::min(units, kServeChunkGroups));
+  j->nchunks = units == 0 || j->W <= 0 ? 0 : (units + j->chunk_units - 1) / j->chunk_units;
+  j->qcap = j->chunk_units;
+  j->words = mask_words(j->pv);
+  j->rest = (uint64_t)8 * 32 * S->sms;
+  if (j->nchunks > 0) {
+    if (!ball_table(S->device, j->pv, S->stream)) { delete j; return MOTIF_ERR_CUDA; }
+    // Private copies of the packed windows, made on the server stream (which every later use of
+    // them is ordered after); the plan's stream waits for the copies, so the plan may be reused
+    // or destroyed as soon as this returns.
+    j->win_bytes = (size_t)j->n * j->wstride * 8;
+    j->planes = (uint2*)salloc(S, j->win_bytes);
+    j->codes = (uint64_t*)salloc(S, j->win_bytes);
+    cudaEvent_t copied = nullptr;
+    cudaError_t e = (j->planes && j->codes) ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(j->planes, p->d_planes, j->win_bytes, cudaMemcpyDeviceToDevice, S->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(j->codes, p->d_codes, j->win_bytes, cudaMemcpyDeviceToDevice, S->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(copied, S->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, copied, 0);
+    if (copied) cudaEventDestroy(copied);
+    if (e != cudaSuccess) {
+      release_buffers(S, j);
+      delete j;
+      return status_from_cuda(e);
+    }
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int max_q = S->o.max_queued > 0 ? S->o.max_queued : 4096;
+  if ((int)S->queue.size() >= max_q) {
+    release_buffers(S, j);
+    delete j;
+    return MOTIF_ERR_BUSY;
+  }
+  j->id = S->next_id++;
+  S->jobs[j->id] = j;
+  if (j->nchunks == 0) {  // no windows or empty range: nothing survives
+    j->done = true;
+    j->t_done = now_ms();
+  } else {
+    S->queue.push_back(j);
+    S->cv_work.notify_all();
+  }
+  *job_id = j->id;
+  return MOTIF_OK;
+}
+
+extern "C" int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity,
+                          int64_t* out_count, int32_t timeout_ms, motif_stats_t* stats) {
+  if (!out_count || capacity < 0 || (capacity > 0 && !out_codes)) return MOTIF_ERR_ARG;
+  Server* S;
+  {
+    std::lock_guard<std::mutex> g(g_life);
+    S = g_srv;
+  }
+  if (!S) return MOTIF_ERR_NOTFOUND;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(job_id);
+  if (it == S->jobs.end()) return MOTIF_ERR_NOTFOUND;
+  Job* j = it->second;
+  if (!j->done && timeout_ms > 0)
+    S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return j->done; });
+  if (!j->done) return MOTIF_PENDING;
+  *out_count = (int64_t)j->result.size();
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->candidates = j->hi - j->lo;
+    stats->survivors = j->result.size();
+    stats->queue_ms = j->t_admit > 0 ? j->t_admit - j->t_submit : 0;
+    stats->total_ms = j->t_done - j->t_submit;
+    stats->search_ms = j->gpu_ms;
+    stats->device_bytes = j->footprint;
+    stats->kernel = j->kind;
+  }
+  if (j->status == MOTIF_OK && (int64_t)j->result.size() > capacity) return MOTIF_ERR_CAPACITY;
+  if (!j->result.empty()) memcpy(out_codes, j->result.data(), j->result.size() * 8);
+  const int st = j->status;
+  S->jobs.erase(it);
+  delete j;  // the scheduler released its device buffers when it retired the job
+  return st;
+}

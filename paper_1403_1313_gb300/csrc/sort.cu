@@ -1,0 +1,311 @@
+// K2: sort and de-duplicate the accepted codes.
+//
+// The search appends accepted codes in whatever order warps finish.  The result is returned
+// ascending (which, with the code layout, is lexicographic order of the l-mers) and free of
+// duplicates.  Every kernel here reads the element count from device memory, so the whole
+// sequence can be enqueued without the host knowing how many codes were accepted:
+//   - up to kSmallMax codes: one CTA sorts them in shared memory (bitonic network) and drops
+//     repeats;
+//   - above that: a stable least-significant-digit radix sort with 8-bit digits (per-CTA
+//     histograms, one global digit-major scan, stable scatter ranked with warp match masks),
+//     then a keep-flag compaction of repeats.
+// Each path returns at once when the count belongs to the other path (or exceeds `cap`).
+#include "motif_internal.h"
+
+namespace motif {
+namespace {
+
+constexpr int kSmallMax = 4096;
+constexpr int kSmallThreads = 1024;
+constexpr int kRadixThreads = 256;
+constexpr int kRadixBits = 8;
+constexpr int kDigits = 1 << kRadixBits;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long read_count(const unsigned long long* c) {
+  return *reinterpret_cast<const volatile unsigned long long*>(c);
+}
+
+// ---- small path ----------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kSmallThreads) small_sort_kernel(uint64_t* codes,
+                                                                   unsigned long long* count,
+                                                                   long long cap) {
+  __shared__ uint64_t a[kSmallMax];
+  __shared__ unsigned warp_tot[kSmallThreads / 32];
+  const unsigned long long n = read_count(count);
+  if (n <= 1 || n > (unsigned long long)kSmallMax || n > (unsigned long long)cap) return;
+  int size = 2;
+  while ((unsigned long long)size < n) size <<= 1;
+  for (int i = threadIdx.x; i < size; i += blockDim.x) a[i] = (unsigned long long)i < n ? codes[i] : ~0ull;
+  __syncthreads();
+  // Bitonic sorting network over `size` (a power of two) elements.
+  for (int k = 2; k <= size; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        const int p = i ^ j;
+        if (p > i) {
+          const bool up = (i & k) == 0;
+          const uint64_t x = a[i], y = a[p];
+          if ((x > y) == up) { a[i] = y; a[p] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // Keep the first of each run of equal codes: each thread owns kSmallMax/kSmallThreads slots.
+  const int per = kSmallMax / kSmallThreads;
+  const int first = threadIdx.x * per;
+  unsigned keep = 0;
+  for (int q = 0; q < per; ++q) {
+    const int i = first + q;
+    if ((unsigned long long)i < n && (i == 0 || a[i] != a[i - 1])) keep |= 1u << q;
+  }
+  const unsigned mine = __popc(keep);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  unsigned before = 0, total = 0;
+  for (int w = 0; w < kSmallThreads / 32; ++w) {
+    if (w < warp) before += warp_tot[w];
+    total += warp_tot[w];
+  }
+  unsigned pos = before + incl - mine;
+  for (int q = 0; q < per; ++q)
+    if (keep & (1u << q)) codes[pos++] = a[first + q];
+  __syncthreads();
+  if (threadIdx.x == 0) *count = total;
+}
+
+// ---- large path: LSD radix sort --------------------------------------------------------------
+
+__device__ __forceinline__ bool large_active(unsigned long long n, long long cap) {
+  return n > (unsigned long long)kSmallMax && n <= (unsigned long long)cap;
+}
+
+__device__ __forceinline__ void segment(unsigned long long n, unsigned long long& b,
+                                        unsigned long long& e) {
+  const unsigned long long per = (n + gridDim.x - 1) / gridDim.x;
+  b = per * blockIdx.x;
+  e = b + per;
+  if (b > n) b = n;
+  if (e > n) e = n;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(
+    const uint64_t* __restrict__ keys, const unsigned long long* count, long long cap, int shift,
+    unsigned* __restrict__ hist) {
+  __shared__ unsigned h[kDigits];
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  for (int i = threadIdx.x; i < kDigits; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  unsigned long long b, e;
+  segment(n, b, e);
+  for (unsigned long long i = b + threadIdx.x; i < e; i += blockDim.x)
+    atomicAdd(&h[(keys[i] >> shift) & (kDigits - 1)], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kDigits; i += blockDim.x) hist[(size_t)i * gridDim.x + blockIdx.x] = h[i];
+}
+
+// Exclusive scan of `len` counters in place by one CTA of kRadixThreads threads.
+__global__ void __launch_bounds__(kRadixThreads) scan_kernel(unsigned* __restrict__ v, int len,
+                                                             const unsigned long long* count,
+                                                             long long cap, int need_large) {
+  __shared__ unsigned warp_tot[kRadixThreads / 32];
+  __shared__ unsigned carry;
+  const unsigned long long n = read_count(count);
+  if (need_large && !large_active(n, cap)) return;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < len; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const unsigned x = i < len ? v[i] : 0;
+    unsigned incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int w = 0; w < kRadixThreads / 32; ++w) {
+      if (w < warp) before += warp_tot[w];
+      total += warp_tot[w];
+    }
+    if (i < len) v[i] = carry + before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+    const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, const unsigned long long* count,
+    long long cap, int shift, const unsigned* __restrict__ offsets) {
+  constexpr int kWarps = kRadixThreads / 32;
+  __shared__ unsigned base[kDigits];
+  __shared__ unsigned warp_cnt[kWarps][kDigits];
+  __shared__ unsigned chunk_tot[kDigits];
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  base[tid] = offsets[(size_t)tid * gridDim.x + blockIdx.x];  // kRadixThreads == kDigits
+  unsigned long long b, e;
+  segment(n, b, e);
+  const unsigned lt_mask = (1u << lane) - 1;
+  for (unsigned long long c = b; c < e; c += kRadixThreads) {
+    for (int w = 0; w < kWarps; ++w) warp_cnt[w][tid] = 0;
+    __syncthreads();
+    const unsigned long long i = c + tid;
+    const bool valid = i < e;
+    const uint64_t key = valid ? src[i] : 0;
+    const unsigned digit = valid ? (unsigned)((key >> shift) & (kDigits - 1)) : kDigits;
+    const unsigned peers = __match_any_sync(kFull, digit);
+    const unsigned rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) warp_cnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    {  // exclusive prefix over warps for digit `tid`
+      unsigned acc = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const unsigned x = warp_cnt[w][tid];
+        warp_cnt[w][tid] = acc;
+        acc += x;
+      }
+      chunk_tot[tid] = acc;
+    }
+    __syncthreads();
+    if (valid) dst[base[digit] + warp_cnt[warp][digit] + rank] = key;
+    __syncthreads();
+    base[tid] += chunk_tot[tid];
+    __syncthreads();
+  }
+}
+
+// Keep flags: per-CTA counts of first-of-run elements.
+__global__ void __launch_bounds__(kRadixThreads) unique_count_kernel(
+    const uint64_t* __restrict__ keys, const unsigned long long* count, long long cap,
+    unsigned* __restrict__ per_cta) {
+  __shared__ unsigned tot;
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  unsigned long long b, e;
+  segment(n, b, e);
+  unsigned mine = 0;
+  for (unsigned long long i = b + threadIdx.x; i < e; i += blockDim.x)
+    mine += (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+  atomicAdd(&tot, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) per_cta[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kRadixThreads) unique_write_kernel(
+    const uint64_t* __restrict__ keys, uint64_t* __restrict__ dst, const unsigned long long* count,
+    long long cap, const unsigned* __restrict__ offsets) {
+  __shared__ unsigned warp_tot[kRadixThreads / 32];
+  __shared__ unsigned run;
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  if (threadIdx.x == 0) run = offsets[blockIdx.x];
+  __syncthreads();
+  unsigned long long b, e;
+  segment(n, b, e);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (unsigned long long c = b; c < e; c += blockDim.x) {
+    const unsigned long long i = c + threadIdx.x;
+    const bool keep = i < e && (i == 0 || keys[i] != keys[i - 1]);
+    const unsigned bal = __ballot_sync(kFull, keep);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int w = 0; w < kRadixThreads / 32; ++w) {
+      if (w < warp) before += warp_tot[w];
+      total += warp_tot[w];
+    }
+    if (keep) dst[run + before + __popc(bal & ((1u << lane) - 1))] = keys[i];
+    __syncthreads();
+    if (threadIdx.x == 0) run += total;
+    __syncthreads();
+  }
+}
+
+// Copies the de-duplicated codes back and stores the new count.
+__global__ void unique_finish_kernel(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
+                                     unsigned long long* count, long long cap,
+                                     const unsigned* __restrict__ per_cta_scanned,
+                                     const unsigned* __restrict__ per_cta_raw, int ctas) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  const unsigned long long total =
+      (unsigned long long)per_cta_scanned[ctas - 1] + per_cta_raw[ctas - 1];
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+__global__ void store_count_kernel(unsigned long long* count, long long cap,
+                                   const unsigned* __restrict__ per_cta_scanned,
+                                   const unsigned* __restrict__ per_cta_raw, int ctas) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    *count = (unsigned long long)per_cta_scanned[ctas - 1] + per_cta_raw[ctas - 1];
+}
+
+int radix_ctas(int sms) { return sms > 0 ? 2 * sms : 256; }
+
+}  // namespace
+
+// Scratch layout: [keys: cap u64][hist: kDigits*ctas u32][per_cta raw: ctas][per_cta scan: ctas]
+size_t sort_scratch_bytes(int64_t cap, int sms) {
+  const int ctas = radix_ctas(sms);
+  size_t b = (size_t)(cap > 0 ? cap : 1) * 8;
+  b += (size_t)kDigits * ctas * 4 + 2 * (size_t)ctas * 4 + 64;
+  return b;
+}
+
+cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, int64_t cap,
+                               int key_bits, void* scratch, int sms, long long known_count,
+                               cudaStream_t s) {
+  const bool want_small = known_count < 0 || (known_count > 1 && known_count <= kSmallMax);
+  const bool want_large = known_count < 0 || (known_count > kSmallMax && known_count <= cap);
+  if (want_small) {
+    small_sort_kernel<<<1, kSmallThreads, 0, s>>>(d_codes, d_count, cap);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (!want_large || cap <= kSmallMax) return cudaSuccess;
+  const int ctas = radix_ctas(sms);
+  uint64_t* alt = reinterpret_cast<uint64_t*>(scratch);
+  unsigned* hist = reinterpret_cast<unsigned*>(alt + cap);
+  unsigned* raw = hist + (size_t)kDigits * ctas;
+  unsigned* scanned = raw + ctas;
+  uint64_t* a = d_codes;
+  uint64_t* b = alt;
+  const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * kRadixBits;
+    radix_hist_kernel<<<ctas, kRadixThreads, 0, s>>>(a, d_count, cap, shift, hist);
+    scan_kernel<<<1, kRadixThreads, 0, s>>>(hist, kDigits * ctas, d_count, cap, 1);
+    radix_scatter_kernel<<<ctas, kRadixThreads, 0, s>>>(a, b, d_count, cap, shift, hist);
+    uint64_t* tmp = a; a = b; b = tmp;
+  }
+  // Sorted keys are in `a`; compact first-of-run elements into `b`, then back to d_codes.
+  unique_count_kernel<<<ctas, kRadixThreads, 0, s>>>(a, d_count, cap, raw);
+  cudaMemcpyAsync(scanned, raw, sizeof(unsigned) * ctas, cudaMemcpyDeviceToDevice, s);
+  scan_kernel<<<1, kRadixThreads, 0, s>>>(scanned, ctas, d_count, cap, 1);
+  unique_write_kernel<<<ctas, kRadixThreads, 0, s>>>(a, b, d_count, cap, scanned);
+  unique_finish_kernel<<<ctas, kRadixThreads, 0, s>>>(b, d_codes, d_count, cap, scanned, raw, ctas);
+  store_count_kernel<<<1, 32, 0, s>>>(d_count, cap, scanned, raw, ctas);
+  return cudaGetLastError();
+}
+
+}  // namespace motif

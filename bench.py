@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the skip-BF (l,d) motif search on GB300.
+
+One step = the whole hot path over one synthetic workload: window extraction and packing (K0),
+the pass-structured search with survivor compaction (K1 steps) and sort/dedup (K2).  The
+default workload is the challenge-shaped (15,4) instance: n = 20 sequences of t = 600 bases,
+uniform ACGT, one FM-planted instance per sequence (seed 2), all 4^15 candidates.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value   = candidates/s over the whole job (all ranks), inputs resident in HBM, per-step CUDA
+          events on the plan's stream, L2 flushed (256 MiB write) before every step outside the
+          timed intervals.
+e2e     = the same metric through the blocking C-ABI call with host buffers (H2D of the
+          characters, D2H of the codes inside the timed region).
+roofline= the step kernel against its POPC issue bound (one POPC per canonical unit step).
+cpu_baseline / --impl reference = the CPU oracle (C, POSIX threads over all host cores, the
+          paper's index-range split) on a bounded sub-range of the same workload.
+Multi-GPU (torchrun): every rank searches its own independently seeded instance of the
+workload (weak scaling, no collective on the data path); max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "(15,4) candidates/s & window-compares/s vs INT/POPC roofline; serve p50/p99"
+CONFIGS = {  # name: (l, d, n, t, seed)
+    "l9d2": (9, 2, 20, 600, 1),
+    "l15d4": (15, 4, 20, 600, 2),
+    "l17d5": (17, 5, 20, 600, 3),
+}
+POPC_PER_SM_CLK = 16.0  # measured by the K4 probe (motif_probe_rate POPC) on GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="l15d4")
+    ap.add_argument("--kernel", choices=["auto", "group", "cand"], default="auto")
+    ap.add_argument("--suffix-bases", type=int, default=0)
+    ap.add_argument("--cands-per-thread", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(job, seconds: float, steps: int = 1):
+    """Times the oracle (all host cores, the paper's range split) on a bounded sub-range."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    l = job.l
+    lo = (4 ** l) // 3
+    probe = 1 << 12
+    t0 = time.perf_counter()
+    oracle.search(job.rows(), l, job.d, lo=lo, hi=lo + probe, threads=cores)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    size = int(min(4 ** l - lo, max(probe, rate * seconds / max(steps, 1))))
+    times = []
+    for s in range(steps):
+        a = lo + s * size
+        b = min(4 ** l, a + size)
+        t0 = time.perf_counter()
+        oracle.search(job.rows(), l, job.d, lo=a, hi=b, threads=cores)
+        times.append(time.perf_counter() - t0)
+    return size, times, cores, lo
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1403_1313_gb300 import fmgen
+    l, d, n, t, seed = CONFIGS[args.config]
+    job = fmgen.fm_job(n, t, l, d, seed)
+    # Warm-up steps, then K timed steps; each step is one bounded sub-range of the workload.
+    per_step = max(0.05, min(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+    size, times, cores, lo = cpu_baseline(job, per_step * (args.steps + args.warmup),
+                                          steps=args.steps + args.warmup)
+    timed = times[args.warmup:]
+    value = size * len(timed) / sum(timed)
+    sample = "candidates [%d, %d) of the (%d,%d) n=%d t=%d seed-%d workload, %d per step" % (
+        lo, lo + size * len(times), l, d, n, t, seed, size)
+    line = {
+        "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "l%dd%d_n%d_t%d_seed%d" % (l, d, n, t, seed), "l": l, "d": d,
+                   "n": n, "t": t, "seed": seed, "sample_candidates_per_step": size},
+        "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1403_1313_gb300 as m
+    from paper_1403_1313_gb300 import fmgen
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    l, d, n, t, seed = CONFIGS[args.config]
+    job = fmgen.fm_job(n, t, l, d, seed + rank * 1000)
+    workload = "l%dd%d_n%d_t%d_seed%d" % (l, d, n, t, seed)
+
+    stream = torch.cuda.Stream()
+    kw = {}
+    if args.kernel == "group":
+        kw["kernel"] = m.KERNEL_GROUP
+    elif args.kernel == "cand":
+        kw["kernel"] = m.KERNEL_CAND
+    if args.suffix_bases:
+        kw["suffix_bases"] = args.suffix_bases
+    if args.cands_per_thread:
+        kw["cands_per_thread"] = args.cands_per_thread
+    opts = m.torch_opts(stream=stream, **kw)
+    plan = m.motif_plan_create(n, t, l, d, opts)
+    cap = 1 << 16
+    with torch.cuda.stream(stream):
+        d_chars = torch.from_numpy(job.seqs.copy()).cuda()
+        d_out = torch.zeros(cap, dtype=torch.int64, device="cuda")
+        d_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        m.motif_load_seqs_device(plan, d_chars)
+        m.motif_search_device(plan, d_out, cap, d_cnt)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    stream.synchronize()
+    count = int(d_cnt.item())
+    codes = d_out[:max(count, 0)].cpu().numpy().astype(np.uint64)
+    assert count >= 1 and m.motif_encode(job.consensus) in set(codes.tolist()), "result check failed"
+    compares, unit_steps = m.motif_count_work(plan)
+    m.motif_stats(plan)  # resets the summed device times
+    st0 = m.motif_stats(plan)
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)  # let the sampler come up before the timed region
+    launches0 = m.motif_kernel_launches()
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            ev_s[k].record(stream)
+            step()
+            ev_e[k].record(stream)
+    stream.synchronize()
+    launches = m.motif_kernel_launches() - launches0
+    clocks = sampler.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e))
+    st = m.motif_stats(plan)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+
+    cands = 4 ** l
+    value = world * cands * args.steps / (t_ms / 1e3)
+    cps = world * compares * args.steps / (t_ms / 1e3)
+
+    # Roofline of the dominant kernel: the step kernel, whose launches are bracketed by the
+    # plan's events (search_ms_sum over the timed searches).
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    step_ms = st["search_ms_sum"] / max(st["searches"], 1)
+    sort_ms = st["sort_ms_sum"] / max(st["searches"], 1)
+    achieved = unit_steps / (step_ms / 1e3)
+    peak = POPC_PER_SM_CLK * sms * max_mhz * 1e6
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "G unit-steps/s (1 POPC each)", "frac": achieved / peak, "traffic": None,
+            "kernel": "step_kernel<%s>" % ("GROUP" if st["kernel"] == m.KERNEL_GROUP else "CAND"),
+            "peak_basis": "16 POPC/clk/SM (K4 probe) x %d SMs x %.0f MHz (max SM clock)" % (sms, max_mhz),
+            "step_kernel_ms": step_ms, "sort_ms": sort_ms,
+            "unit_steps_per_search": unit_steps}
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_observed_clock"] = achieved / (POPC_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
+
+    # End to end through the blocking C ABI with host buffers.
+    e2e = None
+    if rank == 0 or world > 1:
+        plan2 = m.motif_plan_create(n, t, l, d, m.torch_opts(stream=stream, **kw))
+        host_chars = np.ascontiguousarray(job.seqs)
+        m.motif_load_seqs(plan2, host_chars)
+        m.motif_search(plan2)
+        ne = max(3, args.e2e_steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            m.motif_load_seqs(plan2, host_chars)
+            got = m.motif_search(plan2)
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * cands * ne / dt, "unit": "candidates/s",
+               "h2d_bytes_per_step": int(n * t), "d2h_bytes_per_step": int(8 * got.size + 8)}
+        m.motif_plan_destroy(plan2)
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": workload, "l": l, "d": d, "n": n, "t": t, "seed": seed,
+                       "candidates": cands, "kernel": roof["kernel"],
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "weak: one independent instance per GPU" if world > 1 else "1 GPU"},
+            "window_compares_per_s": cps,
+            "algorithmic_compares_per_search": compares,
+            "survivors": count,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            size, times, cores, lo = cpu_baseline(job, args.cpu_seconds)
+            line["cpu_baseline"] = {
+                "value": size / times[0], "unit": "candidates/s", "cores": cores, "kind": "oracle",
+                "sample": "candidates [%d, %d) of %s (%.1f s wall, all %d cores)" % (
+                    lo, lo + size, workload, times[0], cores)}
+        print(json.dumps(line), flush=True)
+    m.motif_plan_destroy(plan)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

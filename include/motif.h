@@ -92,6 +92,9 @@ typedef struct {
   int32_t kernel;                /* kernel that ran (motif_kernel) */
   int32_t grid;                  /* CTAs launched */
   int32_t block;                 /* threads per CTA */
+  double search_ms_sum;          /* device time of the search kernels, summed over the */
+  double sort_ms_sum;            /* searches since the previous motif_stats call, and of */
+  int64_t searches;              /* sort/dedup; `searches` is how many were summed */
 } motif_stats_t;
 
 /* ---- plans ------------------------------------------------------------------------------ */
@@ -149,8 +152,22 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
  * windows of the first sequence with none, and no sequence after it.  Blocking. */
 int motif_count_compares(motif_plan p, uint64_t* out);
 
-/* Statistics of the last search / served job of the plan. */
+/* Runs the counting forms of the search over the plan's range (blocking).  *compares receives
+ * the canonical window-compare tally (as motif_count_compares).  *unit_steps receives the same
+ * tally for the plan's kernel formulation: for MOTIF_KERNEL_CAND it equals *compares; for
+ * MOTIF_KERNEL_GROUP it counts (group, window) prefix compares: per group of 4^k candidates
+ * sharing their first l-k bases, sequences in input order, windows left to right up to and
+ * including the first window after which every candidate of the group still alive has a
+ * window within d, W for a sequence that leaves none alive, and nothing after it.  Either
+ * pointer may be NULL. */
+int motif_count_work(motif_plan p, uint64_t* compares, uint64_t* unit_steps);
+
+/* Statistics of the plan: the last search / served job, plus device times summed over every
+ * search since the previous call (waits for the plan's stream). */
 int motif_stats(motif_plan p, motif_stats_t* s);
+
+/* Kernel launches the library has issued in this process, over all entry points. */
+uint64_t motif_kernel_launches(void);
 
 /* ---- batching: many uneven jobs in one persistent launch -------------------------------- */
 

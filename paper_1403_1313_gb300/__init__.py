@@ -24,7 +24,7 @@ __all__ = [
     "MotifError", "MotifLibraryError", "Plan", "motif_opts", "motif_stats_t",
     "motif_server_opts", "motif_opts_default", "motif_plan_create", "motif_plan_destroy",
     "motif_load_seqs", "motif_load_seqs_device", "motif_search", "motif_search_device",
-    "motif_count_compares", "motif_stats", "motif_batch_search", "motif_autotune",
+    "motif_count_compares", "motif_count_work", "motif_kernel_launches", "motif_stats", "motif_batch_search", "motif_autotune",
     "motif_tune_cache_save", "motif_tune_cache_load", "motif_server_start", "motif_server_stop",
     "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
@@ -66,7 +66,8 @@ class motif_stats_t(ctypes.Structure):
         ("sort_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
         ("queue_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64),
         ("smem_bytes", ctypes.c_int32), ("kernel", ctypes.c_int32), ("grid", ctypes.c_int32),
-        ("block", ctypes.c_int32),
+        ("block", ctypes.c_int32), ("search_ms_sum", ctypes.c_double),
+        ("sort_ms_sum", ctypes.c_double), ("searches", ctypes.c_int64),
     ]
 
 
@@ -119,6 +120,8 @@ def _load():
             "motif_search": (ctypes.c_int, [P, u64p, i64, i64p]),
             "motif_search_device": (ctypes.c_int, [P, P, i64, P]),
             "motif_count_compares": (ctypes.c_int, [P, u64p]),
+            "motif_count_work": (ctypes.c_int, [P, u64p, u64p]),
+            "motif_kernel_launches": (ctypes.c_uint64, []),
             "motif_stats": (ctypes.c_int, [P, ctypes.POINTER(motif_stats_t)]),
             "motif_batch_search": (ctypes.c_int, [i32, ctypes.POINTER(P), ctypes.POINTER(u64p), i64p, i64p, ctypes.POINTER(i32), i32]),
             "motif_autotune": (ctypes.c_int, [P, i32, ctypes.POINTER(motif_opts)]),
@@ -247,6 +250,17 @@ def motif_count_compares(plan: Plan) -> int:
     v = ctypes.c_uint64(0)
     _check(_load().motif_count_compares(plan, ctypes.byref(v)), "motif_count_compares")
     return int(v.value)
+
+
+def motif_count_work(plan: Plan) -> tuple[int, int]:
+    """(canonical window compares, canonical unit steps of the plan's kernel formulation)."""
+    c, u = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_load().motif_count_work(plan, ctypes.byref(c), ctypes.byref(u)), "motif_count_work")
+    return int(c.value), int(u.value)
+
+
+def motif_kernel_launches() -> int:
+    return int(_load().motif_kernel_launches())
 
 
 def _stats_dict(s: motif_stats_t) -> dict:

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "plan.h"
@@ -18,6 +19,43 @@ int status_from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return MOTIF_OK;
   if (e == cudaErrorMemoryAllocation) return MOTIF_ERR_OOM;
   return MOTIF_ERR_CUDA;
+}
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+cudaEvent_t* next_event_quad(motif_plan_s* p) {
+  if (p->evq_used * 4 + 4 > p->evq.size()) {
+    const size_t grow = std::max<size_t>(16, p->evq.size() / 4) * 4;
+    for (size_t i = 0; i < grow; ++i) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      p->evq.push_back(e);
+    }
+  }
+  return &p->evq[4 * p->evq_used++];
+}
+
+int fold_event_quads(motif_plan_s* p) {
+  if (p->evq_used == 0) return MOTIF_OK;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  for (size_t q = 0; q < p->evq_used; ++q) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, p->evq[4 * q], p->evq[4 * q + 1]);
+    cudaEventElapsedTime(&b, p->evq[4 * q + 2], p->evq[4 * q + 3]);
+    p->sum_search_ms += a;
+    p->sum_sort_ms += b;
+    p->sum_searches += 1;
+    p->stats.search_ms = a;
+    p->stats.sort_ms = b;
+  }
+  cudaGetLastError();
+  p->evq_used = 0;
+  return MOTIF_OK;
 }
 
 void* plan_alloc(motif_plan_s* p, size_t bytes) {
@@ -131,19 +169,9 @@ int plan_configure(motif_plan_s* p) {
   const uint64_t max_chunk = kind == MOTIF_KERNEL_GROUP ? (1ull << 22) : (1ull << 28);
   const uint64_t chunk = std::max<uint64_t>(1, std::min(units, max_chunk));
   const int words = kind == MOTIF_KERNEL_GROUP ? mask_words(pv) : 0;
-  if (chunk != p->qcap || words != p->qmask_words) {
-    free_queues(p);
-    for (int i = 0; i < 2; ++i) {
-      p->d_qidx[i] = (uint32_t*)plan_alloc(p, chunk * 4);
-      if (!p->d_qidx[i]) return MOTIF_ERR_OOM;
-      if (words) {
-        p->d_qmask[i] = (uint64_t*)plan_alloc(p, chunk * 8 * (size_t)words);
-        if (!p->d_qmask[i]) return MOTIF_ERR_OOM;
-      }
-    }
-    p->qcap = chunk;
-    p->qmask_words = words;
-  }
+  if (chunk != p->qcap || words != p->qmask_words) free_queues(p);  // re-made on first use
+  p->want_qcap = chunk;
+  p->want_qwords = words;
   p->kind = kind;
   p->p = pv;
   p->span0 = span0;
@@ -159,6 +187,27 @@ int plan_configure(motif_plan_s* p) {
   return MOTIF_OK;
 }
 
+int plan_ensure_buffers(motif_plan_s* p) {
+  if (!p->d_qidx[0]) {
+    for (int i = 0; i < 2; ++i) {
+      p->d_qidx[i] = (uint32_t*)plan_alloc(p, p->want_qcap * 4);
+      if (!p->d_qidx[i]) return MOTIF_ERR_OOM;
+      if (p->want_qwords) {
+        p->d_qmask[i] = (uint64_t*)plan_alloc(p, p->want_qcap * 8 * (size_t)p->want_qwords);
+        if (!p->d_qmask[i]) return MOTIF_ERR_OOM;
+      }
+    }
+    p->qcap = p->want_qcap;
+    p->qmask_words = p->want_qwords;
+  }
+  if (!p->d_out) {
+    p->d_out = (uint64_t*)plan_alloc(p, (size_t)(1 << 16) * 8);
+    if (!p->d_out) return MOTIF_ERR_OOM;
+    p->out_cap = 1 << 16;
+  }
+  return MOTIF_OK;
+}
+
 int run_steps(int kind, int pv, const JobDesc* d_jobs, JobState* d_states, int njobs,
               StepCtl* d_ctl, int grid, int block, size_t smem, int max_steps, bool poll,
               int timeout_ms, cudaStream_t s, int* steps_run) {
@@ -171,6 +220,7 @@ int run_steps(int kind, int pv, const JobDesc* d_jobs, JobState* d_states, int n
       cudaError_t e = launch_step(kind, pv, d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
       if (e != cudaSuccess) return status_from_cuda(e);
     }
+    note_launches(todo);
     launched += todo;
     if (!poll) break;
     unsigned active = 0;
@@ -242,6 +292,8 @@ int check_alphabet(motif_plan_s* p) {
 
 // Enqueues one search of the plan writing into (out, cap): descriptor, state reset, steps.
 int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll, int* steps) {
+  int rc = plan_ensure_buffers(p);
+  if (rc) return rc;
   JobDesc jd;
   fill_desc(p, &jd, out, cap);
   if (p->kind == MOTIF_KERNEL_GROUP && !jd.ball) return MOTIF_ERR_CUDA;
@@ -313,9 +365,6 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
   if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, p->device);
   if (e != cudaSuccess) { cudaGetLastError(); delete p; return MOTIF_ERR_CUDA; }
   p->sms = prop.multiProcessorCount;
-  for (auto& ev : p->ev) {
-    if (cudaEventCreate(&ev) != cudaSuccess) { motif_plan_destroy(p); return MOTIF_ERR_CUDA; }
-  }
   const size_t chars = (size_t)n * t;
   const size_t wins = (size_t)n * std::max(p->wstride, 0);
   p->d_chars = (char*)plan_alloc(p, chars);
@@ -334,7 +383,6 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
   }
   if (p->opts.kernel == MOTIF_KERNEL_AUTO) tune_lookup(p, &p->opts);
   rc = plan_configure(p);
-  if (rc == MOTIF_OK) rc = ensure_out(p, 1 << 16);
   if (rc) { motif_plan_destroy(p); return rc; }
   *out = p;
   return MOTIF_OK;
@@ -357,7 +405,7 @@ void motif_plan_destroy(motif_plan p) {
   plan_free(p, p->d_out, (size_t)p->out_cap * 8);
   plan_free(p, p->d_sort, p->sort_bytes);
   cudaStreamSynchronize(p->stream);
-  for (auto& ev : p->ev)
+  for (cudaEvent_t ev : p->evq)
     if (ev) cudaEventDestroy(ev);
   delete p;
 }
@@ -413,12 +461,16 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
     return MOTIF_OK;
   }
   unsigned long long found = 0;
+  cudaEvent_t* ev = next_event_quad(p);
+  if (!ev) return MOTIF_ERR_CUDA;
   for (;;) {
-    cudaEventRecord(p->ev[0], p->stream);
+    cudaEventRecord(ev[0], p->stream);
     int steps = 0;
+    rc = plan_ensure_buffers(p);
+    if (rc) return rc;
     rc = enqueue_search(p, p->d_out, (uint64_t)p->out_cap, true, &steps);
     if (rc) return rc;
-    cudaEventRecord(p->ev[1], p->stream);
+    cudaEventRecord(ev[1], p->stream);
     cudaError_t e = cudaMemcpyAsync(&found, &p->d_state->out_count, sizeof(found),
                                     cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -431,10 +483,10 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
     rc = ensure_sort(p, p->out_cap);
     if (rc) return rc;
   }
-  cudaEventRecord(p->ev[2], p->stream);
+  cudaEventRecord(ev[2], p->stream);
   cudaError_t e = launch_sort_unique(p->d_out, &p->d_state->out_count, p->out_cap, 2 * p->l,
                                      p->d_sort, p->sms, (long long)found, p->stream);
-  cudaEventRecord(p->ev[3], p->stream);
+  cudaEventRecord(ev[3], p->stream);
   unsigned long long final_count = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&final_count, &p->d_state->out_count, sizeof(final_count),
@@ -442,11 +494,8 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return status_from_cuda(e);
   *out_count = (int64_t)final_count;
-  float ms = 0;
-  cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]);
-  p->stats.search_ms = ms;
-  cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]);
-  p->stats.sort_ms = ms;
+  rc = fold_event_quads(p);
+  if (rc) return rc;
   p->stats.survivors = final_count;
   if ((int64_t)final_count > capacity) {
     p->stats.total_ms = now_ms() - t0;
@@ -467,6 +516,11 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
   if (!p->loaded) return MOTIF_ERR_STATE;
   DeviceGuard g(p->device);
   int rc = MOTIF_OK;
+  p->stats.candidates = p->hi - p->lo;
+  p->stats.kernel = p->kind;
+  p->stats.grid = p->grid;
+  p->stats.block = p->block;
+  p->stats.smem_bytes = (int32_t)p->smem;
   if (capacity > 4096) {
     rc = ensure_sort(p, capacity);
     if (rc) return rc;
@@ -475,12 +529,19 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
     cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
   } else {
+    cudaEvent_t* ev = next_event_quad(p);
+    if (!ev) return MOTIF_ERR_CUDA;
+    cudaEventRecord(ev[0], p->stream);
     rc = enqueue_search(p, d_out_codes, (uint64_t)capacity, false, nullptr);
     if (rc) return rc;
+    cudaEventRecord(ev[1], p->stream);
+    cudaEventRecord(ev[2], p->stream);
     cudaError_t e = launch_sort_unique(d_out_codes, &p->d_state->out_count, capacity, 2 * p->l,
                                        p->d_sort, p->sms, -1, p->stream);
+    cudaEventRecord(ev[3], p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
   }
+  note_launches(1);
   finalize_count_kernel<<<1, 32, 0, p->stream>>>(p->d_err, &p->d_state->out_count, d_out_count);
   return status_from_cuda(cudaGetLastError());
 }
@@ -508,12 +569,48 @@ int motif_count_compares(motif_plan p, uint64_t* out) {
   return MOTIF_OK;
 }
 
-int motif_stats(motif_plan p, motif_stats_t* s) {
-  if (!p || !s) return MOTIF_ERR_ARG;
-  *s = p->stats;
-  s->device_bytes = p->device_bytes;
+int motif_count_work(motif_plan p, uint64_t* compares, uint64_t* unit_steps) {
+  if (!p) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  uint64_t c = 0;
+  int rc = motif_count_compares(p, &c);
+  if (rc) return rc;
+  if (compares) *compares = c;
+  if (!unit_steps) return MOTIF_OK;
+  if (p->kind == MOTIF_KERNEL_CAND || p->W <= 0 || p->hi <= p->lo) {
+    *unit_steps = p->kind == MOTIF_KERNEL_CAND ? c : 0;
+    return MOTIF_OK;
+  }
+  JobDesc jd;
+  fill_desc(p, &jd, p->d_out, p->out_cap);
+  unsigned long long total = 0;
+  cudaError_t e = cudaMemcpyAsync(p->d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_total, 0, sizeof(unsigned long long), p->stream);
+  if (e == cudaSuccess) e = launch_count_group(p->d_job, p->p, p->d_total, p->sms * 8, 256, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, p->d_total, sizeof(total), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  *unit_steps = total;
   return MOTIF_OK;
 }
+
+int motif_stats(motif_plan p, motif_stats_t* s) {
+  if (!p || !s) return MOTIF_ERR_ARG;
+  DeviceGuard g(p->device);
+  int rc = fold_event_quads(p);
+  *s = p->stats;
+  s->device_bytes = p->device_bytes;
+  s->search_ms_sum = p->sum_search_ms;
+  s->sort_ms_sum = p->sum_sort_ms;
+  s->searches = p->sum_searches;
+  p->sum_search_ms = p->sum_sort_ms = 0;
+  p->sum_searches = 0;
+  return rc;
+}
+
+uint64_t motif_kernel_launches(void) { return launches_total(); }
 
 int motif_shard_range(uint64_t total, int32_t rank, int32_t world, const double* weights,
                       uint64_t* lo, uint64_t* hi) {

@@ -75,6 +75,7 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
   int launched = 0, rc = MOTIF_OK;
   while (e == cudaSuccess && launched < max_steps) {
     e = cudaGraphLaunch(exec, s);
+    note_launches(group);
     launched += group;
     unsigned active = 0;
     if (e == cudaSuccess)
@@ -129,6 +130,10 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
   for (int j = 0; j < njobs; ++j) {
     motif_plan_s* p = plans[j];
     if (statuses[j] != MOTIF_OK || p->W <= 0 || p->hi <= p->lo || p->nchunks == 0) continue;
+    if (plan_ensure_buffers(p) != MOTIF_OK || cudaStreamSynchronize(p->stream) != cudaSuccess) {
+      statuses[j] = MOTIF_ERR_OOM;
+      continue;
+    }
     groups[{p->kind, p->p}].push_back(j);
   }
   std::vector<char> redo(njobs, 0);

@@ -65,6 +65,10 @@ __host__ __device__ inline int ball_table_words(int ks) {
   return (1 << (2 * ks)) * (ks + 1) * mask_words(ks);
 }
 
+// Process-wide count of kernel launches issued by the library.
+void note_launches(int n);
+unsigned long long launches_total();
+
 // ---- launchers (stream-ordered, no host synchronisation) ---------------------------------
 cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l, int wstride,
                         uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s);
@@ -80,6 +84,9 @@ cudaError_t launch_step(int kind, int p, const JobDesc* d_jobs, JobState* d_stat
                         StepCtl* d_ctl, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
                          cudaStream_t s);
+// Canonical (group, window) prefix-compare tally of the GROUP formulation with ks suffix bases.
+cudaError_t launch_count_group(const JobDesc* d_job, int ks, unsigned long long* d_total, int grid,
+                               int block, cudaStream_t s);
 // Sorts d_codes[0 .. *d_count) ascending and removes repeats in place (count updated) when
 // *d_count <= cap.  known_count >= 0 lets the host skip the path that cannot apply.
 size_t sort_scratch_bytes(int64_t cap, int sms);

@@ -68,12 +68,14 @@ cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
   validate_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, d_err);
+  note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || t < l) return e;
   const int64_t wins = (int64_t)n * wstride;
   grid = (int)((wins + block - 1) / block);
   if (grid > 4096) grid = 4096;
   pack_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, l, wstride, planes, codes);
+  note_launches(1);
   return cudaGetLastError();
 }
 

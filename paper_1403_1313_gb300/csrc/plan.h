@@ -36,6 +36,8 @@ struct motif_plan_s {
   uint64_t* d_qmask[2] = {nullptr, nullptr};
   uint64_t qcap = 0;
   int qmask_words = 0;
+  uint64_t want_qcap = 0;    // queue size of the current configuration (allocated lazily)
+  int want_qwords = 0;
   uint64_t* d_out = nullptr;
   int64_t out_cap = 0;
   void* d_sort = nullptr;
@@ -49,7 +51,12 @@ struct motif_plan_s {
   bool loaded = false;
   bool check_alpha = false;  // device-loaded characters not yet validated on the host
   motif_stats_t stats{};
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // Four events per search (steps begin/end, sort begin/end), folded into the statistics by
+  // motif_stats; `evq_used` quads are pending.
+  std::vector<cudaEvent_t> evq;
+  size_t evq_used = 0;
+  double sum_search_ms = 0, sum_sort_ms = 0;
+  int64_t sum_searches = 0;
 };
 
 namespace motif {
@@ -64,8 +71,10 @@ const uint64_t* ball_table(int device, int ks, cudaStream_t s);
 // Fills the device descriptor of the plan's job (host copy).
 void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_cap);
 
-// (Re)applies the kernel configuration: variant, grid, shared memory, chunking and queues.
+// (Re)applies the kernel configuration: variant, grid, shared memory and chunking.
 int plan_configure(motif_plan_s* p);
+// Allocates the survivor queues and the default output buffer on first use.
+int plan_ensure_buffers(motif_plan_s* p);
 
 // Launches steps for a job table until no job is active (polling every `group` steps), or
 // blindly `max_steps` steps when poll == false.  Returns a motif_status.
@@ -74,6 +83,11 @@ int run_steps(int kind, int pv, const JobDesc* d_jobs, JobState* d_states, int n
               int timeout_ms, cudaStream_t s, int* steps_run);
 
 int status_from_cuda(cudaError_t e);
+
+// Next free event quad of the plan (grown on demand); nullptr on failure.
+cudaEvent_t* next_event_quad(motif_plan_s* p);
+// Waits for the plan's stream and folds pending event quads into the statistics.
+int fold_event_quads(motif_plan_s* p);
 
 // Copies a cached tuning choice for the plan's shape into *o; false when none is cached.
 bool tune_lookup(const motif_plan_s* p, motif_opts* o);

@@ -131,6 +131,7 @@ cudaError_t launch_probe(int sms, uint32_t seed, int iters, long long* cyc, uint
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pad);
   if (e != cudaSuccess) return e;
   probe_kernel<KIND><<<sms, kProbeThreads, smem_pad>>>(seed, iters, cyc, sink);
+  motif::note_launches(1);
   return cudaGetLastError();
 }
 

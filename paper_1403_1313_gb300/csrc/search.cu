@@ -564,6 +564,50 @@ __global__ void __launch_bounds__(256) count_kernel(const JobDesc* __restrict__ 
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
 }
 
+// Canonical (group, window) prefix-compare tally of the GROUP formulation: per group,
+// sequences in input order, windows left to right up to and including the first window after
+// which every live candidate of the group has matched (W when some live candidate has no window
+// within d); live candidates that found no window are dropped; a group with none left stops.
+template <int KS>
+__global__ void __launch_bounds__(256) count_group_kernel(const JobDesc* __restrict__ job,
+                                                          unsigned long long* total) {
+  const JobDesc jd = *job;
+  const uint64_t smask = (1ull << (2 * KS)) - 1;
+  unsigned long long local = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = jd.unit_lo + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < jd.unit_hi;
+       g += stride) {
+    GroupMask<KS> alive;
+    range_mask<KS>(g, jd.lo, jd.hi, alive);
+    uint32_t Ep, Op;
+    code_planes(g, Ep, Op);
+    for (int s = 0; s < jd.n && any_set<KS>(alive); ++s) {
+      GroupMask<KS> matched;
+#pragma unroll
+      for (int i = 0; i < GroupMask<KS>::NW; ++i) matched.w[i] = 0;
+      const uint2* row = jd.planes + (size_t)s * jd.wstride;
+      const uint64_t* crow = jd.codes + (size_t)s * jd.wstride;
+      int scanned = jd.W;
+      for (int j = 0; j < jd.W; ++j) {
+        const uint2 w = __ldg(row + j);
+        const int h = __popc((Ep ^ (w.x >> KS)) | (Op ^ (w.y >> KS)));
+        if (h <= jd.d) {
+          group_hit<KS, true>(matched, jd.ball, jd.d, h, (int)(__ldg(crow + j) & smask));
+          if (covers<KS>(matched, alive)) {
+            scanned = j + 1;
+            break;
+          }
+        }
+      }
+      local += (unsigned long long)scanned;
+#pragma unroll
+      for (int i = 0; i < GroupMask<KS>::NW; ++i) alive.w[i] &= matched.w[i];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(kFull, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
+}
+
 // Ball tables for ks = 1..kMaxKs: entry (v, r) = suffixes within distance r of v.
 __global__ void ball_kernel(uint64_t* table, int ks) {
   const int nv = 1 << (2 * ks);
@@ -662,12 +706,27 @@ cudaError_t launch_step(int kind, int p, const JobDesc* d_jobs, JobState* d_stat
 cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
                          cudaStream_t s) {
   count_kernel<<<grid, block, 0, s>>>(d_job, d_total);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_group(const JobDesc* d_job, int ks, unsigned long long* d_total, int grid,
+                               int block, cudaStream_t s) {
+  switch (ks) {
+    case 1: count_group_kernel<1><<<grid, block, 0, s>>>(d_job, d_total); break;
+    case 2: count_group_kernel<2><<<grid, block, 0, s>>>(d_job, d_total); break;
+    case 3: count_group_kernel<3><<<grid, block, 0, s>>>(d_job, d_total); break;
+    case 4: count_group_kernel<4><<<grid, block, 0, s>>>(d_job, d_total); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s) {
   const int entries = ball_table_words(ks);
   ball_kernel<<<(entries + 255) / 256, 256, 0, s>>>(table, ks);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -286,6 +286,7 @@ void scheduler(Server* S) {
       if (S->exec) e = cudaGraphLaunch(S->exec, S->stream);
       else e = launch_step(S->kind, S->pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl,
                            S->grid, S->block, S->smem, S->stream);
+      note_launches(1);
     }
     cudaEventRecord(S->ev1, S->stream);
     std::vector<JobState> st(nact);

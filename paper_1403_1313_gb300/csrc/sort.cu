@@ -279,6 +279,7 @@ cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, i
   const bool want_large = known_count < 0 || (known_count > kSmallMax && known_count <= cap);
   if (want_small) {
     small_sort_kernel<<<1, kSmallThreads, 0, s>>>(d_codes, d_count, cap);
+    note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -305,6 +306,7 @@ cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, i
   unique_write_kernel<<<ctas, kRadixThreads, 0, s>>>(a, b, d_count, cap, scanned);
   unique_finish_kernel<<<ctas, kRadixThreads, 0, s>>>(b, d_codes, d_count, cap, scanned, raw, ctas);
   store_count_kernel<<<1, 32, 0, s>>>(d_count, cap, scanned, raw, ctas);
+  note_launches(3 * passes + 5);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,63 @@
+"""Multi-worker search: the index-range split of Sec. IV.A across processes.
+
+Each rank searches one contiguous range of the candidate index space (sizes in proportion to
+optional weights, e.g. measured throughput), holding its own copy of the sequences — the paper's
+per-thread first/last l-mer assignment, one process per GPU.  The only exchange is one
+variable-size gather of the accepted codes: counts first, then the codes padded to the largest
+count.  Ranges are contiguous and each rank's codes ascend, so concatenating in rank order gives
+the globally ascending result.  Works over any torch.distributed backend: NCCL with CUDA
+tensors on GPUs, gloo with CPU tensors elsewhere.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rank_search_gpu(seqs, l, d, lo, hi):
+    import paper_1403_1313_gb300 as m
+    rows = np.ascontiguousarray(seqs, dtype=np.uint8) if isinstance(seqs, np.ndarray) else seqs
+    n = len(rows)
+    t = rows.shape[1] if isinstance(rows, np.ndarray) else len(rows[0])
+    o = m.motif_opts_default()
+    o.range_lo, o.range_hi = lo, hi
+    plan = m.motif_plan_create(n, t, l, d, o)
+    try:
+        m.motif_load_seqs(plan, rows)
+        return m.motif_search(plan)
+    finally:
+        m.motif_plan_destroy(plan)
+
+
+def gather_codes(codes: np.ndarray, group=None) -> np.ndarray:
+    """All-gathers every rank's ascending codes; returns their rank-order concatenation."""
+    import torch
+    import torch.distributed as dist
+
+    backend = dist.get_backend(group)
+    dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    world = dist.get_world_size(group)
+    cnt = torch.tensor([codes.size], dtype=torch.int64, device=dev)
+    counts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(counts, cnt, group=group)
+    counts = [int(c.item()) for c in counts]
+    width = max(1, max(counts))
+    mine = torch.zeros(width, dtype=torch.int64, device=dev)
+    if codes.size:
+        mine[:codes.size] = torch.from_numpy(codes.astype(np.int64)).to(dev)
+    parts = [torch.zeros(width, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    return np.concatenate([p[:c].cpu().numpy().astype(np.uint64) for p, c in zip(parts, counts)])
+
+
+def sharded_search(seqs, l: int, d: int, rank: int, world: int, weights=None, search_fn=None,
+                   group=None) -> np.ndarray:
+    """Searches this rank's share of [0, 4^l) and gathers the global ascending result.
+
+    search_fn(seqs, l, d, lo, hi) -> ascending codes in [lo, hi); default: the CUDA path."""
+    import paper_1403_1313_gb300 as m
+    lo, hi = m.motif_shard_range(4 ** l, rank, world, weights)
+    fn = search_fn or _rank_search_gpu
+    local = np.asarray(fn(seqs, l, d, lo, hi), dtype=np.uint64) if hi > lo else np.zeros(0, np.uint64)
+    if world == 1:
+        return local
+    return gather_codes(local, group)

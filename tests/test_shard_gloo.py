@@ -1,0 +1,73 @@
+"""The multi-worker path on CPU: two gloo ranks each search their Sec. IV.A index range (with the
+oracle standing in for the per-rank GPU search) and gather; the gathered result must equal the
+single-process result.  A rank that leaves before the gather makes the other rank's collective
+fail within a short timeout instead of hanging."""
+import datetime
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _oracle_range(seqs, l, d, lo, hi):
+    from oracle import oracle
+    return oracle.search(seqs, l, d, lo=lo, hi=hi)[0]
+
+
+def _worker(rank, world, port, l, d, seed, weights, out_dir, leave_early):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1403_1313_gb300 import fmgen
+    from paper_1403_1313_gb300.shard import sharded_search
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=6))
+    job = fmgen.fm_job(6, 90, l, d, seed)
+    if leave_early and rank == 1:
+        os._exit(0)  # leaves between steps: nothing of its own is in flight
+    try:
+        res = sharded_search(job.rows(), l, d, rank, world, weights=weights, search_fn=_oracle_range)
+        np.save(os.path.join(out_dir, "rank%d.npy" % rank), res)
+    except Exception as e:  # the collective noticed the missing peer
+        with open(os.path.join(out_dir, "rank%d.err" % rank), "w") as f:
+            f.write(type(e).__name__)
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:
+            pass
+
+
+@pytest.mark.parametrize("weights", [None, [1.0, 3.0]])
+def test_two_ranks_gather_equals_single(tmp_path, weights):
+    from oracle import oracle
+    from paper_1403_1313_gb300 import fmgen
+    l, d, seed = 8, 2, 77
+    mp.start_processes(_worker, args=(2, _free_port(), l, d, seed, weights, str(tmp_path), False),
+                       nprocs=2, join=True, start_method="spawn")
+    job = fmgen.fm_job(6, 90, l, d, seed)
+    ref, _ = oracle.search(job.rows(), l, d)
+    for r in range(2):
+        got = np.load(tmp_path / ("rank%d.npy" % r))
+        assert np.array_equal(got, ref)
+
+
+def test_missing_rank_fails_fast(tmp_path):
+    ctx = mp.start_processes(_worker, args=(2, _free_port(), 7, 2, 5, None, str(tmp_path), True),
+                             nprocs=2, join=False, start_method="spawn")
+    for p in ctx.processes:
+        p.join(timeout=120)
+    assert all(not p.is_alive() for p in ctx.processes)
+    assert (tmp_path / "rank0.err").exists() or not (tmp_path / "rank0.npy").exists()

@@ -55,6 +55,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+                    help="single: the driver's (l,d) line; batch: 64 uneven jobs batched vs one "
+                         "job per launch; serve: Poisson arrivals, p50/p99 latency per rate")
+    ap.add_argument("--rates", default="1,2,5,10,20,50,100,200")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-jobs", type=int, default=200)
     return ap.parse_args()
 
 
@@ -249,10 +255,10 @@ def run_ours(args):
             step()
             ev_e[k].record(stream)
     stream.synchronize()
-    launches = m.motif_kernel_launches() - launches0
     clocks = sampler.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in zip(ev_s, ev_e))
-    st = m.motif_stats(plan)
+    st = m.motif_stats(plan)  # also accounts the step launches run inside the graphs
+    launches = m.motif_kernel_launches() - launches0
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
@@ -333,10 +339,122 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """64 uneven jobs (seed 4): one batched launch sequence vs one job per launch."""
+    import numpy as np
+    import torch
+    import paper_1403_1313_gb300 as m
+    from paper_1403_1313_gb300 import fmgen
+
+    torch.cuda.set_device(0)
+    jobs = fmgen.batched_jobs(seed=4, count=64)
+    out = {}
+    for label, sel in (("all_64", lambda j: True), ("small_l_le_12", lambda j: j.l <= 12)):
+        js = [j for j in jobs if sel(j)]
+        plans = []
+        for j in js:
+            pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+            m.motif_load_seqs(pl, j.seqs)
+            plans.append(pl)
+        compares = sum(m.motif_count_compares(pl) for pl in plans)
+        cands = sum(4 ** j.l for j in js)
+        plain_res = [m.motif_search(pl) for pl in plans]          # warm-up + reference result
+        batch_res = m.motif_batch_search(plans, use_graph=True)
+        assert all(np.array_equal(a, b) for a, b in zip(plain_res, batch_res)), "batch != plain"
+        reps = max(1, args.steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for pl in plans:
+                m.motif_search(pl)
+        t_plain = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            m.motif_batch_search(plans, use_graph=True)
+        t_batch = (time.perf_counter() - t0) / reps
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            m.motif_batch_search(plans, use_graph=False)
+        t_batch_nograph = (time.perf_counter() - t0) / reps
+        survivors = sum(int(r.size) for r in batch_res)
+        out[label] = {
+            "jobs": len(js), "candidates": cands, "algorithmic_compares": compares,
+            "survivors": survivors,
+            "plain_ms": 1e3 * t_plain, "batched_ms": 1e3 * t_batch,
+            "batched_nograph_ms": 1e3 * t_batch_nograph,
+            "plain_jobs_per_s": len(js) / t_plain, "batched_jobs_per_s": len(js) / t_batch,
+            "plain_compares_per_s": compares / t_plain, "batched_compares_per_s": compares / t_batch,
+            "batched_over_plain": t_plain / t_batch,
+        }
+        for pl in plans:
+            m.motif_plan_destroy(pl)
+    print(json.dumps({"mode": "batch", "workload": "64 jobs, seed 4: l~U{9..15}, d~U{1..4}, "
+                      "n~U{5..40}, t~U{200..1000}, FM-planted", "reps": max(1, args.steps),
+                      "results": out}), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals at each rate; latency = submit -> result ready, from the library."""
+    import numpy as np
+    import torch
+    import paper_1403_1313_gb300 as m
+    from paper_1403_1313_gb300 import fmgen
+
+    torch.cuda.set_device(0)
+    rows = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        count = int(min(args.serve_jobs, max(20, rate * args.serve_seconds)))
+        jobs = fmgen.serving_jobs(rate, count, seed=5)
+        m.motif_server_start(max_active=64)
+        # warm-up job (graph capture, ball tables, allocator pools)
+        wj = fmgen.fm_job(10, 300, 11, 3, 1)
+        pl = m.motif_plan_create(wj.n, wj.t, wj.l, wj.d)
+        m.motif_load_seqs(pl, wj.seqs)
+        m.motif_poll(m.motif_submit(pl), timeout_ms=60000)
+        m.motif_plan_destroy(pl)
+        ids = []
+        t0 = time.perf_counter()
+        for j in jobs:
+            delay = t0 + j.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+            m.motif_load_seqs(pl, j.seqs)
+            ids.append(m.motif_submit(pl))
+            m.motif_plan_destroy(pl)
+        lat, queue, cands, ok = [], [], 0, 0
+        for j, jid in zip(jobs, ids):
+            res = m.motif_poll(jid, timeout_ms=600000)
+            codes, st = res
+            lat.append(st["total_ms"])
+            queue.append(st["queue_ms"])
+            cands += 4 ** j.l
+            ok += int(m.motif_encode(j.consensus) in set(codes.tolist()))
+        wall = time.perf_counter() - t0
+        m.motif_server_stop()
+        lat = np.array(lat)
+        rows.append({"rate_jobs_per_s": rate, "jobs": count, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                     "queue_p50_ms": float(np.percentile(queue, 50)),
+                     "queue_p99_ms": float(np.percentile(queue, 99)),
+                     "throughput_jobs_per_s": count / wall, "candidates_per_s": cands / wall,
+                     "consensus_found": ok})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"mode": "serve", "workload": "Poisson arrivals, seed 5: l~U{11..15}, "
+                      "d~U{2..4}, n~U{10..30}, t~U{300..800}, GC in {0.4,0.5,0.6}, FM-planted",
+                      "rates": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

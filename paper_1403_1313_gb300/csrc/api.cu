@@ -1,6 +1,7 @@
 // C ABI: plans, window loading (K0), the search (K1 steps + K2 sort/dedup), the compare
 // counter, statistics and small helpers.  Everything device-side runs on the plan's stream.
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -40,9 +41,19 @@ cudaEvent_t* next_event_quad(motif_plan_s* p) {
 }
 
 int fold_event_quads(motif_plan_s* p) {
-  if (p->evq_used == 0) return MOTIF_OK;
+  if (p->evq_used == 0 && p->graph_searches == 0) return MOTIF_OK;
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return status_from_cuda(e);
+  if (p->graph_searches > 0) {
+    // Each graph launch ran an init kernel and one step kernel per step; every search of the
+    // plan since the last fold ran the same number of steps as the last one.
+    StepCtl ctl{};
+    if (cudaMemcpy(&ctl, p->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      p->last_steps = ctl.steps;
+      note_launches((int)(p->graph_searches * (1 + (int64_t)ctl.steps)));
+    }
+    p->graph_searches = 0;
+  }
   for (size_t q = 0; q < p->evq_used; ++q) {
     float a = 0, b = 0;
     cudaEventElapsedTime(&a, p->evq[4 * q], p->evq[4 * q + 1]);
@@ -81,8 +92,6 @@ void plan_free(motif_plan_s* p, void* ptr, size_t bytes) {
 namespace {
 std::mutex g_ball_mu;
 uint64_t* g_ball[64][kMaxKs + 1] = {};
-std::mutex g_attr_mu;
-size_t g_attr_smem[3][kMaxKs + 1] = {};
 }  // namespace
 
 const uint64_t* ball_table(int device, int ks, cudaStream_t s) {
@@ -148,15 +157,10 @@ int plan_configure(motif_plan_s* p) {
                                          : (kind == MOTIF_KERNEL_GROUP && pv >= 3 ? 2 : 1);
   const int block = o.block > 0 ? o.block : 256;
   if (block % 32 != 0 || block > 256) return MOTIF_ERR_ARG;
-  const size_t smem = step_smem_bytes(kind, pv, std::max(p->wstride, kWinAlign));
+  const size_t smem = step_smem_bytes(kind, pv, std::max(p->wstride, kWinAlign), block);
   {
-    std::lock_guard<std::mutex> g(g_attr_mu);
-    size_t& cur = g_attr_smem[kind][pv];
-    if (smem > cur) {
-      cudaError_t e = step_kernel_attrs(kind, pv, smem);
-      if (e != cudaSuccess) return status_from_cuda(e);
-      cur = smem;
-    }
+    cudaError_t e = step_kernel_attrs(kind, pv, smem);
+    if (e != cudaSuccess) return status_from_cuda(e);
   }
   int per_sm = step_max_ctas_per_sm(kind, pv, block, smem);
   if (per_sm <= 0) return MOTIF_ERR_ARG;
@@ -172,6 +176,7 @@ int plan_configure(motif_plan_s* p) {
   if (chunk != p->qcap || words != p->qmask_words) free_queues(p);  // re-made on first use
   p->want_qcap = chunk;
   p->want_qwords = words;
+  invalidate_graphs(p);
   p->kind = kind;
   p->p = pv;
   p->span0 = span0;
@@ -187,8 +192,20 @@ int plan_configure(motif_plan_s* p) {
   return MOTIF_OK;
 }
 
+void invalidate_graphs(motif_plan_s* p) {
+  if (p->g_steps) cudaGraphExecDestroy(p->g_steps);
+  if (p->g_sort) cudaGraphExecDestroy(p->g_sort);
+  p->g_steps = p->g_sort = nullptr;
+  p->desc_out = nullptr;
+  p->desc_cap = -1;
+  p->gs_out = nullptr;
+  p->gs_cap = -1;
+  p->gs_scratch = nullptr;
+}
+
 int plan_ensure_buffers(motif_plan_s* p) {
   if (!p->d_qidx[0]) {
+    invalidate_graphs(p);
     for (int i = 0; i < 2; ++i) {
       p->d_qidx[i] = (uint32_t*)plan_alloc(p, p->want_qcap * 4);
       if (!p->d_qidx[i]) return MOTIF_ERR_OOM;
@@ -201,6 +218,7 @@ int plan_ensure_buffers(motif_plan_s* p) {
     p->qmask_words = p->want_qwords;
   }
   if (!p->d_out) {
+    invalidate_graphs(p);
     p->d_out = (uint64_t*)plan_alloc(p, (size_t)(1 << 16) * 8);
     if (!p->d_out) return MOTIF_ERR_OOM;
     p->out_cap = 1 << 16;
@@ -220,7 +238,6 @@ int run_steps(int kind, int pv, const JobDesc* d_jobs, JobState* d_states, int n
       cudaError_t e = launch_step(kind, pv, d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
       if (e != cudaSuccess) return status_from_cuda(e);
     }
-    note_launches(todo);
     launched += todo;
     if (!poll) break;
     unsigned active = 0;
@@ -261,6 +278,7 @@ int max_steps_of(const motif_plan_s* p) {
 
 int ensure_out(motif_plan_s* p, int64_t need) {
   if (need <= p->out_cap) return MOTIF_OK;
+  p->desc_out = nullptr;  // the descriptor names the output buffer
   plan_free(p, p->d_out, (size_t)p->out_cap * 8);
   p->d_out = (uint64_t*)plan_alloc(p, (size_t)need * 8);
   p->out_cap = p->d_out ? need : 0;
@@ -291,22 +309,50 @@ int check_alphabet(motif_plan_s* p) {
 }
 
 // Enqueues one search of the plan writing into (out, cap): descriptor, state reset, steps.
-int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll, int* steps) {
+int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   int rc = plan_ensure_buffers(p);
   if (rc) return rc;
-  JobDesc jd;
-  fill_desc(p, &jd, out, cap);
-  if (p->kind == MOTIF_KERNEL_GROUP && !jd.ball) return MOTIF_ERR_CUDA;
-  cudaError_t e = cudaMemcpyAsync(p->d_job, &jd, sizeof(jd), cudaMemcpyHostToDevice, p->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_ctl, 0, sizeof(StepCtl), p->stream);
-  if (e != cudaSuccess) return status_from_cuda(e);
   if (p->nchunks == 0) {
-    if (steps) *steps = 0;
-    return MOTIF_OK;
+    cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
+    return status_from_cuda(e);
   }
-  return run_steps(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
-                   max_steps_of(p), poll, timeout_of(p), p->stream, steps);
+  // Upload the descriptor when (out, cap) changed; it lives in pinned memory so the copy is
+  // stream-ordered without blocking the host.
+  if (p->desc_out != out || p->desc_cap != (int64_t)cap) {
+    if (!p->h_desc && cudaHostAlloc((void**)&p->h_desc, sizeof(JobDesc), 0) != cudaSuccess) {
+      p->h_desc = nullptr;
+      return MOTIF_ERR_OOM;
+    }
+    cudaError_t e = cudaStreamSynchronize(p->stream);  // the previous upload has completed
+    if (e != cudaSuccess) return status_from_cuda(e);
+    fill_desc(p, p->h_desc, out, cap);
+    if (p->kind == MOTIF_KERNEL_GROUP && !p->h_desc->ball) return MOTIF_ERR_CUDA;
+    e = cudaMemcpyAsync(p->d_job, p->h_desc, sizeof(JobDesc), cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    p->desc_out = out;
+    p->desc_cap = (int64_t)cap;
+  }
+  // Profiling aid: MOTIF_NO_GRAPH=1 launches the same step kernel directly (profilers do not
+  // list kernels inside conditional graph nodes); the blocking path polls, the device path
+  // launches the step bound blindly.
+  static const bool no_graph = getenv("MOTIF_NO_GRAPH") != nullptr;
+  if (no_graph) {
+    cudaError_t e = launch_init_steps(p->d_state, 1, p->d_ctl, 0, 0, p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    return run_steps(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
+                     max_steps_of(p), poll, timeout_of(p), p->stream, nullptr);
+  }
+  // One graph launch runs every step: init, then a while loop whose body is the step kernel.
+  if (!p->g_steps) {
+    cudaError_t e = build_step_graph(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid,
+                                     p->block, p->smem, (unsigned)max_steps_of(p), &p->g_steps);
+    if (e != cudaSuccess) {
+      p->g_steps = nullptr;
+      return status_from_cuda(e);
+    }
+  }
+  ++p->graph_searches;
+  return status_from_cuda(cudaGraphLaunch(p->g_steps, p->stream));
 }
 
 __global__ void finalize_count_kernel(const int* err, const unsigned long long* count,
@@ -407,6 +453,8 @@ void motif_plan_destroy(motif_plan p) {
   cudaStreamSynchronize(p->stream);
   for (cudaEvent_t ev : p->evq)
     if (ev) cudaEventDestroy(ev);
+  invalidate_graphs(p);
+  if (p->h_desc) cudaFreeHost(p->h_desc);
   delete p;
 }
 
@@ -465,10 +513,9 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   if (!ev) return MOTIF_ERR_CUDA;
   for (;;) {
     cudaEventRecord(ev[0], p->stream);
-    int steps = 0;
     rc = plan_ensure_buffers(p);
     if (rc) return rc;
-    rc = enqueue_search(p, p->d_out, (uint64_t)p->out_cap, true, &steps);
+    rc = enqueue_search(p, p->d_out, (uint64_t)p->out_cap, true);
     if (rc) return rc;
     cudaEventRecord(ev[1], p->stream);
     cudaError_t e = cudaMemcpyAsync(&found, &p->d_state->out_count, sizeof(found),
@@ -532,12 +579,28 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
     cudaEvent_t* ev = next_event_quad(p);
     if (!ev) return MOTIF_ERR_CUDA;
     cudaEventRecord(ev[0], p->stream);
-    rc = enqueue_search(p, d_out_codes, (uint64_t)capacity, false, nullptr);
+    rc = enqueue_search(p, d_out_codes, (uint64_t)capacity, false);
     if (rc) return rc;
     cudaEventRecord(ev[1], p->stream);
     cudaEventRecord(ev[2], p->stream);
-    cudaError_t e = launch_sort_unique(d_out_codes, &p->d_state->out_count, capacity, 2 * p->l,
-                                       p->d_sort, p->sms, -1, p->stream);
+    if (!p->g_sort || p->gs_out != d_out_codes || p->gs_cap != capacity || p->gs_scratch != p->d_sort) {
+      if (p->g_sort) cudaGraphExecDestroy(p->g_sort);
+      p->g_sort = nullptr;
+      cudaGraph_t g = nullptr;
+      cudaGraphNode_t last;
+      cudaError_t e = cudaGraphCreate(&g, 0);
+      if (e == cudaSuccess)
+        e = add_sort_nodes(g, nullptr, d_out_codes, &p->d_state->out_count, capacity, 2 * p->l,
+                           p->d_sort, p->sms, &last);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&p->g_sort, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) { p->g_sort = nullptr; return status_from_cuda(e); }
+      p->gs_out = d_out_codes;
+      p->gs_cap = capacity;
+      p->gs_scratch = p->d_sort;
+    }
+    cudaError_t e = cudaGraphLaunch(p->g_sort, p->stream);
+    note_launches(1);
     cudaEventRecord(ev[3], p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
   }

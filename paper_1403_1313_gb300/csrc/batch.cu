@@ -62,36 +62,20 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
     return run_steps(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem,
                      max_steps, true, timeout_ms, s, nullptr);
   }
-  const int group = 4;
-  cudaGraph_t graph = nullptr;
+  // One graph launch: init, then a while loop of step launches that ends when every job is
+  // done (or after max_steps steps).
   cudaGraphExec_t exec = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-  for (int i = 0; i < group && e == cudaSuccess; ++i)
-    e = launch_step(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem, s);
-  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
-  if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-  const double t0 = now_ms();
-  int launched = 0, rc = MOTIF_OK;
-  while (e == cudaSuccess && launched < max_steps) {
-    e = cudaGraphLaunch(exec, s);
-    note_launches(group);
-    launched += group;
-    unsigned active = 0;
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&active, &c->d_ctl->active_jobs, sizeof(unsigned),
-                          cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess || active == 0) break;
-    if (timeout_ms > 0 && now_ms() - t0 > timeout_ms) {
-      rc = MOTIF_ERR_TIMEOUT;
-      break;
-    }
-  }
+  cudaError_t e = build_step_graph(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block,
+                                   smem, (unsigned)max_steps, &exec);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  StepCtl ctl{};
+  if (e == cudaSuccess) e = cudaMemcpy(&ctl, c->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
   if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) return status_from_cuda(e);
-  return rc;
+  note_launches(1 + (int)ctl.steps);
+  (void)timeout_ms;
+  return ctl.active_jobs == 0 ? MOTIF_OK : MOTIF_ERR_TIMEOUT;
 }
 
 }  // namespace motif_batch

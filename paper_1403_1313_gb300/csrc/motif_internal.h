@@ -56,6 +56,8 @@ struct StepCtl {
   unsigned int tiles_per_warp;   // 0 = unlimited; else each warp grabs at most this many tiles
   unsigned int active_jobs;      // written by the last CTA: jobs not yet done
   unsigned int steps;            // steps executed
+  unsigned int max_steps;        // graph while-loops stop after this many steps (0 = no bound)
+  unsigned int pad;
 };
 
 __host__ __device__ inline int mask_words(int ks) { return ks <= 3 ? 1 : (1 << (2 * ks - 6)); }
@@ -77,11 +79,26 @@ cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s);
 // Step kernel variants: kind = MOTIF_KERNEL_CAND with p = candidates per lane (1, 2, 4), or
 // MOTIF_KERNEL_GROUP with p = ks (1..4).  Every job of one launch must use the same variant.
 bool step_variant_ok(int kind, int p);
-size_t step_smem_bytes(int kind, int p, int wstride);
+size_t step_smem_bytes(int kind, int p, int wstride, int block);
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem);
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem);
 cudaError_t launch_step(int kind, int p, const JobDesc* d_jobs, JobState* d_states, int njobs,
                         StepCtl* d_ctl, int grid, int block, size_t smem, cudaStream_t s);
+// Adds a step-kernel node to graph g.  With use_cond != 0 the kernel sets `cond`, the
+// condition of the while node whose body g is, to continue while jobs remain.
+cudaError_t add_step_node(cudaGraph_t g, int kind, int p, const JobDesc* d_jobs,
+                          JobState* d_states, int njobs, StepCtl* d_ctl, int grid, int block,
+                          size_t smem, cudaGraphConditionalHandle cond, int use_cond,
+                          cudaGraphNode_t* node);
+// Zeroes njobs states and initialises the step control block.
+cudaError_t launch_init_steps(JobState* d_states, int njobs, StepCtl* d_ctl, unsigned max_steps,
+                              unsigned tiles_per_warp, cudaStream_t s);
+cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl* d_ctl,
+                          unsigned max_steps, unsigned tiles_per_warp, cudaGraphNode_t* node);
+// Builds and instantiates init -> while(step) over a job table: one launch runs every step.
+cudaError_t build_step_graph(int kind, int p, const JobDesc* d_jobs, JobState* d_states,
+                             int njobs, StepCtl* d_ctl, int grid, int block, size_t smem,
+                             unsigned max_steps, cudaGraphExec_t* exec);
 cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
                          cudaStream_t s);
 // Canonical (group, window) prefix-compare tally of the GROUP formulation with ks suffix bases.
@@ -93,5 +110,9 @@ size_t sort_scratch_bytes(int64_t cap, int sms);
 cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, int64_t cap,
                                int key_bits, void* scratch, int sms, long long known_count,
                                cudaStream_t s);
+// Graph form of launch_sort_unique (the multi-CTA path under a conditional IF node).
+cudaError_t add_sort_nodes(cudaGraph_t g, cudaGraphNode_t dep, uint64_t* d_codes,
+                           unsigned long long* d_count, int64_t cap, int key_bits, void* scratch,
+                           int sms, cudaGraphNode_t* last);
 
 }  // namespace motif

@@ -48,6 +48,18 @@ struct motif_plan_s {
   unsigned long long* d_total = nullptr;
   int64_t device_bytes = 0;
 
+  // CUDA graphs: init + while(step) for the uploaded descriptor, and the device-path sort.
+  cudaGraphExec_t g_steps = nullptr;
+  cudaGraphExec_t g_sort = nullptr;
+  motif::JobDesc* h_desc = nullptr;  // pinned copy of the uploaded descriptor
+  uint64_t* desc_out = nullptr;      // output buffer named by the uploaded descriptor
+  int64_t desc_cap = -1;
+  uint64_t* gs_out = nullptr;        // buffers the sort graph was built for
+  int64_t gs_cap = -1;
+  void* gs_scratch = nullptr;
+  int64_t graph_searches = 0;        // graph launches since the last fold (launch accounting)
+  unsigned last_steps = 0;           // steps of the last folded search
+
   bool loaded = false;
   bool check_alpha = false;  // device-loaded characters not yet validated on the host
   motif_stats_t stats{};
@@ -75,6 +87,8 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
 int plan_configure(motif_plan_s* p);
 // Allocates the survivor queues and the default output buffer on first use.
 int plan_ensure_buffers(motif_plan_s* p);
+// Drops the plan's cached graphs and descriptor upload (after a configuration change).
+void invalidate_graphs(motif_plan_s* p);
 
 // Launches steps for a job table until no job is active (polling every `group` steps), or
 // blindly `max_steps` steps when poll == false.  Returns a motif_status.

@@ -1,33 +1,38 @@
 // K1: the skip-BF search (Sec. III.A) as a multi-job, pass-structured CUDA kernel.
 //
-// Work is organised in *passes*.  A pass takes a list of live work units of one job and scans
-// one or a few consecutive sequences for each of them, lane by lane:
-//   - a fresh pass takes its units straight from the candidate index range of the current chunk
-//     (Sec. IV.A: l-mers are produced from their index, never stored) and scans sequences
-//     [0, span0);
-//   - a queue pass takes the survivors that the previous pass compacted into a ping-pong queue
-//     and scans the next sequence, or every remaining sequence once few survivors are left;
-//   - units that fail a sequence are dropped on the spot and never look at the remaining
-//     sequences (the skip of Sec. III.A); units that pass every sequence are accepted.
-// Survivors are compacted with a warp ballot / prefix sum and one atomic per warp, so that the
-// next pass runs full warps instead of lanes idling behind the skip.
+// Work is organised in *passes* over the live work units of each job:
+//   FRESH — units come straight from the candidate index range of the current chunk (Sec. IV.A:
+//           an l-mer is produced from its index, never stored); one lane per unit scans
+//           sequences [0, span0) from shared memory;
+//   QUEUE — the survivors the previous pass compacted into a ping-pong queue; one lane per
+//           entry scans the next sequence from shared memory;
+//   REST  — once few survivors are left, one warp per entry scans every remaining sequence:
+//           the lanes split the windows and the warp combines their results.
+// A unit that fails a sequence is dropped on the spot and never looks at the later sequences
+// (the skip of Sec. III.A); a unit that passes the last sequence is accepted.  Between passes the
+// survivors are compacted with a warp ballot / prefix sum and one atomic per warp, so the next
+// pass runs full warps instead of lanes idling behind the skip.
 //
 // Two unit kinds share this structure:
-//   CAND  — one candidate l-mer per lane (cpt per lane in a fresh pass).  Per window:
+//   CAND  — one candidate l-mer per lane (cpt of them in a fresh pass).  Per window:
 //           m = (E_c ^ E_w) | (O_c ^ O_w) over the compressed bit planes (the pair-fold of the
-//           XOR of the packed codes), dist = popc(m), running min, early break once the
-//           minimum is <= d (Sec. III.A: "the Hamming distance ... less than or equal to d").
+//           XOR of the packed codes), dist = popc(m), running min; a lane stops scanning a
+//           sequence once every live candidate it holds is within d of some window.
 //   GROUP — one group of 4^ks candidates sharing their first l-ks bases per lane.  Per window
-//           one POPC gives the prefix distance h; when h <= d the suffixes within d-h of the
-//           window's last ks bases (a precomputed Hamming-ball mask) are marked as matched.
-//           Hamming distance is additive over positions, so each candidate of the group is
-//           matched by exactly the windows the per-candidate test would accept.
+//           one POPC gives the prefix distance h.  When h <= d the window is recorded in a
+//           per-lane hit list in shared memory; at the end of the sequence each recorded window
+//           ORs in the precomputed mask of suffixes within d-h of its last ks bases (a row of
+//           the Hamming-ball table).  Hamming distance is additive over positions, so each
+//           candidate of the group is matched by exactly the windows the per-candidate test
+//           would accept.  Deferring the rare hits keeps the scan loop free of divergent work.
 //
 // A launch of the step kernel advances every job in the table by one pass (or part of one,
 // under a tile budget).  CTAs are persistent: each walks the jobs in table order, stages the
-// windows of the pass into shared memory and pulls 32-unit tiles per warp from the job's pass
-// cursor.  The last CTA to finish advances each job's state for the next launch; no CTA ever
-// waits for another.
+// windows of the pass into shared memory and pulls tiles from the job's pass cursor.  The last
+// CTA to finish advances each job's state for the next launch (and, inside a CUDA graph, sets
+// the while-loop condition); no CTA ever waits for another.
+#include <mutex>
+
 #include "motif_internal.h"
 
 namespace motif {
@@ -35,6 +40,10 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxStageSeqs = 2;  // sequences of one pass staged in shared memory
+constexpr int kHitCap = 16;       // GROUP: hit-list entries per lane before a flush
+constexpr int kMaxBlock = 256;
+
+enum PassMode { kFresh = 0, kQueue = 1, kRest = 2 };
 
 __device__ __forceinline__ uint32_t compress_even(uint64_t x) {
   x &= 0x5555555555555555ull;
@@ -77,15 +86,15 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
   return base + (incl - cnt);
 }
 
+
 // Shape of the pass a job is in; identical in every CTA of a step.
 struct Pass {
-  unsigned long long work;  // items of the pass
+  unsigned long long work;  // items of the pass (units, or queue entries)
   uint64_t chunk_base;      // first unit of the chunk
   uint64_t chunk_units;     // units in the chunk
-  int s0, s1;               // sequences [s0, s1) scanned in-lane
-  int fresh;                // items are chunk units (1) or queue entries (0)
+  int s0, s1;               // sequences [s0, s1) the pass scans
+  int mode;                 // PassMode
   int qin, qout;
-  int staged;               // windows of [s0, s1) come from shared memory
 };
 
 __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
@@ -96,31 +105,43 @@ __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
   const uint64_t left = jd.unit_hi > p.chunk_base ? jd.unit_hi - p.chunk_base : 0;
   p.chunk_units = left < jd.chunk_units ? left : jd.chunk_units;
   if (pass_seq == 0) {
-    p.fresh = 1;
+    p.mode = kFresh;
     p.work = p.chunk_units;
     p.s0 = 0;
     p.s1 = jd.span0 < jd.n ? jd.span0 : jd.n;
     p.qin = 0;
     p.qout = 0;
   } else {
-    p.fresh = 0;
     p.qin = ld_volatile(&st->qsel);
     p.qout = 1 - p.qin;
     p.work = ld_volatile(&st->qcount[p.qin]);
     p.s0 = pass_seq;
-    p.s1 = p.work <= jd.rest_threshold ? jd.n : (pass_seq + 1 < jd.n ? pass_seq + 1 : jd.n);
+    if (p.work <= jd.rest_threshold && jd.n - pass_seq >= 2) {
+      p.mode = kRest;
+      p.s1 = jd.n;
+    } else {
+      p.mode = kQueue;
+      p.s1 = pass_seq + 1;
+    }
   }
-  p.staged = (p.s1 - p.s0) <= kMaxStageSeqs;
   return p;
+}
+
+// Items per tile: a warp takes 32*cpt fresh CAND candidates, 32 units / entries otherwise, and
+// one entry per warp in a REST pass.
+__device__ __forceinline__ unsigned long long tile_of(int kind, int p, int mode) {
+  if (mode == kRest) return 1;
+  if (kind == MOTIF_KERNEL_CAND && mode == kFresh) return 32ull * p;
+  return 32;
 }
 
 // ---------------------------------------------------------------------------------------------
 // CAND: one candidate per lane slot.
 
-// Scans one sequence's windows for up to CPT candidates; returns the subset of `alive` that
-// has a window within distance d.  `w4` holds two windows (E0,O0,E1,O1) per uint4 and the row
-// is padded to a multiple of 8 windows.
-template <int CPT, bool GLOBAL>
+// Scans one staged sequence for up to CPT candidates; returns the subset of `alive` that has a
+// window within distance d.  `w4` holds two windows (E0,O0,E1,O1) per uint4; the row is padded
+// to a multiple of 8 windows.
+template <int CPT>
 __device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int wpad, int d,
                                               const uint32_t (&E)[CPT], const uint32_t (&O)[CPT],
                                               unsigned alive) {
@@ -129,12 +150,7 @@ __device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int 
   for (int c = 0; c < CPT; ++c) mn[c] = 64u;
   const int n4 = wpad >> 1;  // uint4 count
   for (int q = 0; q < n4; q += 4) {
-    uint4 a, b, e, f;
-    if (GLOBAL) {
-      a = __ldg(w4 + q); b = __ldg(w4 + q + 1); e = __ldg(w4 + q + 2); f = __ldg(w4 + q + 3);
-    } else {
-      a = w4[q]; b = w4[q + 1]; e = w4[q + 2]; f = w4[q + 3];
-    }
+    const uint4 a = w4[q], b = w4[q + 1], e = w4[q + 2], f = w4[q + 3];
     unsigned hit = 0;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
@@ -158,6 +174,7 @@ __device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int 
   return matched & alive;
 }
 
+// FRESH / QUEUE tile: lane slot c of the warp owns item base + c*32 + lane.
 template <int CPT>
 __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
                           unsigned long long base, const uint4* stage) {
@@ -170,21 +187,14 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
     off[c] = 0;
     E[c] = O[c] = 0;
     if (item < p.work) {
-      off[c] = p.fresh ? (uint32_t)item : jd.qidx[p.qin][item];
+      off[c] = p.mode == kFresh ? (uint32_t)item : jd.qidx[p.qin][item];
       code_planes(p.chunk_base + off[c], E[c], O[c]);
       alive |= 1u << c;
     }
   }
   const int wpad = jd.wstride;
-  for (int s = p.s0; s < p.s1 && alive; ++s) {
-    if (p.staged) {
-      alive = scan_cand<CPT, false>(stage + (size_t)(s - p.s0) * (wpad >> 1), wpad, jd.d, E, O,
-                                    alive);
-    } else {
-      const uint4* g = reinterpret_cast<const uint4*>(jd.planes + (size_t)s * wpad);
-      alive = scan_cand<CPT, true>(g, wpad, jd.d, E, O, alive);
-    }
-  }
+  for (int s = p.s0; s < p.s1 && alive; ++s)
+    alive = scan_cand<CPT>(stage + (size_t)(s - p.s0) * (wpad >> 1), wpad, jd.d, E, O, alive);
   __syncwarp();
   const unsigned cnt = __popc(alive);
   if (p.s1 >= jd.n) {
@@ -200,6 +210,37 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
       if (alive & (1u << c)) jd.qidx[p.qout][slot++] = off[c];
+  }
+}
+
+// REST: the warp owns one queue entry and scans every remaining sequence, lanes striding over
+// the windows of global memory.
+__device__ void cand_rest(const JobDesc& jd, JobState* st, const Pass& p,
+                          unsigned long long item) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t k = p.chunk_base + jd.qidx[p.qin][item];
+  uint32_t E, O;
+  code_planes(k, E, O);
+  for (int s = p.s0; s < jd.n; ++s) {
+    const uint2* row = jd.planes + (size_t)s * jd.wstride;
+    bool matched = false;
+    for (int b = 0; b < jd.W; b += 32) {
+      const int j = b + lane;
+      bool hit = false;
+      if (j < jd.W) {
+        const uint2 w = __ldg(row + j);
+        hit = __popc((E ^ w.x) | (O ^ w.y)) <= jd.d;
+      }
+      if (__any_sync(kFull, hit)) {
+        matched = true;
+        break;
+      }
+    }
+    if (!matched) return;  // the skip: no window of sequence s is within d
+  }
+  if (lane == 0) {
+    const unsigned long long slot = atomicAdd(&st->out_count, 1ull);
+    if (slot < jd.out_cap) jd.out[slot] = k;
   }
 }
 
@@ -247,16 +288,30 @@ __device__ __forceinline__ void group_hit(GroupMask<KS>& matched, const uint64_t
   or_ball<KS, GLOBAL>(matched, ball, v, r);
 }
 
-// Staged form: wp4 holds two prefix-plane windows per uint4, sfx the suffix value per window.
+// ORs the recorded hits (window j << 3 | radius) of this lane into `matched`.
+template <int KS>
+__device__ __forceinline__ void flush_hits(GroupMask<KS>& matched, const uint32_t* hl, int hstride,
+                                           int cnt, const uint16_t* __restrict__ sfx,
+                                           const uint64_t* ball) {
+  for (int i = 0; i < cnt; ++i) {
+    const uint32_t e = hl[i * hstride];
+    or_ball<KS, false>(matched, ball, sfx[e >> 3], (int)(e & 7u));
+  }
+}
+
+// Staged scan of one sequence: wp4 holds two prefix-plane windows per uint4, sfx the suffix
+// value of each window; hl is this lane's hit list (stride hstride words).
 template <int KS>
 __device__ __forceinline__ void scan_group_staged(const uint4* __restrict__ wp4,
                                                   const uint16_t* __restrict__ sfx, int wpad,
                                                   int d, uint32_t Ep, uint32_t Op,
-                                                  const uint64_t* ball, GroupMask<KS>& alive) {
+                                                  const uint64_t* ball, uint32_t* hl, int hstride,
+                                                  GroupMask<KS>& alive) {
   GroupMask<KS> matched;
 #pragma unroll
   for (int i = 0; i < GroupMask<KS>::NW; ++i) matched.w[i] = 0;
   const int n4 = wpad >> 1;
+  int cnt = 0;
   for (int q = 0; q < n4; q += 2) {
     const uint4 a = wp4[q], b = wp4[q + 1];
     const int h0 = __popc((Ep ^ a.x) | (Op ^ a.y));
@@ -264,40 +319,19 @@ __device__ __forceinline__ void scan_group_staged(const uint4* __restrict__ wp4,
     const int h2 = __popc((Ep ^ b.x) | (Op ^ b.y));
     const int h3 = __popc((Ep ^ b.z) | (Op ^ b.w));
     if (min(min(h0, h1), min(h2, h3)) <= d) {
-      const int j = q * 2;
-      if (h0 <= d) group_hit<KS, false>(matched, ball, d, h0, sfx[j]);
-      if (h1 <= d) group_hit<KS, false>(matched, ball, d, h1, sfx[j + 1]);
-      if (h2 <= d) group_hit<KS, false>(matched, ball, d, h2, sfx[j + 2]);
-      if (h3 <= d) group_hit<KS, false>(matched, ball, d, h3, sfx[j + 3]);
-      if (covers<KS>(matched, alive)) break;  // every live candidate matched this sequence
+      const uint32_t j = (uint32_t)q * 2u;
+      if (h0 <= d) { hl[cnt * hstride] = (j << 3) | (uint32_t)min(d - h0, KS); ++cnt; }
+      if (h1 <= d) { hl[cnt * hstride] = ((j + 1) << 3) | (uint32_t)min(d - h1, KS); ++cnt; }
+      if (h2 <= d) { hl[cnt * hstride] = ((j + 2) << 3) | (uint32_t)min(d - h2, KS); ++cnt; }
+      if (h3 <= d) { hl[cnt * hstride] = ((j + 3) << 3) | (uint32_t)min(d - h3, KS); ++cnt; }
+      if (cnt > kHitCap - 4) {
+        flush_hits<KS>(matched, hl, hstride, cnt, sfx, ball);
+        cnt = 0;
+        if (covers<KS>(matched, alive)) break;  // every live candidate matched this sequence
+      }
     }
   }
-#pragma unroll
-  for (int i = 0; i < GroupMask<KS>::NW; ++i) alive.w[i] &= matched.w[i];
-}
-
-// Global form (few survivors left): planes and codes read through the read-only path.
-template <int KS>
-__device__ __forceinline__ void scan_group_global(const uint2* __restrict__ planes,
-                                                  const uint64_t* __restrict__ codes, int wpad,
-                                                  int d, uint32_t Ep, uint32_t Op,
-                                                  const uint64_t* ball, GroupMask<KS>& alive) {
-  GroupMask<KS> matched;
-#pragma unroll
-  for (int i = 0; i < GroupMask<KS>::NW; ++i) matched.w[i] = 0;
-  const uint4* p4 = reinterpret_cast<const uint4*>(planes);
-  const uint64_t smask = (1ull << (2 * KS)) - 1;
-  for (int q = 0; q < (wpad >> 1); ++q) {
-    const uint4 a = __ldg(p4 + q);
-    const int h0 = __popc((Ep ^ (a.x >> KS)) | (Op ^ (a.y >> KS)));
-    const int h1 = __popc((Ep ^ (a.z >> KS)) | (Op ^ (a.w >> KS)));
-    if (min(h0, h1) <= d) {
-      if (h0 <= d) group_hit<KS, true>(matched, ball, d, h0, (int)(__ldg(codes + 2 * q) & smask));
-      if (h1 <= d)
-        group_hit<KS, true>(matched, ball, d, h1, (int)(__ldg(codes + 2 * q + 1) & smask));
-      if (covers<KS>(matched, alive)) break;
-    }
-  }
+  flush_hits<KS>(matched, hl, hstride, cnt, sfx, ball);
 #pragma unroll
   for (int i = 0; i < GroupMask<KS>::NW; ++i) alive.w[i] &= matched.w[i];
 }
@@ -314,13 +348,11 @@ __device__ __forceinline__ void range_mask(uint64_t g, uint64_t lo, uint64_t hi,
     const int wbits = BITS < 64 ? BITS : 64;
     uint64_t word = wbits == 64 ? ~0ull : ((1ull << wbits) - 1);
     const uint64_t wlo = first + (uint64_t)i * 64;  // code of bit 0 of this word
-    // clear bits below lo
-    if (lo > wlo) {
+    if (lo > wlo) {  // clear bits below lo
       const uint64_t k = lo - wlo;
       word = k >= 64 ? 0 : (word & (~0ull << k));
     }
-    // clear bits at or above hi
-    if (hi < wlo + (uint64_t)wbits) {
+    if (hi < wlo + (uint64_t)wbits) {  // clear bits at or above hi
       const uint64_t k = hi > wlo ? hi - wlo : 0;
       word = k == 0 ? 0 : (word & (~0ull >> (64 - k)));
     }
@@ -328,10 +360,32 @@ __device__ __forceinline__ void range_mask(uint64_t g, uint64_t lo, uint64_t hi,
   }
 }
 
+// Appends the accepted codes of `alive` (group g) to the output; all 32 lanes call it.
+template <int KS>
+__device__ __forceinline__ void group_output(const JobDesc& jd, JobState* st, uint64_t g,
+                                             const GroupMask<KS>& alive) {
+  constexpr int NW = GroupMask<KS>::NW;
+  unsigned cnt = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) cnt += __popcll(alive.w[i]);
+  unsigned long long slot = warp_reserve(&st->out_count, cnt);
+  const uint64_t first = g << (2 * KS);
+#pragma unroll
+  for (int i = 0; i < NW; ++i) {
+    uint64_t w = alive.w[i];
+    while (w) {
+      const int b = __ffsll((long long)w) - 1;
+      w &= w - 1;
+      if (slot < jd.out_cap) jd.out[slot] = first + (uint64_t)i * 64 + b;
+      ++slot;
+    }
+  }
+}
+
 template <int KS>
 __device__ void group_tile(const JobDesc& jd, JobState* st, const Pass& p,
                            unsigned long long base, const uint4* stage_wp,
-                           const uint16_t* stage_sfx, const uint64_t* stage_ball) {
+                           const uint16_t* stage_sfx, const uint64_t* stage_ball, uint32_t* hl) {
   constexpr int NW = GroupMask<KS>::NW;
   const int lane = threadIdx.x & 31;
   const unsigned long long item = base + lane;
@@ -340,7 +394,7 @@ __device__ void group_tile(const JobDesc& jd, JobState* st, const Pass& p,
 #pragma unroll
   for (int i = 0; i < NW; ++i) alive.w[i] = 0;
   if (item < p.work) {
-    if (p.fresh) {
+    if (p.mode == kFresh) {
       off = (uint32_t)item;
       range_mask<KS>(p.chunk_base + off, jd.lo, jd.hi, alive);
     } else {
@@ -353,32 +407,13 @@ __device__ void group_tile(const JobDesc& jd, JobState* st, const Pass& p,
   }
   const int wpad = jd.wstride;
   for (int s = p.s0; s < p.s1 && any_set<KS>(alive); ++s) {
-    if (p.staged) {
-      const int r = s - p.s0;
-      scan_group_staged<KS>(stage_wp + (size_t)r * (wpad >> 1), stage_sfx + (size_t)r * wpad, wpad,
-                            jd.d, Ep, Op, stage_ball, alive);
-    } else {
-      scan_group_global<KS>(jd.planes + (size_t)s * wpad, jd.codes + (size_t)s * wpad, wpad, jd.d,
-                            Ep, Op, jd.ball, alive);
-    }
+    const int r = s - p.s0;
+    scan_group_staged<KS>(stage_wp + (size_t)r * (wpad >> 1), stage_sfx + (size_t)r * wpad, wpad,
+                          jd.d, Ep, Op, stage_ball, hl, blockDim.x, alive);
   }
   __syncwarp();
   if (p.s1 >= jd.n) {
-    unsigned cnt = 0;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) cnt += __popcll(alive.w[i]);
-    unsigned long long slot = warp_reserve(&st->out_count, cnt);
-    const uint64_t first = (p.chunk_base + off) << (2 * KS);
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      uint64_t w = alive.w[i];
-      while (w) {
-        const int b = __ffsll((long long)w) - 1;
-        w &= w - 1;
-        if (slot < jd.out_cap) jd.out[slot] = first + (uint64_t)i * 64 + b;
-        ++slot;
-      }
-    }
+    group_output<KS>(jd, st, p.chunk_base + off, alive);
   } else {
     const unsigned cnt = any_set<KS>(alive) ? 1u : 0u;
     const unsigned long long slot = warp_reserve(&st->qcount[p.qout], cnt);
@@ -391,19 +426,68 @@ __device__ void group_tile(const JobDesc& jd, JobState* st, const Pass& p,
   }
 }
 
+// REST: the warp owns one queue entry; lanes stride over each remaining sequence's windows in
+// global memory, OR their hits locally, and the warp combines the masks.
+template <int KS>
+__device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsigned long long item,
+                           const uint64_t* stage_ball) {
+  constexpr int NW = GroupMask<KS>::NW;
+  const int lane = threadIdx.x & 31;
+  const uint32_t off = jd.qidx[p.qin][item];
+  const uint64_t g = p.chunk_base + off;
+  GroupMask<KS> alive;
+  const uint64_t* src = jd.qmask[p.qin] + item * NW;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) alive.w[i] = src[i];
+  uint32_t Ep, Op;
+  code_planes(g, Ep, Op);
+  const uint64_t smask = (1ull << (2 * KS)) - 1;
+  for (int s = p.s0; s < jd.n && any_set<KS>(alive); ++s) {
+    const uint2* row = jd.planes + (size_t)s * jd.wstride;
+    const uint64_t* crow = jd.codes + (size_t)s * jd.wstride;
+    GroupMask<KS> matched;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) matched.w[i] = 0;
+    for (int j = lane; j < jd.W; j += 32) {
+      const uint2 w = __ldg(row + j);
+      const int h = __popc((Ep ^ (w.x >> KS)) | (Op ^ (w.y >> KS)));
+      if (h <= jd.d)
+        group_hit<KS, false>(matched, stage_ball, jd.d, h, (int)(__ldg(crow + j) & smask));
+    }
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      uint64_t v = matched.w[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(kFull, v, o);
+      alive.w[i] &= v;
+    }
+  }
+  if (lane != 0) {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) alive.w[i] = 0;
+  }
+  group_output<KS>(jd, st, g, alive);
+}
+
 // ---------------------------------------------------------------------------------------------
 // The step kernel.
 
 // KIND = MOTIF_KERNEL_CAND with P = candidates per lane, or MOTIF_KERNEL_GROUP with P = ks.
+// Shared memory: staged windows of the pass (CAND: planes; GROUP: prefix planes, suffix values,
+// the ball table and one hit list per thread).
 template <int KIND, int P>
-__global__ void __launch_bounds__(256) step_kernel(const JobDesc* __restrict__ jobs,
-                                                   JobState* states, int njobs, StepCtl* ctl) {
+__global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restrict__ jobs,
+                                                         JobState* states, int njobs,
+                                                         StepCtl* ctl,
+                                                         cudaGraphConditionalHandle cond,
+                                                         int use_cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ JobDesc s_jd;
   __shared__ Pass s_pass;
   __shared__ int s_skip;
   __shared__ unsigned s_tiles;
   __shared__ int s_last;
+  __shared__ unsigned s_act[kMaxBlock / 32];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const unsigned budget = ctl->tiles_per_warp * (blockDim.x >> 5);
@@ -426,38 +510,40 @@ __global__ void __launch_bounds__(256) step_kernel(const JobDesc* __restrict__ j
     const Pass p = s_pass;
     JobState* st = &states[j];
     const int wpad = jd.wstride;
-    const int nst = p.staged ? p.s1 - p.s0 : 0;
+    const int nst = p.mode == kRest ? 0 : p.s1 - p.s0;
 
-    // Stage the windows of the pass (and the ball table) in shared memory.
+    // Stage the windows of the pass (and, for GROUP, the ball table) in shared memory.
     const uint4* stage4 = reinterpret_cast<const uint4*>(smem);
     const uint16_t* stage_sfx = nullptr;
     const uint64_t* stage_ball = nullptr;
+    uint32_t* hits = nullptr;
     if (KIND == MOTIF_KERNEL_CAND) {
       uint4* dst = reinterpret_cast<uint4*>(smem);
       const uint4* src = reinterpret_cast<const uint4*>(jd.planes + (size_t)p.s0 * wpad);
       for (int i = tid; i < nst * (wpad >> 1); i += blockDim.x) dst[i] = src[i];
     } else {
+      const size_t wp_bytes = (size_t)kMaxStageSeqs * wpad * 8;
+      size_t ball_off = wp_bytes + (size_t)kMaxStageSeqs * wpad * 2;
+      ball_off += 16 - ball_off % 16;
+      const int bw = ball_table_words(P);
       uint2* dwp = reinterpret_cast<uint2*>(smem);
-      uint16_t* dsfx = reinterpret_cast<uint16_t*>(smem + (size_t)kMaxStageSeqs * wpad * 8);
-      uint64_t* dball =
-          reinterpret_cast<uint64_t*>(smem + (size_t)kMaxStageSeqs * wpad * 10 + 16 -
-                                      ((size_t)kMaxStageSeqs * wpad * 10) % 16);
+      uint16_t* dsfx = reinterpret_cast<uint16_t*>(smem + wp_bytes);
+      uint64_t* dball = reinterpret_cast<uint64_t*>(smem + ball_off);
       const uint64_t smask = (1ull << (2 * P)) - 1;
       for (int i = tid; i < nst * wpad; i += blockDim.x) {
         const uint2 pl = jd.planes[(size_t)p.s0 * wpad + i];
         dwp[i] = make_uint2(pl.x >> P, pl.y >> P);
         dsfx[i] = (uint16_t)(jd.codes[(size_t)p.s0 * wpad + i] & smask);
       }
-      const int bw = ball_table_words(P);
       for (int i = tid; i < bw; i += blockDim.x) dball[i] = jd.ball[i];
       stage_sfx = dsfx;
       stage_ball = dball;
+      hits = reinterpret_cast<uint32_t*>(smem + ball_off + (size_t)bw * 8) + tid;
     }
     __syncthreads();
 
-    // Pull 32-unit tiles (32*cpt candidates for a fresh CAND pass) until the pass is exhausted.
-    const unsigned long long tile =
-        (KIND == MOTIF_KERNEL_CAND && p.fresh) ? 32ull * P : 32ull;
+    // Pull tiles until the pass is exhausted (or the step's tile budget is spent).
+    const unsigned long long tile = tile_of(KIND, P, p.mode);
     for (;;) {
       unsigned long long base = 0;
       int stop = 0;
@@ -473,10 +559,12 @@ __global__ void __launch_bounds__(256) step_kernel(const JobDesc* __restrict__ j
       if (stop) break;
       base = __shfl_sync(kFull, base, 0);
       if (KIND == MOTIF_KERNEL_CAND) {
-        if (p.fresh) cand_tile<P>(jd, st, p, base, stage4);
+        if (p.mode == kRest) cand_rest(jd, st, p, base);
+        else if (p.mode == kFresh) cand_tile<P>(jd, st, p, base, stage4);
         else cand_tile<1>(jd, st, p, base, stage4);
       } else {
-        group_tile<P>(jd, st, p, base, stage4, stage_sfx, stage_ball);
+        if (p.mode == kRest) group_rest<P>(jd, st, p, base, stage_ball);
+        else group_tile<P>(jd, st, p, base, stage4, stage_sfx, stage_ball, hits);
       }
     }
   }
@@ -516,18 +604,40 @@ __global__ void __launch_bounds__(256) step_kernel(const JobDesc* __restrict__ j
     }
     if (!ld_volatile(&st->done)) ++active;
   }
-  // Block-wide sum of `active`.
   for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(kFull, active, o);
-  __shared__ unsigned s_act[32];
   if (lane == 0) s_act[tid >> 5] = active;
   __syncthreads();
   if (tid == 0) {
     unsigned tot = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_act[w];
+    const unsigned steps = ctl->steps + 1;
     ctl->active_jobs = tot;
-    ctl->steps += 1;
+    ctl->steps = steps;
     __threadfence();
     ctl->ctas_done = 0;
+    if (use_cond) {
+      // Inside a graph's while loop: run another step while work remains, never beyond the
+      // step bound (which ends the loop even if a job failed to complete).
+      const bool more = tot > 0 && (ctl->max_steps == 0 || steps < ctl->max_steps);
+      cudaGraphSetConditional(cond, more ? 1u : 0u);
+    }
+  }
+}
+
+// Resets the states of a job table and its step control block.
+__global__ void init_steps_kernel(JobState* states, int njobs, StepCtl* ctl, unsigned max_steps,
+                                  unsigned tiles_per_warp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < njobs) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(&states[i]);
+    for (int k = 0; k < (int)(sizeof(JobState) / 8); ++k) w[k] = 0;
+  }
+  if (i == 0) {
+    ctl->ctas_done = 0;
+    ctl->tiles_per_warp = tiles_per_warp;
+    ctl->active_jobs = (unsigned)njobs;
+    ctl->steps = 0;
+    ctl->max_steps = max_steps;
   }
 }
 
@@ -629,12 +739,6 @@ __global__ void ball_kernel(uint64_t* table, int ks) {
   }
 }
 
-template <int KIND, int P>
-cudaError_t step_launch_t(const JobDesc* d_jobs, JobState* d_states, int njobs, StepCtl* d_ctl,
-                          int grid, int block, size_t smem, cudaStream_t s) {
-  step_kernel<KIND, P><<<grid, block, smem, s>>>(d_jobs, d_states, njobs, d_ctl);
-  return cudaGetLastError();
-}
 
 template <int KIND, int P>
 const void* step_fn() {
@@ -663,17 +767,26 @@ const void* step_function(int kind, int p) {
 
 bool step_variant_ok(int kind, int p) { return step_function(kind, p) != nullptr; }
 
-size_t step_smem_bytes(int kind, int p, int wstride) {
+size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
-  return b + (size_t)ball_table_words(p) * 8;
+  b += (size_t)ball_table_words(p) * 8;
+  return b + (size_t)kHitCap * block * 4;
 }
 
+// Raises (never lowers) a variant's dynamic shared memory limit: plans, batches and the server
+// share the kernels, and one caller's smaller request must not break another's launch.
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem) {
+  static std::mutex mu;
+  static size_t set[3][kMaxKs + 1] = {};
   const void* f = step_function(kind, p);
-  if (!f) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!f || kind < 1 || kind > 2 || p < 1 || p > kMaxKs) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> g(mu);
+  if (smem <= set[kind][p]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) set[kind][p] = smem;
+  return e;
 }
 
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem) {
@@ -686,21 +799,77 @@ int step_max_ctas_per_sm(int kind, int p, int block, size_t smem) {
 
 cudaError_t launch_step(int kind, int p, const JobDesc* d_jobs, JobState* d_states, int njobs,
                         StepCtl* d_ctl, int grid, int block, size_t smem, cudaStream_t s) {
-  if (kind == MOTIF_KERNEL_CAND) {
-    switch (p) {
-      case 1: return step_launch_t<MOTIF_KERNEL_CAND, 1>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-      case 2: return step_launch_t<MOTIF_KERNEL_CAND, 2>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-      case 4: return step_launch_t<MOTIF_KERNEL_CAND, 4>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-    }
-  } else if (kind == MOTIF_KERNEL_GROUP) {
-    switch (p) {
-      case 1: return step_launch_t<MOTIF_KERNEL_GROUP, 1>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-      case 2: return step_launch_t<MOTIF_KERNEL_GROUP, 2>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-      case 3: return step_launch_t<MOTIF_KERNEL_GROUP, 3>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-      case 4: return step_launch_t<MOTIF_KERNEL_GROUP, 4>(d_jobs, d_states, njobs, d_ctl, grid, block, smem, s);
-    }
-  }
-  return cudaErrorInvalidValue;
+  const void* f = step_function(kind, p);
+  if (!f) return cudaErrorInvalidValue;
+  cudaGraphConditionalHandle none = 0;
+  int use_cond = 0;
+  void* args[] = {(void*)&d_jobs, (void*)&d_states, (void*)&njobs, (void*)&d_ctl, (void*)&none,
+                  (void*)&use_cond};
+  note_launches(1);
+  return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t add_step_node(cudaGraph_t g, int kind, int p, const JobDesc* d_jobs,
+                          JobState* d_states, int njobs, StepCtl* d_ctl, int grid, int block,
+                          size_t smem, cudaGraphConditionalHandle cond, int use_cond,
+                          cudaGraphNode_t* node) {
+  const void* f = step_function(kind, p);
+  if (!f) return cudaErrorInvalidValue;
+  void* args[] = {(void*)&d_jobs, (void*)&d_states, (void*)&njobs, (void*)&d_ctl, (void*)&cond,
+                  (void*)&use_cond};
+  cudaKernelNodeParams kp = {};
+  kp.func = const_cast<void*>(f);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, nullptr, 0, &kp);
+}
+
+cudaError_t launch_init_steps(JobState* d_states, int njobs, StepCtl* d_ctl, unsigned max_steps,
+                              unsigned tiles_per_warp, cudaStream_t s) {
+  init_steps_kernel<<<(njobs + 255) / 256, 256, 0, s>>>(d_states, njobs, d_ctl, max_steps,
+                                                        tiles_per_warp);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl* d_ctl,
+                          unsigned max_steps, unsigned tiles_per_warp, cudaGraphNode_t* node) {
+  void* args[] = {(void*)&d_states, (void*)&njobs, (void*)&d_ctl, (void*)&max_steps,
+                  (void*)&tiles_per_warp};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)init_steps_kernel;
+  kp.gridDim = dim3((njobs + 255) / 256);
+  kp.blockDim = dim3(256);
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, nullptr, 0, &kp);
+}
+
+cudaError_t build_step_graph(int kind, int p, const JobDesc* d_jobs, JobState* d_states,
+                             int njobs, StepCtl* d_ctl, int grid, int block, size_t smem,
+                             unsigned max_steps, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphNode_t init;
+  e = add_init_node(g, d_states, njobs, d_ctl, max_steps, 0, &init);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&loop, g, &init, nullptr, 1, &cp);
+  cudaGraphNode_t step;
+  if (e == cudaSuccess)
+    e = add_step_node(cp.conditional.phGraph_out[0], kind, p, d_jobs, d_states, njobs, d_ctl, grid,
+                      block, smem, h, 1, &step);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e;
 }
 
 cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,

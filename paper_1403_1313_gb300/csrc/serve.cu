@@ -43,6 +43,8 @@ struct Job {
   void* sort = nullptr;
   size_t sort_bytes = 0;
   int64_t footprint = 0;
+  const uint64_t* ball = nullptr;     // Hamming-ball table for pv on the server's device
+  cudaEvent_t ready = nullptr;        // recorded after the window copies (submit stream)
   double t_submit = 0, t_admit = 0, t_done = 0, gpu_ms = 0;
   int status = MOTIF_OK;
   bool done = false;
@@ -56,7 +58,9 @@ struct Server {
   bool running = false, stopping = false;
   motif_server_opts o{};
   int device = 0, sms = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;         // scheduler thread only
+  cudaStream_t submit_stream = nullptr;  // client threads (window copies); guarded by submit_mu
+  std::mutex submit_mu;
   std::deque<Job*> queue;
   std::vector<Job*> active;       // table order = admission order
   std::map<int64_t, Job*> jobs;   // every job not yet released by motif_poll
@@ -88,6 +92,31 @@ void sfree(Server* S, void* p) {
   if (p) cudaFreeAsync(p, S->stream);
 }
 
+void release_windows_from_client(Server* S, Job* j) {
+  std::lock_guard<std::mutex> g(S->submit_mu);
+  if (j->planes) cudaFreeAsync(j->planes, S->submit_stream);
+  if (j->codes) cudaFreeAsync(j->codes, S->submit_stream);
+  j->planes = nullptr;
+  j->codes = nullptr;
+  if (j->ready) cudaEventDestroy(j->ready);
+  j->ready = nullptr;
+}
+
+// Queues, output and sort scratch: held only while the job is admitted.
+void release_run_buffers(Server* S, Job* j) {
+  for (int i = 0; i < 2; ++i) {
+    sfree(S, j->qidx[i]);
+    sfree(S, j->qmask[i]);
+    j->qidx[i] = nullptr;
+    j->qmask[i] = nullptr;
+  }
+  sfree(S, j->out);
+  sfree(S, j->sort);
+  j->out = nullptr;
+  j->sort = nullptr;
+}
+
+// Everything, including the job's private window copies.
 void release_buffers(Server* S, Job* j) {
   for (int i = 0; i < 2; ++i) {
     sfree(S, j->qidx[i]);
@@ -103,6 +132,8 @@ void release_buffers(Server* S, Job* j) {
   j->sort = nullptr;
   j->planes = nullptr;
   j->codes = nullptr;
+  if (j->ready) cudaEventDestroy(j->ready);
+  j->ready = nullptr;
 }
 
 int64_t footprint_of(const Job* j) {
@@ -132,6 +163,7 @@ void fill_job_desc(const Job* j, JobDesc* jd) {
   jd->qmask[0] = j->qmask[0]; jd->qmask[1] = j->qmask[1];
   jd->qcap = j->qcap;
   jd->out = j->out; jd->out_cap = (uint64_t)j->out_cap;
+  jd->ball = j->ball;
 }
 
 int max_active(const Server* S) { return S->o.max_active > 0 ? S->o.max_active : 64; }
@@ -151,14 +183,20 @@ int prepare_launch(Server* S, int kind, int pv, size_t smem) {
   if (S->exec) { cudaGraphExecDestroy(S->exec); S->exec = nullptr; }
   if (S->graph) { cudaGraphDestroy(S->graph); S->graph = nullptr; }
   if (S->o.use_graph) {
-    cudaError_t e = cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal);
+    // One step-kernel node, built explicitly (no stream capture, so client threads can never
+    // leak work into the graph).
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess)
-      e = launch_step(kind, pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl, S->grid,
-                      S->block, S->smem, S->stream);
-    cudaError_t e2 = cudaStreamEndCapture(S->stream, &S->graph);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->exec, S->graph, 0);
-    if (e != cudaSuccess) return status_from_cuda(e);
+      e = add_step_node(g, kind, pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl, S->grid,
+                        S->block, S->smem, 0, 0, &node);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      S->exec = nullptr;
+      return status_from_cuda(e);
+    }
   }
   return MOTIF_OK;
 }
@@ -236,8 +274,9 @@ void scheduler(Server* S) {
       j->footprint = footprint_of(j);
       if (!S->active.empty() && S->budget_used + j->footprint > budget) break;
       if (!allocate_job(S, j)) {
-        release_buffers(S, j);
+        release_run_buffers(S, j);  // keeps the window copies: the job stays queued
         if (S->active.empty()) {  // cannot ever fit: fail the job
+          release_buffers(S, j);
           S->queue.pop_front();
           j->status = MOTIF_ERR_OOM;
           j->done = true;
@@ -248,6 +287,7 @@ void scheduler(Server* S) {
         break;
       }
       S->queue.pop_front();
+      if (j->ready) cudaStreamWaitEvent(S->stream, j->ready, 0);  // its windows are copied
       if (prepare_launch(S, j->kind, j->pv, j->smem) != MOTIF_OK) {
         release_buffers(S, j);
         j->status = MOTIF_ERR_CUDA;
@@ -283,10 +323,13 @@ void scheduler(Server* S) {
     cudaError_t e = cudaMemcpyAsync(S->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, S->stream);
     cudaEventRecord(S->ev0, S->stream);
     if (e == cudaSuccess) {
-      if (S->exec) e = cudaGraphLaunch(S->exec, S->stream);
-      else e = launch_step(S->kind, S->pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl,
-                           S->grid, S->block, S->smem, S->stream);
-      note_launches(1);
+      if (S->exec) {
+        e = cudaGraphLaunch(S->exec, S->stream);
+        note_launches(1);
+      } else {
+        e = launch_step(S->kind, S->pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl,
+                        S->grid, S->block, S->smem, S->stream);
+      }
     }
     cudaEventRecord(S->ev1, S->stream);
     std::vector<JobState> st(nact);
@@ -367,6 +410,7 @@ int start_locked(const motif_server_opts* opts) {
   S->sms = prop.multiProcessorCount;
   const int cap = max_active(S);
   if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->submit_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&S->d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
       cudaMalloc(&S->d_states, sizeof(JobState) * cap) != cudaSuccess ||
       cudaMalloc(&S->d_ctl, sizeof(StepCtl)) != cudaSuccess ||
@@ -416,6 +460,8 @@ extern "C" int motif_server_stop(void) {
   cudaFree(S->d_ctl);
   cudaEventDestroy(S->ev0);
   cudaEventDestroy(S->ev1);
+  cudaStreamSynchronize(S->submit_stream);
+  cudaStreamDestroy(S->submit_stream);
   cudaStreamDestroy(S->stream);
   delete S;
   return MOTIF_OK;
@@ -451,7 +497,7 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   j->kind = MOTIF_KERNEL_GROUP;
   j->pv = std::min(kMaxKs, p->l);
   j->span0 = j->pv >= 3 ? 2 : 1;
-  j->smem = step_smem_bytes(j->kind, j->pv, std::max(j->wstride, kWinAlign));
+  j->smem = step_smem_bytes(j->kind, j->pv, std::max(j->wstride, kWinAlign), 256);
   j->lo = p->lo; j->hi = p->hi;
   const int shift = 2 * j->pv;
   j->unit_lo = j->lo >> shift;
@@ -463,25 +509,29 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   j->words = mask_words(j->pv);
   j->rest = (uint64_t)8 * 32 * S->sms;
   if (j->nchunks > 0) {
-    if (!ball_table(S->device, j->pv, S->stream)) { delete j; return MOTIF_ERR_CUDA; }
-    // Private copies of the packed windows, made on the server stream (which every later use of
-    // them is ordered after); the plan's stream waits for the copies, so the plan may be reused
-    // or destroyed as soon as this returns.
+    std::lock_guard<std::mutex> sg(S->submit_mu);
+    j->ball = ball_table(S->device, j->pv, S->submit_stream);
+    if (!j->ball) { delete j; return MOTIF_ERR_CUDA; }
+    // Private copies of the packed windows, made on the submit stream; the scheduler's stream
+    // waits for `ready` before the job's first step, and the plan's stream waits for it too, so
+    // the plan may be reused or destroyed as soon as this returns.
     j->win_bytes = (size_t)j->n * j->wstride * 8;
-    j->planes = (uint2*)salloc(S, j->win_bytes);
-    j->codes = (uint64_t*)salloc(S, j->win_bytes);
-    cudaEvent_t copied = nullptr;
-    cudaError_t e = (j->planes && j->codes) ? cudaSuccess : cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMallocAsync((void**)&j->planes, j->win_bytes, S->submit_stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&j->codes, j->win_bytes, S->submit_stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(j->planes, p->d_planes, j->win_bytes, cudaMemcpyDeviceToDevice, S->stream);
+      e = cudaMemcpyAsync(j->planes, p->d_planes, j->win_bytes, cudaMemcpyDeviceToDevice,
+                          S->submit_stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(j->codes, p->d_codes, j->win_bytes, cudaMemcpyDeviceToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(copied, S->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, copied, 0);
-    if (copied) cudaEventDestroy(copied);
+      e = cudaMemcpyAsync(j->codes, p->d_codes, j->win_bytes, cudaMemcpyDeviceToDevice,
+                          S->submit_stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ready, S->submit_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, j->ready, 0);
     if (e != cudaSuccess) {
-      release_buffers(S, j);
+      cudaGetLastError();
+      if (j->planes) cudaFreeAsync(j->planes, S->submit_stream);
+      if (j->codes) cudaFreeAsync(j->codes, S->submit_stream);
+      if (j->ready) cudaEventDestroy(j->ready);
       delete j;
       return status_from_cuda(e);
     }
@@ -489,7 +539,7 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   std::lock_guard<std::mutex> lk(S->mu);
   const int max_q = S->o.max_queued > 0 ? S->o.max_queued : 4096;
   if ((int)S->queue.size() >= max_q) {
-    release_buffers(S, j);
+    release_windows_from_client(S, j);
     delete j;
     return MOTIF_ERR_BUSY;
   }

@@ -30,10 +30,14 @@ __device__ __forceinline__ unsigned long long read_count(const unsigned long lon
 
 __global__ void __launch_bounds__(kSmallThreads) small_sort_kernel(uint64_t* codes,
                                                                    unsigned long long* count,
-                                                                   long long cap) {
+                                                                   long long cap,
+                                                                   cudaGraphConditionalHandle cond,
+                                                                   int use_cond) {
   __shared__ uint64_t a[kSmallMax];
   __shared__ unsigned warp_tot[kSmallThreads / 32];
   const unsigned long long n = read_count(count);
+  if (use_cond && threadIdx.x == 0)  // inside a graph: run the multi-CTA path only when needed
+    cudaGraphSetConditional(cond, (n > (unsigned long long)kSmallMax && n <= (unsigned long long)cap) ? 1u : 0u);
   if (n <= 1 || n > (unsigned long long)kSmallMax || n > (unsigned long long)cap) return;
   int size = 2;
   while ((unsigned long long)size < n) size <<= 1;
@@ -278,7 +282,7 @@ cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, i
   const bool want_small = known_count < 0 || (known_count > 1 && known_count <= kSmallMax);
   const bool want_large = known_count < 0 || (known_count > kSmallMax && known_count <= cap);
   if (want_small) {
-    small_sort_kernel<<<1, kSmallThreads, 0, s>>>(d_codes, d_count, cap);
+    small_sort_kernel<<<1, kSmallThreads, 0, s>>>(d_codes, d_count, cap, 0, 0);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -308,6 +312,98 @@ cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, i
   store_count_kernel<<<1, 32, 0, s>>>(d_count, cap, scanned, raw, ctas);
   note_launches(3 * passes + 5);
   return cudaGetLastError();
+}
+
+// Graph form of launch_sort_unique: the one-CTA kernel runs unconditionally and sets an IF
+// condition; the multi-CTA path is the body of that IF node, so it costs nothing when the count
+// fits the one-CTA path.  *last receives the final node.
+cudaError_t add_sort_nodes(cudaGraph_t g, cudaGraphNode_t dep, uint64_t* d_codes,
+                           unsigned long long* d_count, int64_t cap, int key_bits, void* scratch,
+                           int sms, cudaGraphNode_t* last) {
+  const bool large = cap > kSmallMax && scratch != nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaError_t e = cudaSuccess;
+  if (large) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNode_t small;
+  {
+    long long capv = cap;
+    int use = large ? 1 : 0;
+    void* args[] = {(void*)&d_codes, (void*)&d_count, (void*)&capv, (void*)&h, (void*)&use};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)small_sort_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(kSmallThreads);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&small, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+    if (e != cudaSuccess) return e;
+  }
+  if (!large) {  // the count can never need the multi-CTA path
+    *last = small;
+    return cudaSuccess;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t ifnode;
+  e = cudaGraphAddNode(&ifnode, g, &small, nullptr, 1, &cp);
+  if (e != cudaSuccess) return e;
+  *last = ifnode;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const int ctas = radix_ctas(sms);
+  uint64_t* alt = reinterpret_cast<uint64_t*>(scratch);
+  unsigned* hist = reinterpret_cast<unsigned*>(alt + cap);
+  unsigned* raw = hist + (size_t)kDigits * ctas;
+  unsigned* scanned = raw + ctas;
+  long long capv = cap;
+  cudaGraphNode_t prev = nullptr;
+  auto add = [&](void* func, int grid, int block, void** args) -> cudaError_t {
+    cudaKernelNodeParams kp = {};
+    kp.func = func;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.kernelParams = args;
+    cudaGraphNode_t n;
+    cudaError_t r = cudaGraphAddKernelNode(&n, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+    prev = n;
+    return r;
+  };
+  uint64_t* a = d_codes;
+  uint64_t* b = alt;
+  const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+  for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
+    int shift = pass * kRadixBits;
+    int len = kDigits * ctas, need = 1;
+    void* ha[] = {(void*)&a, (void*)&d_count, (void*)&capv, (void*)&shift, (void*)&hist};
+    e = add((void*)radix_hist_kernel, ctas, kRadixThreads, ha);
+    void* sa[] = {(void*)&hist, (void*)&len, (void*)&d_count, (void*)&capv, (void*)&need};
+    if (e == cudaSuccess) e = add((void*)scan_kernel, 1, kRadixThreads, sa);
+    void* xa[] = {(void*)&a, (void*)&b, (void*)&d_count, (void*)&capv, (void*)&shift, (void*)&hist};
+    if (e == cudaSuccess) e = add((void*)radix_scatter_kernel, ctas, kRadixThreads, xa);
+    uint64_t* tmp = a; a = b; b = tmp;
+  }
+  if (e != cudaSuccess) return e;
+  int ctas_i = ctas, need = 1;
+  void* ua[] = {(void*)&a, (void*)&d_count, (void*)&capv, (void*)&raw};
+  e = add((void*)unique_count_kernel, ctas, kRadixThreads, ua);
+  if (e != cudaSuccess) return e;
+  cudaGraphNode_t cpy;
+  e = cudaGraphAddMemcpyNode1D(&cpy, body, &prev, 1, scanned, raw, sizeof(unsigned) * ctas,
+                               cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) return e;
+  prev = cpy;
+  void* sa2[] = {(void*)&scanned, (void*)&ctas_i, (void*)&d_count, (void*)&capv, (void*)&need};
+  e = add((void*)scan_kernel, 1, kRadixThreads, sa2);
+  void* wa[] = {(void*)&a, (void*)&b, (void*)&d_count, (void*)&capv, (void*)&scanned};
+  if (e == cudaSuccess) e = add((void*)unique_write_kernel, ctas, kRadixThreads, wa);
+  void* fa[] = {(void*)&b, (void*)&d_codes, (void*)&d_count, (void*)&capv, (void*)&scanned,
+                (void*)&raw, (void*)&ctas_i};
+  if (e == cudaSuccess) e = add((void*)unique_finish_kernel, ctas, kRadixThreads, fa);
+  void* ca[] = {(void*)&d_count, (void*)&capv, (void*)&scanned, (void*)&raw, (void*)&ctas_i};
+  if (e == cudaSuccess) e = add((void*)store_count_kernel, 1, 32, ca);
+  return e;
 }
 
 }  // namespace motif

@@ -1,0 +1,98 @@
+"""Serving (continuous batching) on the GPU: jobs submitted while others run are admitted into
+the shared job table; every result equals the oracle's and the result of the same job served
+alone (exact equality: the result is an integer set)."""
+import random
+
+import numpy as np
+import pytest
+
+import paper_1403_1313_gb300 as m
+from oracle import oracle
+from paper_1403_1313_gb300 import fmgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def server():
+    from paper_1403_1313_gb300 import build
+    build.build()
+    yield
+    try:
+        m.motif_server_stop()
+    except m.MotifError:
+        pass
+
+
+def _submit(job):
+    plan = m.motif_plan_create(job.n, job.t, job.l, job.d)
+    m.motif_load_seqs(plan, job.seqs)
+    jid = m.motif_submit(plan)
+    m.motif_plan_destroy(plan)  # the job keeps its own copy of the windows
+    return jid
+
+
+def _mix(seed, count):
+    rng = random.Random(seed)
+    jobs = []
+    for j in range(count):
+        l = rng.randint(7, 10)
+        d = rng.randint(1, 3)
+        jobs.append(fmgen.fm_job(rng.randint(3, 9), rng.randint(40, 240), l, d, 900 + j,
+                                 gc=rng.choice([0.4, 0.5, 0.6])))
+    return jobs
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_mix_equals_oracle_and_alone(server, use_graph):
+    # A tiny tile budget per step forces every job to share many steps with the others.
+    m.motif_server_start(max_active=6, step_tiles=64, use_graph=use_graph)
+    jobs = _mix(3, 14)
+    ids = [_submit(j) for j in jobs]
+    mixed = []
+    for jid in ids:
+        res = m.motif_poll(jid, timeout_ms=120000)
+        assert res is not None
+        mixed.append(res[0])
+    for job, got in zip(jobs, mixed):
+        ref, _ = oracle.search(job.rows(), job.l, job.d, threads=8)
+        assert np.array_equal(got, ref)
+        assert m.motif_encode(job.consensus) in set(got.tolist())
+    # The same jobs served alone give identical results.
+    for job, got in zip(jobs[:4], mixed[:4]):
+        alone = m.motif_poll(_submit(job), timeout_ms=120000)[0]
+        assert np.array_equal(alone, got)
+
+
+def test_poll_states(server):
+    m.motif_server_start(max_active=2)
+    job = fmgen.fm_job(8, 300, 11, 3, 5)
+    jid = _submit(job)
+    first = m.motif_poll(jid, timeout_ms=0)          # may still be pending
+    res = first or m.motif_poll(jid, timeout_ms=120000)
+    assert res is not None
+    codes, stats = res
+    assert m.motif_encode(job.consensus) in set(codes.tolist())
+    assert stats["total_ms"] >= stats["queue_ms"] >= 0
+    with pytest.raises(m.MotifError) as e:           # released after a successful poll
+        m.motif_poll(jid, timeout_ms=0)
+    assert e.value.status == m.ERR_NOTFOUND
+
+
+def test_empty_jobs_complete_immediately(server):
+    m.motif_server_start()
+    job = fmgen.fm_job(2, 5, 8, 1, 1)  # t < l: no windows
+    codes, _ = m.motif_poll(_submit(job), timeout_ms=10000)
+    assert codes.size == 0
+
+
+def test_served_matches_blocking_search_larger(server):
+    m.motif_server_start(max_active=4)
+    jobs = [fmgen.fm_job(12, 400, 13, 3, 70 + i) for i in range(3)]
+    ids = [_submit(j) for j in jobs]
+    for job, jid in zip(jobs, ids):
+        got = m.motif_poll(jid, timeout_ms=120000)[0]
+        plan = m.motif_plan_create(job.n, job.t, job.l, job.d)
+        m.motif_load_seqs(plan, job.seqs)
+        assert np.array_equal(got, m.motif_search(plan))
+        m.motif_plan_destroy(plan)

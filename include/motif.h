@@ -51,9 +51,11 @@ typedef enum {
 
 /* Search kernel selection. */
 typedef enum {
-  MOTIF_KERNEL_AUTO = 0,  /* the plan's tuned choice */
+  MOTIF_KERNEL_AUTO = 0,  /* the plan's tuned choice (TILED where it applies, else GROUP) */
   MOTIF_KERNEL_CAND = 1,  /* one candidate per lane: XOR, pair-fold, POPC, running min */
-  MOTIF_KERNEL_GROUP = 2  /* one (l-k)-base prefix per lane, its 4^k suffixes as a bit mask */
+  MOTIF_KERNEL_GROUP = 2, /* one (l-k)-base prefix per lane, its 4^k suffixes as a bit mask */
+  MOTIF_KERNEL_TILED = 3  /* GROUP with k = 4 whose first pass tiles 256 lanes by a shared
+                             (l-8)-base prefix (needs l >= 8; falls back to GROUP otherwise) */
 } motif_kernel;
 
 typedef struct motif_plan_s* motif_plan;

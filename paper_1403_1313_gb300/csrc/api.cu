@@ -118,6 +118,7 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->ks = p->kind == MOTIF_KERNEL_GROUP ? p->p : 0;
   jd->cpt = p->kind == MOTIF_KERNEL_CAND ? p->p : 1;
   jd->span0 = p->span0;
+  jd->tiled = p->tiled ? 1 : 0;
   jd->lo = p->lo; jd->hi = p->hi;
   jd->unit_lo = p->unit_lo; jd->unit_hi = p->unit_hi;
   jd->chunk_units = p->chunk_units; jd->nchunks = p->nchunks;
@@ -143,6 +144,7 @@ static void free_queues(motif_plan_s* p) {
 int plan_configure(motif_plan_s* p) {
   const motif_opts& o = p->opts;
   // Kernel variant.
+  if (o.kernel < MOTIF_KERNEL_AUTO || o.kernel > MOTIF_KERNEL_TILED) return MOTIF_ERR_ARG;
   int kind = o.kernel == MOTIF_KERNEL_CAND ? MOTIF_KERNEL_CAND : MOTIF_KERNEL_GROUP;
   int pv;
   if (kind == MOTIF_KERNEL_CAND) {
@@ -177,6 +179,11 @@ int plan_configure(motif_plan_s* p) {
   p->want_qcap = chunk;
   p->want_qwords = words;
   invalidate_graphs(p);
+  // The prefix-tiled first pass (GROUP, k = 4): 256 lanes per CTA whose groups share all but
+  // their last 4 prefix bases, so tiles must start on multiples of 256 groups.
+  const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
+  p->tiled = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 && p->l >= 8 &&
+             p->W <= 65535 && unit_lo % 256 == 0 && (chunk % 256 == 0 || units <= chunk);
   p->kind = kind;
   p->p = pv;
   p->span0 = span0;
@@ -187,7 +194,7 @@ int plan_configure(motif_plan_s* p) {
   p->unit_hi = unit_hi;
   p->chunk_units = chunk;
   p->nchunks = units == 0 ? 0 : (units + chunk - 1) / chunk;
-  p->rest_threshold = (uint64_t)8 * 32 * p->sms;
+  p->rest_threshold = (uint64_t)256 * p->sms;
   if (kind == MOTIF_KERNEL_GROUP && !ball_table(p->device, pv, p->stream)) return MOTIF_ERR_CUDA;
   return MOTIF_OK;
 }

@@ -23,6 +23,7 @@ struct JobDesc {
   int32_t ks;                // GROUP: suffix bases per group (1..kMaxKs); CAND: 0
   int32_t cpt;               // CAND: candidates per lane in a fresh pass (1, 2 or 4)
   int32_t span0;             // sequences a fresh pass scans before the first compaction
+  int32_t tiled;             // GROUP k=4: fresh passes use the prefix-tiled form (see search.cu)
   uint64_t lo, hi;           // candidate range [lo, hi)
   uint64_t unit_lo, unit_hi; // work units of the range: candidates (CAND) or groups (GROUP)
   uint64_t chunk_units;      // units per chunk (bounds the queues)

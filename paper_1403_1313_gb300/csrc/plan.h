@@ -21,6 +21,7 @@ struct motif_plan_s {
   int kind = MOTIF_KERNEL_GROUP;
   int p = 4;                 // candidates per lane (CAND) or suffix bases ks (GROUP)
   int span0 = 2;
+  bool tiled = false;        // GROUP k=4 fresh passes use the prefix-tiled form
   int block = 256, grid = 0;
   size_t smem = 0;
   uint64_t lo = 0, hi = 0;   // candidate range

@@ -40,10 +40,10 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxStageSeqs = 2;  // sequences of one pass staged in shared memory
-constexpr int kHitCap = 16;       // GROUP: hit-list entries per lane before a flush
+constexpr int kHitCap = 12;       // GROUP: hit-list entries per lane before a flush
 constexpr int kMaxBlock = 256;
 
-enum PassMode { kFresh = 0, kQueue = 1, kRest = 2 };
+enum PassMode { kFresh = 0, kQueue = 1, kRest = 2, kTiled = 3 };
 
 __device__ __forceinline__ uint32_t compress_even(uint64_t x) {
   x &= 0x5555555555555555ull;
@@ -105,10 +105,10 @@ __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
   const uint64_t left = jd.unit_hi > p.chunk_base ? jd.unit_hi - p.chunk_base : 0;
   p.chunk_units = left < jd.chunk_units ? left : jd.chunk_units;
   if (pass_seq == 0) {
-    p.mode = kFresh;
+    p.mode = jd.tiled ? kTiled : kFresh;
     p.work = p.chunk_units;
     p.s0 = 0;
-    p.s1 = jd.span0 < jd.n ? jd.span0 : jd.n;
+    p.s1 = jd.tiled ? jd.n : (jd.span0 < jd.n ? jd.span0 : jd.n);
     p.qin = 0;
     p.qout = 0;
   } else {
@@ -224,13 +224,12 @@ __device__ void cand_rest(const JobDesc& jd, JobState* st, const Pass& p,
   for (int s = p.s0; s < jd.n; ++s) {
     const uint2* row = jd.planes + (size_t)s * jd.wstride;
     bool matched = false;
-    for (int b = 0; b < jd.W; b += 32) {
-      const int j = b + lane;
-      bool hit = false;
-      if (j < jd.W) {
-        const uint2 w = __ldg(row + j);
-        hit = __popc((E ^ w.x) | (O ^ w.y)) <= jd.d;
-      }
+    for (int b = 0; b < jd.W; b += 64) {  // two loads in flight per lane
+      const int j0 = b + lane, j1 = b + 32 + lane;
+      const uint2 w0 = j0 < jd.W ? __ldg(row + j0) : make_uint2(~E, ~O);
+      const uint2 w1 = j1 < jd.W ? __ldg(row + j1) : make_uint2(~E, ~O);
+      const bool hit = (j0 < jd.W && __popc((E ^ w0.x) | (O ^ w0.y)) <= jd.d) ||
+                       (j1 < jd.W && __popc((E ^ w1.x) | (O ^ w1.y)) <= jd.d);
       if (__any_sync(kFull, hit)) {
         matched = true;
         break;
@@ -259,6 +258,15 @@ __device__ __forceinline__ void or_ball(GroupMask<KS>& matched, const uint64_t* 
                                         int r) {
   constexpr int NW = GroupMask<KS>::NW;
   const uint64_t* row = ball + ((size_t)v * (KS + 1) + r) * NW;
+  if (GLOBAL && NW == 4) {  // 32-byte row: two 128-bit read-only loads
+    const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(row));
+    const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2*>(row) + 1);
+    matched.w[0] |= x.x;
+    matched.w[1 % NW] |= x.y;
+    matched.w[2 % NW] |= y.x;
+    matched.w[3 % NW] |= y.y;
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < NW; ++i) matched.w[i] |= GLOBAL ? __ldg(row + i) : row[i];
 }
@@ -295,7 +303,7 @@ __device__ __forceinline__ void flush_hits(GroupMask<KS>& matched, const uint32_
                                            const uint64_t* ball) {
   for (int i = 0; i < cnt; ++i) {
     const uint32_t e = hl[i * hstride];
-    or_ball<KS, false>(matched, ball, sfx[e >> 3], (int)(e & 7u));
+    or_ball<KS, true>(matched, ball, sfx[e >> 3], (int)(e & 7u));
   }
 }
 
@@ -312,19 +320,27 @@ __device__ __forceinline__ void scan_group_staged(const uint4* __restrict__ wp4,
   for (int i = 0; i < GroupMask<KS>::NW; ++i) matched.w[i] = 0;
   const int n4 = wpad >> 1;
   int cnt = 0;
-  for (int q = 0; q < n4; q += 2) {
-    const uint4 a = wp4[q], b = wp4[q + 1];
-    const int h0 = __popc((Ep ^ a.x) | (Op ^ a.y));
-    const int h1 = __popc((Ep ^ a.z) | (Op ^ a.w));
-    const int h2 = __popc((Ep ^ b.x) | (Op ^ b.y));
-    const int h3 = __popc((Ep ^ b.z) | (Op ^ b.w));
-    if (min(min(h0, h1), min(h2, h3)) <= d) {
+  for (int q = 0; q < n4; q += 4) {  // 8 windows per iteration (rows are padded to 8)
+    const uint4 a = wp4[q], b = wp4[q + 1], c = wp4[q + 2], e = wp4[q + 3];
+    int h[8];
+    h[0] = __popc((Ep ^ a.x) | (Op ^ a.y));
+    h[1] = __popc((Ep ^ a.z) | (Op ^ a.w));
+    h[2] = __popc((Ep ^ b.x) | (Op ^ b.y));
+    h[3] = __popc((Ep ^ b.z) | (Op ^ b.w));
+    h[4] = __popc((Ep ^ c.x) | (Op ^ c.y));
+    h[5] = __popc((Ep ^ c.z) | (Op ^ c.w));
+    h[6] = __popc((Ep ^ e.x) | (Op ^ e.y));
+    h[7] = __popc((Ep ^ e.z) | (Op ^ e.w));
+    const int m = min(min(min(h[0], h[1]), min(h[2], h[3])), min(min(h[4], h[5]), min(h[6], h[7])));
+    if (m <= d) {
       const uint32_t j = (uint32_t)q * 2u;
-      if (h0 <= d) { hl[cnt * hstride] = (j << 3) | (uint32_t)min(d - h0, KS); ++cnt; }
-      if (h1 <= d) { hl[cnt * hstride] = ((j + 1) << 3) | (uint32_t)min(d - h1, KS); ++cnt; }
-      if (h2 <= d) { hl[cnt * hstride] = ((j + 2) << 3) | (uint32_t)min(d - h2, KS); ++cnt; }
-      if (h3 <= d) { hl[cnt * hstride] = ((j + 3) << 3) | (uint32_t)min(d - h3, KS); ++cnt; }
-      if (cnt > kHitCap - 4) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (h[i] <= d) {
+          hl[cnt * hstride] = ((j + i) << 3) | (uint32_t)min(d - h[i], KS);
+          ++cnt;
+        }
+      if (cnt > kHitCap - 8) {
         flush_hits<KS>(matched, hl, hstride, cnt, sfx, ball);
         cnt = 0;
         if (covers<KS>(matched, alive)) break;  // every live candidate matched this sequence
@@ -452,7 +468,7 @@ __device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsig
       const uint2 w = __ldg(row + j);
       const int h = __popc((Ep ^ (w.x >> KS)) | (Op ^ (w.y >> KS)));
       if (h <= jd.d)
-        group_hit<KS, false>(matched, stage_ball, jd.d, h, (int)(__ldg(crow + j) & smask));
+        group_hit<KS, true>(matched, stage_ball, jd.d, h, (int)(__ldg(crow + j) & smask));
     }
 #pragma unroll
     for (int i = 0; i < NW; ++i) {
@@ -470,11 +486,138 @@ __device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsig
 }
 
 // ---------------------------------------------------------------------------------------------
+// GROUP, prefix-tiled (k = 4, 256 lanes per CTA).
+//
+// The CTA owns 256 consecutive groups g = T*256 + lane: they share the first l-8 bases (P1)
+// and differ in the last 4 prefix bases (P2 = the lane index); each lane carries the 256
+// suffixes of its group.  Since Ham = Ham(P1) + Ham(P2) + Ham(suffix), per sequence:
+//   1. filter: the CTA computes h1 = Ham(P1, window) once per window; only windows with
+//      h1 <= d can match any of the tile's 65536 candidates, and they are compacted into a list
+//      with, per entry, the 256-bit mask of P2 values within d-h1 of the window (a row of the
+//      4-base ball table), stored word-major so that each warp reads the word of its 32 lanes;
+//   2. scan: each lane tests its bit of every listed entry (no POPC in this loop) and records
+//      the entries it hits;
+//   3. flush: per recorded entry the lane computes h2 = Ham(P2, window) and ORs in the suffixes
+//      within d-h1-h2 of the window's last 4 bases.
+// A lane with no live candidate left idles; a warp with none skips the scan; the CTA stops when
+// no lane has a live candidate (the skip).  Every sequence is handled inside the tile, so this
+// pass accepts its survivors directly.
+
+__device__ __forceinline__ void tiled_flush(GroupMask<4>& matched, const uint32_t* hl, int cnt,
+                                            const uint32_t* head, const uint16_t* vsuf,
+                                            uint32_t P2E, uint32_t P2O, const uint64_t* ball) {
+  for (int i = 0; i < cnt; ++i) {
+    const uint32_t k = hl[i * 256];
+    const uint32_t h = head[k];
+    const int r1 = (int)((h >> 16) & 15u);
+    const uint32_t w2E = (h >> 20) & 15u, w2O = (h >> 24) & 15u;
+    int r = r1 - __popc((P2E ^ w2E) | (P2O ^ w2O));
+    r = r < 4 ? r : 4;
+    or_ball<4, true>(matched, ball, vsuf[k], r);
+  }
+}
+
+__device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
+                            unsigned long long tbase, uint32_t* head, uint16_t* vsuf,
+                            uint32_t* maskw, uint32_t* hl, unsigned* s_cnt) {
+  constexpr int KS = 4;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wcap = jd.wstride;
+  const unsigned long long item = tbase + tid;
+  const uint64_t g = p.chunk_base + item;
+  GroupMask<KS> alive;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) alive.w[i] = 0;
+  if (item < p.work) range_mask<KS>(g, jd.lo, jd.hi, alive);
+  uint32_t E, O;
+  code_planes(g, E, O);  // prefix planes (l-4 bases); the low 4 bits are P2
+  const uint32_t P2E = E & 15u, P2O = O & 15u;
+  const uint32_t P1E = E >> 4, P1O = O >> 4;  // identical in every lane of the tile
+  for (int s = 0; s < jd.n; ++s) {
+    if (!__syncthreads_or(any_set<KS>(alive) ? 1 : 0)) break;  // nothing left in the tile
+    if (tid == 0) *s_cnt = 0;
+    __syncthreads();
+    // 1. filter the windows by the shared prefix
+    const uint2* row = jd.planes + (size_t)s * wcap;
+    const uint64_t* crow = jd.codes + (size_t)s * wcap;
+    for (int b = 0; b < jd.W; b += 256) {
+      const int j = b + tid;
+      bool keep = false;
+      uint32_t wE = 0, wO = 0;
+      int r1 = 0;
+      if (j < jd.W) {
+        const uint2 w = __ldg(row + j);
+        wE = w.x >> KS;
+        wO = w.y >> KS;
+        const int h1 = __popc(((wE >> 4) ^ P1E) | ((wO >> 4) ^ P1O));
+        keep = h1 <= jd.d;
+        r1 = jd.d - h1;
+      }
+      const unsigned bal = __ballot_sync(kFull, keep);
+      unsigned wb = 0;
+      if (lane == 0 && bal) wb = atomicAdd(s_cnt, (unsigned)__popc(bal));
+      wb = __shfl_sync(kFull, wb, 0);
+      if (keep) {
+        const unsigned k = wb + __popc(bal & ((1u << lane) - 1u));
+        const uint64_t code = __ldg(crow + j);
+        const int v2 = (int)((code >> (2 * KS)) & 0xFFu);  // the window's P2 bases
+        const int rr = r1 < 4 ? r1 : 4;
+        head[k] = (uint32_t)j | ((uint32_t)(r1 < 15 ? r1 : 15) << 16) | ((wE & 15u) << 20) |
+                  ((wO & 15u) << 24);
+        vsuf[k] = (uint16_t)(code & 0xFFu);
+        const uint4* brow = reinterpret_cast<const uint4*>(jd.ball + ((size_t)v2 * (KS + 1) + rr) * 4);
+        const uint4 lo = __ldg(brow), hi = __ldg(brow + 1);
+        maskw[0 * wcap + k] = lo.x;
+        maskw[1 * wcap + k] = lo.y;
+        maskw[2 * wcap + k] = lo.z;
+        maskw[3 * wcap + k] = lo.w;
+        maskw[4 * wcap + k] = hi.x;
+        maskw[5 * wcap + k] = hi.y;
+        maskw[6 * wcap + k] = hi.z;
+        maskw[7 * wcap + k] = hi.w;
+      }
+    }
+    __syncthreads();
+    const int K = (int)*s_cnt;
+    const int K4 = (K + 3) & ~3;
+    for (int i = K + tid; i < K4; i += blockDim.x)  // zero the pad of the last uint4
+      for (int w8 = 0; w8 < 8; ++w8) maskw[w8 * wcap + i] = 0;
+    __syncthreads();
+    // 2. scan the listed windows, 3. flush the hits
+    GroupMask<KS> matched;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) matched.w[i] = 0;
+    if (__any_sync(kFull, any_set<KS>(alive))) {
+      const uint32_t bit = 1u << lane;
+      const uint32_t* mrow = maskw + warp * wcap;
+      uint32_t* mine = hl + tid;
+      int cnt = 0;
+      for (int k = 0; k < K; k += 4) {
+        const uint4 m4 = *reinterpret_cast<const uint4*>(mrow + k);
+        if (m4.x & bit) { mine[cnt * 256] = (uint32_t)k; ++cnt; }
+        if (m4.y & bit) { mine[cnt * 256] = (uint32_t)k + 1; ++cnt; }
+        if (m4.z & bit) { mine[cnt * 256] = (uint32_t)k + 2; ++cnt; }
+        if (m4.w & bit) { mine[cnt * 256] = (uint32_t)k + 3; ++cnt; }
+        if (cnt > kHitCap - 4) {
+          tiled_flush(matched, mine, cnt, head, vsuf, P2E, P2O, jd.ball);
+          cnt = 0;
+        }
+      }
+      tiled_flush(matched, mine, cnt, head, vsuf, P2E, P2O, jd.ball);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) alive.w[i] &= matched.w[i];
+    __syncthreads();  // the list is rebuilt for the next sequence
+  }
+  group_output<KS>(jd, st, g, alive);
+}
+
+// ---------------------------------------------------------------------------------------------
 // The step kernel.
 
 // KIND = MOTIF_KERNEL_CAND with P = candidates per lane, or MOTIF_KERNEL_GROUP with P = ks.
-// Shared memory: staged windows of the pass (CAND: planes; GROUP: prefix planes, suffix values,
-// the ball table and one hit list per thread).
+// Shared memory: staged windows of the pass (CAND: planes; GROUP: prefix planes, suffix values
+// and one hit list per thread).
 template <int KIND, int P>
 __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restrict__ jobs,
                                                          JobState* states, int njobs,
@@ -488,6 +631,8 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
   __shared__ unsigned s_tiles;
   __shared__ int s_last;
   __shared__ unsigned s_act[kMaxBlock / 32];
+  __shared__ unsigned long long s_tbase;
+  __shared__ unsigned s_tcnt;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const unsigned budget = ctl->tiles_per_warp * (blockDim.x >> 5);
@@ -510,7 +655,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
     const Pass p = s_pass;
     JobState* st = &states[j];
     const int wpad = jd.wstride;
-    const int nst = p.mode == kRest ? 0 : p.s1 - p.s0;
+    const int nst = (p.mode == kRest || p.mode == kTiled) ? 0 : p.s1 - p.s0;
 
     // Stage the windows of the pass (and, for GROUP, the ball table) in shared memory.
     const uint4* stage4 = reinterpret_cast<const uint4*>(smem);
@@ -522,26 +667,49 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       const uint4* src = reinterpret_cast<const uint4*>(jd.planes + (size_t)p.s0 * wpad);
       for (int i = tid; i < nst * (wpad >> 1); i += blockDim.x) dst[i] = src[i];
     } else {
+      // The ball table stays in global memory (read through L1 only for the rare hits);
+      // shared memory holds the staged prefix planes, suffix values and the hit lists.
       const size_t wp_bytes = (size_t)kMaxStageSeqs * wpad * 8;
-      size_t ball_off = wp_bytes + (size_t)kMaxStageSeqs * wpad * 2;
-      ball_off += 16 - ball_off % 16;
-      const int bw = ball_table_words(P);
+      size_t hit_off = wp_bytes + (size_t)kMaxStageSeqs * wpad * 2;
+      hit_off += 16 - hit_off % 16;
       uint2* dwp = reinterpret_cast<uint2*>(smem);
       uint16_t* dsfx = reinterpret_cast<uint16_t*>(smem + wp_bytes);
-      uint64_t* dball = reinterpret_cast<uint64_t*>(smem + ball_off);
       const uint64_t smask = (1ull << (2 * P)) - 1;
       for (int i = tid; i < nst * wpad; i += blockDim.x) {
         const uint2 pl = jd.planes[(size_t)p.s0 * wpad + i];
         dwp[i] = make_uint2(pl.x >> P, pl.y >> P);
         dsfx[i] = (uint16_t)(jd.codes[(size_t)p.s0 * wpad + i] & smask);
       }
-      for (int i = tid; i < bw; i += blockDim.x) dball[i] = jd.ball[i];
       stage_sfx = dsfx;
-      stage_ball = dball;
-      hits = reinterpret_cast<uint32_t*>(smem + ball_off + (size_t)bw * 8) + tid;
+      stage_ball = jd.ball;
+      hits = reinterpret_cast<uint32_t*>(smem + hit_off) + tid;
     }
     __syncthreads();
 
+    if (KIND == MOTIF_KERNEL_GROUP && P == 4 && p.mode == kTiled) {
+      // CTA-wide tiles of 256 groups.
+      const size_t wc = (size_t)wpad;
+      uint32_t* head = reinterpret_cast<uint32_t*>(smem);
+      uint16_t* vsuf = reinterpret_cast<uint16_t*>(smem + wc * 4);
+      size_t moff = wc * 6;
+      moff += 16 - moff % 16;
+      uint32_t* maskw = reinterpret_cast<uint32_t*>(smem + moff);
+      uint32_t* hl = maskw + 8 * wc;
+      for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+          unsigned long long b = ~0ull;
+          if (budget == 0 || atomicAdd(&s_tiles, blockDim.x >> 5) < budget)
+            b = atomicAdd(&st->cursor, (unsigned long long)blockDim.x);
+          s_tbase = b;
+        }
+        __syncthreads();
+        const unsigned long long b = s_tbase;
+        if (b >= p.work) break;
+        group_tiled(jd, st, p, b, head, vsuf, maskw, hl, &s_tcnt);
+      }
+      continue;
+    }
     // Pull tiles until the pass is exhausted (or the step's tile budget is spent).
     const unsigned long long tile = tile_of(KIND, P, p.mode);
     for (;;) {
@@ -771,8 +939,14 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
-  b += (size_t)ball_table_words(p) * 8;
-  return b + (size_t)kHitCap * block * 4;
+  b += (size_t)kHitCap * block * 4;
+  if (p == 4) {  // the prefix-tiled pass: list heads, suffix values, 8 mask words, hit lists
+    size_t t = (size_t)wstride * 6;
+    t += 16 - t % 16;
+    t += (size_t)wstride * 32 + (size_t)kHitCap * 256 * 4;
+    if (t > b) b = t;
+  }
+  return b;
 }
 
 // Raises (never lowers) a variant's dynamic shared memory limit: plans, batches and the server

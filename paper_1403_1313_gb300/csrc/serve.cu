@@ -29,6 +29,7 @@ struct Job {
   int64_t id = 0;
   int n = 0, t = 0, l = 0, d = 0, W = 0, wstride = 0;
   int kind = MOTIF_KERNEL_GROUP, pv = 4, span0 = 2, sms = 0;
+  bool tiled = false;
   size_t smem = 0;
   uint64_t lo = 0, hi = 0, unit_lo = 0, unit_hi = 0, chunk_units = 0, nchunks = 0, rest = 0;
   uint2* planes = nullptr;
@@ -157,6 +158,7 @@ void fill_job_desc(const Job* j, JobDesc* jd) {
   jd->W = j->W; jd->wstride = j->wstride;
   jd->planes = j->planes; jd->codes = j->codes;
   jd->kind = j->kind; jd->ks = j->pv; jd->cpt = 1; jd->span0 = j->span0;
+  jd->tiled = j->tiled ? 1 : 0;
   jd->lo = j->lo; jd->hi = j->hi; jd->unit_lo = j->unit_lo; jd->unit_hi = j->unit_hi;
   jd->chunk_units = j->chunk_units; jd->nchunks = j->nchunks; jd->rest_threshold = j->rest;
   jd->qidx[0] = j->qidx[0]; jd->qidx[1] = j->qidx[1];
@@ -507,7 +509,9 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   j->nchunks = units == 0 || j->W <= 0 ? 0 : (units + j->chunk_units - 1) / j->chunk_units;
   j->qcap = j->chunk_units;
   j->words = mask_words(j->pv);
-  j->rest = (uint64_t)8 * 32 * S->sms;
+  j->tiled = j->pv == 4 && j->l >= 8 && j->W <= 65535 && j->unit_lo % 256 == 0 &&
+             (j->chunk_units % 256 == 0 || units <= j->chunk_units);
+  j->rest = (uint64_t)256 * S->sms;
   if (j->nchunks > 0) {
     std::lock_guard<std::mutex> sg(S->submit_mu);
     j->ball = ball_table(S->device, j->pv, S->submit_stream);

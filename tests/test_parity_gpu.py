@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 VARIANTS = [
+    ("tiled", dict(kernel=m.KERNEL_TILED)),
     ("group4", dict(kernel=m.KERNEL_GROUP, suffix_bases=4)),
     ("group3", dict(kernel=m.KERNEL_GROUP, suffix_bases=3)),
     ("group2", dict(kernel=m.KERNEL_GROUP, suffix_bases=2)),
@@ -106,6 +107,32 @@ def test_unaligned_subranges(name, kw):
         assert cmp == ref_cmp
 
 
+@pytest.mark.parametrize("l,d", [(8, 1), (9, 2), (10, 3), (12, 4)])
+def test_tiled_aligned_and_partial_ranges(l, d):
+    """The prefix-tiled pass: ranges starting on a tile boundary (multiples of 4^8 candidates)
+    with ragged ends, small sequence counts, and windows near the 16-bit index limit."""
+    job = fmgen.fm_job(4, 70, l, d, 300 + l)
+    rng = random.Random(l * 31 + d)
+    tile = 4 ** 8
+    for _ in range(3):
+        lo = tile * rng.randrange(0, max(1, 4 ** l // tile))
+        hi = min(4 ** l, lo + rng.randrange(1, 3 * tile))
+        ref, ref_cmp = oracle.search(job.rows(), l, d, lo=lo, hi=hi)
+        got, cmp = gpu_search(job.seqs, l, d, lo=lo, hi=hi, kernel=m.KERNEL_TILED)
+        assert np.array_equal(got, ref), (lo, hi)
+        assert cmp == ref_cmp
+
+
+@pytest.mark.parametrize("l,d,n,t", [(8, 8, 2, 9), (9, 4, 3, 40), (11, 6, 2, 30)])
+def test_tiled_every_window_listed(l, d, n, t):
+    """d at or above the shared-prefix length: every window enters the filtered list."""
+    rows = rand_rows(random.Random(l + d), n, t)
+    ref, ref_cmp = oracle.search(rows, l, d, threads=8)
+    got, cmp = gpu_search(rows, l, d, kernel=m.KERNEL_TILED)
+    assert np.array_equal(got, ref)
+    assert cmp == ref_cmp
+
+
 # ---- edge cases ---------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name,kw", VARIANTS, ids=[v[0] for v in VARIANTS])
@@ -119,7 +146,7 @@ def test_everything_survives(name, kw, l, d):
     assert cmp == 4 ** l * 3
 
 
-@pytest.mark.parametrize("name,kw", VARIANTS[:1] + VARIANTS[4:5], ids=["group4", "cand1"])
+@pytest.mark.parametrize("name,kw", VARIANTS[:2] + VARIANTS[5:6], ids=["tiled", "group4", "cand1"])
 def test_no_windows_and_single_windows(name, kw):
     rows = rand_rows(random.Random(3), 4, 5)
     got, cmp = gpu_search(rows, 6, 6, **kw)          # t < l: nothing can match
@@ -231,8 +258,8 @@ def test_full_size_sampled(cfg):
 def test_l15d4_kernels_agree():
     job = fmgen.single("l15d4")
     res = []
-    for kw in (dict(kernel=m.KERNEL_GROUP, suffix_bases=4), dict(kernel=m.KERNEL_GROUP, suffix_bases=3),
-               dict(kernel=m.KERNEL_CAND, cands_per_thread=2)):
+    for kw in (dict(kernel=m.KERNEL_TILED), dict(kernel=m.KERNEL_GROUP, suffix_bases=4),
+               dict(kernel=m.KERNEL_GROUP, suffix_bases=3), dict(kernel=m.KERNEL_CAND, cands_per_thread=2)):
         plan = m.motif_plan_create(job.n, job.t, 15, 4, _opts(**kw))
         m.motif_load_seqs(plan, job.seqs)
         res.append(m.motif_search(plan))

@@ -49,12 +49,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="l15d4")
-    ap.add_argument("--kernel", choices=["auto", "group", "cand"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "tiled", "group", "cand"], default="auto")
     ap.add_argument("--suffix-bases", type=int, default=0)
     ap.add_argument("--cands-per-thread", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cand-subrange", type=int, default=1 << 27,
+                    help="candidates of the roofline_cand sub-range run (0 = skip)")
     ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
                     help="single: the driver's (l,d) line; batch: 64 uneven jobs batched vs one "
                          "job per launch; serve: Poisson arrivals, p50/p99 latency per rate")
@@ -211,6 +213,8 @@ def run_ours(args):
         kw["kernel"] = m.KERNEL_GROUP
     elif args.kernel == "cand":
         kw["kernel"] = m.KERNEL_CAND
+    elif args.kernel == "tiled":
+        kw["kernel"] = m.KERNEL_TILED
     if args.suffix_bases:
         kw["suffix_bases"] = args.suffix_bases
     if args.cands_per_thread:
@@ -270,23 +274,58 @@ def run_ours(args):
     value = world * cands * args.steps / (t_ms / 1e3)
     cps = world * compares * args.steps / (t_ms / 1e3)
 
-    # Roofline of the dominant kernel: the step kernel, whose launches are bracketed by the
-    # plan's events (search_ms_sum over the timed searches).
+    # Roofline of the dominant kernel (the step kernel; its launches are bracketed by the plan's
+    # events: search_ms_sum over the timed searches), by the per-compare recipe: one algorithmic
+    # window compare (the oracle's canonical tally) costs one POPC, so peak = 16 POPC/clk/SM x
+    # SMs x max SM clock.  A kernel that factors the compare (GROUP, TILED) resolves many
+    # compares per POPC and reads above 1.0 here; the per-candidate kernel (CAND), which pays
+    # the full per-compare cost, is timed on a sub-range below as roofline_cand.
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     step_ms = st["search_ms_sum"] / max(st["searches"], 1)
     sort_ms = st["sort_ms_sum"] / max(st["searches"], 1)
-    achieved = unit_steps / (step_ms / 1e3)
     peak = POPC_PER_SM_CLK * sms * max_mhz * 1e6
+    kname = {m.KERNEL_GROUP: "GROUP", m.KERNEL_CAND: "CAND"}.get(st["kernel"], "?")
+    if kname == "GROUP" and kw.get("kernel", m.KERNEL_AUTO) in (m.KERNEL_AUTO, m.KERNEL_TILED) and l >= 8:
+        kname = "TILED"
+    achieved = compares / (step_ms / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "G unit-steps/s (1 POPC each)", "frac": achieved / peak, "traffic": None,
-            "kernel": "step_kernel<%s>" % ("GROUP" if st["kernel"] == m.KERNEL_GROUP else "CAND"),
+            "unit": "G window-compares/s (1 POPC each)", "frac": achieved / peak, "traffic": None,
+            "kernel": "step_kernel<%s>" % kname,
             "peak_basis": "16 POPC/clk/SM (K4 probe) x %d SMs x %.0f MHz (max SM clock)" % (sms, max_mhz),
             "step_kernel_ms": step_ms, "sort_ms": sort_ms,
-            "unit_steps_per_search": unit_steps}
+            "algorithmic_compares_per_search": compares,
+            "group_prefix_compares_per_search": unit_steps,
+            "note": ("frac > 1: the %s kernel factors the Hamming distance over shared candidate "
+                     "prefixes, so one POPC or bit test resolves many algorithmic compares; see "
+                     "roofline_cand for the per-compare kernel" % kname) if kname != "CAND" else ""}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (POPC_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
+    roof_cand = None
+    if kname != "CAND" and args.cand_subrange > 0:
+        # The per-candidate kernel on a sub-range of the same workload (full per-compare cost).
+        ocand = m.torch_opts(stream=stream, kernel=m.KERNEL_CAND, cands_per_thread=2,
+                             range_lo=0, range_hi=min(cands, args.cand_subrange))
+        pc = m.motif_plan_create(n, t, l, d, ocand)
+        with torch.cuda.stream(stream):
+            m.motif_load_seqs_device(pc, d_chars)
+            for _ in range(2):
+                m.motif_search_device(pc, d_out, cap, d_cnt)
+        stream.synchronize()
+        c_cmp = m.motif_count_compares(pc)
+        m.motif_stats(pc)
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                m.motif_search_device(pc, d_out, cap, d_cnt)
+        stc = m.motif_stats(pc)
+        c_ms = stc["search_ms_sum"] / max(stc["searches"], 1)
+        c_ach = c_cmp / (c_ms / 1e3)
+        roof_cand = {"bound": "alu", "achieved": c_ach / 1e9, "peak": peak / 1e9,
+                     "unit": "G window-compares/s (1 POPC each)", "frac": c_ach / peak,
+                     "kernel": "step_kernel<CAND,2>", "step_kernel_ms": c_ms,
+                     "sample": "candidates [0, %d) of %s" % (min(cands, args.cand_subrange), workload)}
+        m.motif_plan_destroy(pc)
 
     # End to end through the blocking C ABI with host buffers.
     e2e = None
@@ -321,6 +360,7 @@ def run_ours(args):
             "algorithmic_compares_per_search": compares,
             "survivors": count,
             "roofline": roof,
+            "roofline_cand": roof_cand,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
@@ -414,15 +454,26 @@ def run_serve(args):
         m.motif_poll(m.motif_submit(pl), timeout_ms=60000)
         m.motif_plan_destroy(pl)
         ids = []
+        client = {"create": 0.0, "load": 0.0, "submit": 0.0, "destroy": 0.0}
         t0 = time.perf_counter()
         for j in jobs:
             delay = t0 + j.arrival_s - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
+            c0 = time.perf_counter()
             pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+            c1 = time.perf_counter()
             m.motif_load_seqs(pl, j.seqs)
+            c2 = time.perf_counter()
             ids.append(m.motif_submit(pl))
+            c3 = time.perf_counter()
             m.motif_plan_destroy(pl)
+            c4 = time.perf_counter()
+            client["create"] += c1 - c0
+            client["load"] += c2 - c1
+            client["submit"] += c3 - c2
+            client["destroy"] += c4 - c3
+        t_submitted = time.perf_counter() - t0
         lat, queue, cands, ok = [], [], 0, 0
         for j, jid in zip(jobs, ids):
             res = m.motif_poll(jid, timeout_ms=600000)
@@ -439,7 +490,10 @@ def run_serve(args):
                      "queue_p50_ms": float(np.percentile(queue, 50)),
                      "queue_p99_ms": float(np.percentile(queue, 99)),
                      "throughput_jobs_per_s": count / wall, "candidates_per_s": cands / wall,
-                     "consensus_found": ok})
+                     "consensus_found": ok,
+                     "client_ms_per_job": {k: 1e3 * v / count for k, v in client.items()},
+                     "last_arrival_s": jobs[-1].arrival_s, "submitted_all_s": t_submitted,
+                     "done_all_s": wall})
         print(json.dumps(rows[-1]), flush=True)
     print(json.dumps({"mode": "serve", "workload": "Poisson arrivals, seed 5: l~U{11..15}, "
                       "d~U{2..4}, n~U{10..30}, t~U{300..800}, GC in {0.4,0.5,0.6}, FM-planted",

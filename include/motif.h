@@ -115,10 +115,11 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
 /* Releases the plan and its device memory (after its stream has drained).  NULL is a no-op. */
 void motif_plan_destroy(motif_plan p);
 
-/* ---- input: window extraction (Sec. IV.A "all the windows are first extracted") -------- */
+/* ---- input: window extraction (Sec. IV.A: windows are extracted before the search) ------ */
 
 /* Copies n rows of t characters (row r at seqs + r*stride, stride >= t) to the device and
- * packs every window into a 2l-bit word (32-bit for l <= 16, 64-bit above).  Blocking; the
+ * packs every window into its 2l-bit code (a 64-bit word) and two l-bit planes (the low and
+ * the high bit of every base, one 32-bit word each).  Blocking; the
  * characters are validated and a character outside ACGTacgt returns MOTIF_ERR_ALPHABET
  * (the plan then holds no sequences).  Errors: MOTIF_ERR_ARG, MOTIF_ERR_ALPHABET,
  * MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */

@@ -16,7 +16,7 @@
  * generated in advance); compare it with the windows of each sequence by counting mismatched
  * nucleotides (Sec. III.A); it matches a sequence when some window has at most d mismatches;
  * when a sequence has no matching window the l-mer is discarded and the remaining sequences
- * are skipped (Sec. III.A, the "skip").  Readings where the paper is silent:
+ * are skipped (Sec. III.A: the skip).  Readings where the paper is silent:
  *   - sequences are visited in input order, windows left to right;
  *   - a sequence's scan stops at its first matching window (the result set does not depend on
  *     this; the compare tally does);

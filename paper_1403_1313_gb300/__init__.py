@@ -160,6 +160,7 @@ class Plan:
         self.handle = handle
         self.n, self.t, self.l, self.d = n, t, l, d
         self._opts = opts  # keeps allocator callbacks alive
+        self.capacity_hint = 1 << 16  # output room for the next search (grows with results)
 
     def __del__(self):
         try:
@@ -223,9 +224,12 @@ def motif_load_seqs_device(plan: Plan, d_seqs, stride: int | None = None) -> Non
     _check(_load().motif_load_seqs_device(plan, ctypes.c_void_p(ptr), stride), "motif_load_seqs_device")
 
 
-def motif_search(plan: Plan, capacity: int = 1 << 16) -> np.ndarray:
-    """Blocking search; returns the ascending accepted codes (grows the buffer on demand)."""
+def motif_search(plan: Plan, capacity: int | None = None) -> np.ndarray:
+    """Blocking search; returns the ascending accepted codes.  The output buffer starts at the
+    plan's capacity hint (the size of its previous result) and grows on demand."""
     lib = _load()
+    if capacity is None:
+        capacity = plan.capacity_hint
     while True:
         out = np.zeros(max(capacity, 1), dtype=np.uint64)
         cnt = ctypes.c_int64(0)
@@ -235,6 +239,7 @@ def motif_search(plan: Plan, capacity: int = 1 << 16) -> np.ndarray:
             capacity = cnt.value
             continue
         _check(st, "motif_search")
+        plan.capacity_hint = max(plan.capacity_hint, int(cnt.value))
         return out[:cnt.value].copy()
 
 
@@ -275,11 +280,12 @@ def motif_stats(plan: Plan) -> dict:
 
 # ---- batching and tuning ---------------------------------------------------------------------
 
-def motif_batch_search(plans, use_graph: bool = True, capacity: int = 1 << 16):
-    """Runs loaded plans together in one persistent launch; returns (codes list, statuses)."""
+def motif_batch_search(plans, use_graph: bool = True, capacity: int | None = None):
+    """Runs loaded plans together in one persistent launch; returns the codes of each job.
+    Each job's output buffer starts at its plan's capacity hint (or `capacity`)."""
     lib = _load()
     k = len(plans)
-    caps = [capacity] * k
+    caps = [capacity if capacity is not None else p.capacity_hint for p in plans]
     while True:
         outs = [np.zeros(max(c, 1), dtype=np.uint64) for c in caps]
         handles = (ctypes.c_void_p * k)(*[p.handle for p in plans])
@@ -295,6 +301,8 @@ def motif_batch_search(plans, use_graph: bool = True, capacity: int = 1 << 16):
                 caps[j] = counts[j]
             continue
         _check(st, "motif_batch_search")
+        for j, p in enumerate(plans):
+            p.capacity_hint = max(p.capacity_hint, int(counts[j]))
         return [outs[j][:counts[j]].copy() for j in range(k)]
 
 

@@ -151,6 +151,9 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
+    // Sort/dedup every job's codes in its own buffer (counts live in the batch state array),
+    // read all final counts with one copy, then copy the codes with one final wait.
+    std::vector<char> sorted(ids.size(), 0);
     for (size_t i = 0; i < ids.size(); ++i) {
       const int j = ids[i];
       motif_plan_s* p = plans[j];
@@ -159,26 +162,31 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         redo[j] = 1;  // the plan's own buffer was too small: rerun this job alone below
         continue;
       }
-      // Sort/dedup this job's codes in its own buffer (count in the batch state array).
       if (found > 4096) {
         const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
         if (need > p->sort_bytes) {
           plan_free(p, p->d_sort, p->sort_bytes);
-          cudaStreamSynchronize(p->stream);
           p->d_sort = plan_alloc(p, need);
-          cudaStreamSynchronize(p->stream);
+          cudaStreamSynchronize(p->stream);  // the scratch is used on the batch stream
           p->sort_bytes = p->d_sort ? need : 0;
+          p->gs_scratch = nullptr;  // any cached sort graph names the old scratch
           if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
         }
       }
       e = launch_sort_unique(p->d_out, &c->d_states[i].out_count, p->out_cap, 2 * p->l,
                              p->d_sort, p->sms, (long long)found, c->stream);
-      unsigned long long fc = 0;
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&fc, &c->d_states[i].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
-                            c->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) return status_from_cuda(e);
+      sorted[i] = 1;
+    }
+    e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    for (size_t i = 0; i < ids.size(); ++i) {
+      if (!sorted[i]) continue;
+      const int j = ids[i];
+      motif_plan_s* p = plans[j];
+      const unsigned long long fc = st[i].out_count;
       out_counts[j] = (int64_t)fc;
       p->stats.survivors = fc;
       p->stats.candidates = p->hi - p->lo;
@@ -188,10 +196,11 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       }
       if (fc) {
         e = cudaMemcpyAsync(out_codes[j], p->d_out, fc * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return status_from_cuda(e);
       }
     }
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
   }
   for (int j = 0; j < njobs; ++j) {
     if (!redo[j]) continue;

@@ -495,31 +495,46 @@ __device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsig
 //      h1 <= d can match any of the tile's 65536 candidates, and they are compacted into a list
 //      with, per entry, the 256-bit mask of P2 values within d-h1 of the window (a row of the
 //      4-base ball table), stored word-major so that each warp reads the word of its 32 lanes;
-//   2. scan: each lane tests its bit of every listed entry (no POPC in this loop) and records
-//      the entries it hits;
-//   3. flush: per recorded entry the lane computes h2 = Ham(P2, window) and ORs in the suffixes
+//   2. scan: 32 listed entries at a time, each warp transposes the 32 words of its lanes into
+//      one 32-bit mask per lane of the entries it hits (no POPC in this loop);
+//   3. hits: per hit entry the lane computes h2 = Ham(P2, window) and ORs in the suffixes
 //      within d-h1-h2 of the window's last 4 bases.
 // A lane with no live candidate left idles; a warp with none skips the scan; the CTA stops when
 // no lane has a live candidate (the skip).  Every sequence is handled inside the tile, so this
 // pass accepts its survivors directly.
 
-__device__ __forceinline__ void tiled_flush(GroupMask<4>& matched, const uint32_t* hl, int cnt,
-                                            const uint32_t* head, const uint16_t* vsuf,
-                                            uint32_t P2E, uint32_t P2O, const uint64_t* ball) {
-  for (int i = 0; i < cnt; ++i) {
-    const uint32_t k = hl[i * 256];
-    const uint32_t h = head[k];
-    const int r1 = (int)((h >> 16) & 15u);
-    const uint32_t w2E = (h >> 20) & 15u, w2O = (h >> 24) & 15u;
-    int r = r1 - __popc((P2E ^ w2E) | (P2O ^ w2O));
-    r = r < 4 ? r : 4;
-    or_ball<4, true>(matched, ball, vsuf[k], r);
+// One hit of lane (P2E, P2O) on listed entry k: OR in the suffixes within d-h1-h2 of the
+// window's last 4 bases (h1 and the window's P2 planes are in the entry's head word).
+__device__ __forceinline__ void tiled_hit(GroupMask<4>& matched, uint32_t k, const uint32_t* head,
+                                          const uint16_t* vsuf, uint32_t P2E, uint32_t P2O,
+                                          const uint64_t* ball) {
+  const uint32_t h = head[k];
+  const int r1 = (int)((h >> 16) & 15u);
+  const uint32_t w2E = (h >> 20) & 15u, w2O = (h >> 24) & 15u;
+  int r = r1 - __popc((P2E ^ w2E) | (P2O ^ w2O));
+  r = r < 4 ? r : 4;
+  or_ball<4, true>(matched, ball, vsuf[k], r);
+}
+
+// 32x32 bit-matrix transpose across the warp: on entry lane i holds row i; on exit lane j holds
+// column j (bit i of lane j's result = bit j of lane i's input).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int sh = 16 >> i;
+    const uint32_t y = __shfl_xor_sync(kFull, x, sh);
+    const bool up = (lane & sh) == 0;
+    const uint32_t keep = up ? masks[i] : ~masks[i];
+    const uint32_t t = up ? (y << sh) : (y >> sh);
+    x = (x & keep) | (t & ~keep);
   }
+  return x;
 }
 
 __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
                             unsigned long long tbase, uint32_t* head, uint16_t* vsuf,
-                            uint32_t* maskw, uint32_t* hl, unsigned* s_cnt) {
+                            uint32_t* maskw, unsigned* s_cnt /* [2] */) {
   constexpr int KS = 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wcap = jd.wstride;
@@ -533,11 +548,12 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
   code_planes(g, E, O);  // prefix planes (l-4 bases); the low 4 bits are P2
   const uint32_t P2E = E & 15u, P2O = O & 15u;
   const uint32_t P1E = E >> 4, P1O = O >> 4;  // identical in every lane of the tile
-  for (int s = 0; s < jd.n; ++s) {
-    if (!__syncthreads_or(any_set<KS>(alive) ? 1 : 0)) break;  // nothing left in the tile
-    if (tid == 0) *s_cnt = 0;
-    __syncthreads();
-    // 1. filter the windows by the shared prefix
+  if (tid == 0) s_cnt[0] = 0;
+  int live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
+  for (int s = 0; s < jd.n && live; ++s) {
+    unsigned* cnt = s_cnt + (s & 1);
+    // 1. filter the windows by the shared prefix (the list count was zeroed before the
+    //    barrier that precedes this phase)
     const uint2* row = jd.planes + (size_t)s * wcap;
     const uint64_t* crow = jd.codes + (size_t)s * wcap;
     for (int b = 0; b < jd.W; b += 256) {
@@ -555,7 +571,7 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
       }
       const unsigned bal = __ballot_sync(kFull, keep);
       unsigned wb = 0;
-      if (lane == 0 && bal) wb = atomicAdd(s_cnt, (unsigned)__popc(bal));
+      if (lane == 0 && bal) wb = atomicAdd(cnt, (unsigned)__popc(bal));
       wb = __shfl_sync(kFull, wb, 0);
       if (keep) {
         const unsigned k = wb + __popc(bal & ((1u << lane) - 1u));
@@ -577,37 +593,30 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
         maskw[7 * wcap + k] = hi.w;
       }
     }
+    if (tid == 0) s_cnt[(s + 1) & 1] = 0;  // the next sequence's list count
     __syncthreads();
-    const int K = (int)*s_cnt;
-    const int K4 = (K + 3) & ~3;
-    for (int i = K + tid; i < K4; i += blockDim.x)  // zero the pad of the last uint4
-      for (int w8 = 0; w8 < 8; ++w8) maskw[w8 * wcap + i] = 0;
-    __syncthreads();
-    // 2. scan the listed windows, 3. flush the hits
+    const int K = (int)*cnt;
+    // 2. scan: 32 listed entries at a time; a warp transpose turns the entries' words for this
+    //    warp's 32 lanes into one 32-bit hit mask per lane.  3. OR in each hit's suffix ball.
     GroupMask<KS> matched;
 #pragma unroll
     for (int i = 0; i < 4; ++i) matched.w[i] = 0;
     if (__any_sync(kFull, any_set<KS>(alive))) {
-      const uint32_t bit = 1u << lane;
       const uint32_t* mrow = maskw + warp * wcap;
-      uint32_t* mine = hl + tid;
-      int cnt = 0;
-      for (int k = 0; k < K; k += 4) {
-        const uint4 m4 = *reinterpret_cast<const uint4*>(mrow + k);
-        if (m4.x & bit) { mine[cnt * 256] = (uint32_t)k; ++cnt; }
-        if (m4.y & bit) { mine[cnt * 256] = (uint32_t)k + 1; ++cnt; }
-        if (m4.z & bit) { mine[cnt * 256] = (uint32_t)k + 2; ++cnt; }
-        if (m4.w & bit) { mine[cnt * 256] = (uint32_t)k + 3; ++cnt; }
-        if (cnt > kHitCap - 4) {
-          tiled_flush(matched, mine, cnt, head, vsuf, P2E, P2O, jd.ball);
-          cnt = 0;
+      for (int k = 0; k < K; k += 32) {
+        uint32_t x = k + lane < K ? mrow[k + lane] : 0u;
+        x = warp_transpose32(x, lane);
+        while (x) {
+          const int i = __ffs(x) - 1;
+          x &= x - 1;
+          tiled_hit(matched, (uint32_t)(k + i), head, vsuf, P2E, P2O, jd.ball);
         }
       }
-      tiled_flush(matched, mine, cnt, head, vsuf, P2E, P2O, jd.ball);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) alive.w[i] &= matched.w[i];
-    __syncthreads();  // the list is rebuilt for the next sequence
+    // One barrier: the list may be rebuilt, and the tile stops once no lane has a live candidate.
+    live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
   }
   group_output<KS>(jd, st, g, alive);
 }
@@ -632,7 +641,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
   __shared__ int s_last;
   __shared__ unsigned s_act[kMaxBlock / 32];
   __shared__ unsigned long long s_tbase;
-  __shared__ unsigned s_tcnt;
+  __shared__ unsigned s_tcnt[2];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const unsigned budget = ctl->tiles_per_warp * (blockDim.x >> 5);
@@ -694,7 +703,6 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       size_t moff = wc * 6;
       moff += 16 - moff % 16;
       uint32_t* maskw = reinterpret_cast<uint32_t*>(smem + moff);
-      uint32_t* hl = maskw + 8 * wc;
       for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -706,7 +714,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
         __syncthreads();
         const unsigned long long b = s_tbase;
         if (b >= p.work) break;
-        group_tiled(jd, st, p, b, head, vsuf, maskw, hl, &s_tcnt);
+        group_tiled(jd, st, p, b, head, vsuf, maskw, s_tcnt);
       }
       continue;
     }
@@ -940,10 +948,10 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
   b += (size_t)kHitCap * block * 4;
-  if (p == 4) {  // the prefix-tiled pass: list heads, suffix values, 8 mask words, hit lists
+  if (p == 4) {  // the prefix-tiled pass: list heads, suffix values, 8 mask words per entry
     size_t t = (size_t)wstride * 6;
     t += 16 - t % 16;
-    t += (size_t)wstride * 32 + (size_t)kHitCap * 256 * 4;
+    t += (size_t)wstride * 32;
     if (t > b) b = t;
   }
   return b;

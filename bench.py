@@ -481,7 +481,9 @@ def run_serve(args):
             lat.append(st["total_ms"])
             queue.append(st["queue_ms"])
             cands += 4 ** j.l
-            ok += int(m.motif_encode(j.consensus) in set(codes.tolist()))
+            c = m.motif_encode(j.consensus)
+            pos = int(np.searchsorted(codes, np.uint64(c)))
+            ok += int(pos < codes.size and int(codes[pos]) == c)
         wall = time.perf_counter() - t0
         m.motif_server_stop()
         lat = np.array(lat)

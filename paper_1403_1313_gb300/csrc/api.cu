@@ -344,7 +344,7 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   // launches the step bound blindly.
   static const bool no_graph = getenv("MOTIF_NO_GRAPH") != nullptr;
   if (no_graph) {
-    cudaError_t e = launch_init_steps(p->d_state, 1, p->d_ctl, 0, 0, p->stream);
+    cudaError_t e = launch_init_steps(p->d_state, 1, p->d_ctl, 0, 0, 0, p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
     return run_steps(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
                      max_steps_of(p), poll, timeout_of(p), p->stream, nullptr);
@@ -352,7 +352,7 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   // One graph launch runs every step: init, then a while loop whose body is the step kernel.
   if (!p->g_steps) {
     cudaError_t e = build_step_graph(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid,
-                                     p->block, p->smem, (unsigned)max_steps_of(p), &p->g_steps);
+                                     p->block, p->smem, (unsigned)max_steps_of(p), 0, &p->g_steps);
     if (e != cudaSuccess) {
       p->g_steps = nullptr;
       return status_from_cuda(e);

@@ -66,7 +66,7 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
   // done (or after max_steps steps).
   cudaGraphExec_t exec = nullptr;
   cudaError_t e = build_step_graph(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block,
-                                   smem, (unsigned)max_steps, &exec);
+                                   smem, (unsigned)max_steps, 1, &exec);
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   StepCtl ctl{};
@@ -140,8 +140,9 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     if (grid <= 0) return MOTIF_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(c->d_jobs, descs.data(), sizeof(JobDesc) * ids.size(),
                                     cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_states, 0, sizeof(JobState) * ids.size(), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctl, 0, sizeof(StepCtl), c->stream);
+    // Zero the states; CTAs rotate their starting job so every job's tiles start at once.
+    if (e == cudaSuccess)
+      e = launch_init_steps(c->d_states, (int)ids.size(), c->d_ctl, 0, 0, 1, c->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
     rc = run_table(c, kind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
                    timeout);

@@ -58,7 +58,7 @@ struct StepCtl {
   unsigned int active_jobs;      // written by the last CTA: jobs not yet done
   unsigned int steps;            // steps executed
   unsigned int max_steps;        // graph while-loops stop after this many steps (0 = no bound)
-  unsigned int pad;
+  unsigned int rotate;           // != 0: CTA b starts its walk over the jobs at job b % njobs
 };
 
 __host__ __device__ inline int mask_words(int ks) { return ks <= 3 ? 1 : (1 << (2 * ks - 6)); }
@@ -93,13 +93,15 @@ cudaError_t add_step_node(cudaGraph_t g, int kind, int p, const JobDesc* d_jobs,
                           cudaGraphNode_t* node);
 // Zeroes njobs states and initialises the step control block.
 cudaError_t launch_init_steps(JobState* d_states, int njobs, StepCtl* d_ctl, unsigned max_steps,
-                              unsigned tiles_per_warp, cudaStream_t s);
+                              unsigned tiles_per_warp, unsigned rotate, cudaStream_t s);
 cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl* d_ctl,
-                          unsigned max_steps, unsigned tiles_per_warp, cudaGraphNode_t* node);
+                          unsigned max_steps, unsigned tiles_per_warp, unsigned rotate,
+                          cudaGraphNode_t* node);
 // Builds and instantiates init -> while(step) over a job table: one launch runs every step.
+// rotate != 0 spreads the CTAs' starting jobs (batches); 0 keeps table (arrival) order.
 cudaError_t build_step_graph(int kind, int p, const JobDesc* d_jobs, JobState* d_states,
                              int njobs, StepCtl* d_ctl, int grid, int block, size_t smem,
-                             unsigned max_steps, cudaGraphExec_t* exec);
+                             unsigned max_steps, unsigned rotate, cudaGraphExec_t* exec);
 cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
                          cudaStream_t s);
 // Canonical (group, window) prefix-compare tally of the GROUP formulation with ks suffix bases.

@@ -645,9 +645,12 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const unsigned budget = ctl->tiles_per_warp * (blockDim.x >> 5);
+  const int first = ctl->rotate ? (int)(blockIdx.x % (unsigned)njobs) : 0;
   if (tid == 0) s_tiles = 0;
 
-  for (int j = 0; j < njobs; ++j) {
+  for (int jj = 0; jj < njobs; ++jj) {
+    int j = first + jj;
+    if (j >= njobs) j -= njobs;
     __syncthreads();
     if (tid == 0) {
       int skip = 1;
@@ -802,7 +805,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
 
 // Resets the states of a job table and its step control block.
 __global__ void init_steps_kernel(JobState* states, int njobs, StepCtl* ctl, unsigned max_steps,
-                                  unsigned tiles_per_warp) {
+                                  unsigned tiles_per_warp, unsigned rotate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < njobs) {
     unsigned long long* w = reinterpret_cast<unsigned long long*>(&states[i]);
@@ -814,6 +817,7 @@ __global__ void init_steps_kernel(JobState* states, int njobs, StepCtl* ctl, uns
     ctl->active_jobs = (unsigned)njobs;
     ctl->steps = 0;
     ctl->max_steps = max_steps;
+    ctl->rotate = rotate;
   }
 }
 
@@ -1009,17 +1013,18 @@ cudaError_t add_step_node(cudaGraph_t g, int kind, int p, const JobDesc* d_jobs,
 }
 
 cudaError_t launch_init_steps(JobState* d_states, int njobs, StepCtl* d_ctl, unsigned max_steps,
-                              unsigned tiles_per_warp, cudaStream_t s) {
+                              unsigned tiles_per_warp, unsigned rotate, cudaStream_t s) {
   init_steps_kernel<<<(njobs + 255) / 256, 256, 0, s>>>(d_states, njobs, d_ctl, max_steps,
-                                                        tiles_per_warp);
+                                                        tiles_per_warp, rotate);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl* d_ctl,
-                          unsigned max_steps, unsigned tiles_per_warp, cudaGraphNode_t* node) {
+                          unsigned max_steps, unsigned tiles_per_warp, unsigned rotate,
+                          cudaGraphNode_t* node) {
   void* args[] = {(void*)&d_states, (void*)&njobs, (void*)&d_ctl, (void*)&max_steps,
-                  (void*)&tiles_per_warp};
+                  (void*)&tiles_per_warp, (void*)&rotate};
   cudaKernelNodeParams kp = {};
   kp.func = (void*)init_steps_kernel;
   kp.gridDim = dim3((njobs + 255) / 256);
@@ -1030,12 +1035,12 @@ cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl*
 
 cudaError_t build_step_graph(int kind, int p, const JobDesc* d_jobs, JobState* d_states,
                              int njobs, StepCtl* d_ctl, int grid, int block, size_t smem,
-                             unsigned max_steps, cudaGraphExec_t* exec) {
+                             unsigned max_steps, unsigned rotate, cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return e;
   cudaGraphNode_t init;
-  e = add_init_node(g, d_states, njobs, d_ctl, max_steps, 0, &init);
+  e = add_init_node(g, d_states, njobs, d_ctl, max_steps, 0, rotate, &init);
   cudaGraphConditionalHandle h;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
   cudaGraphNodeParams cp = {};

@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--cand-subrange", type=int, default=1 << 27,
                     help="candidates of the roofline_cand sub-range run (0 = skip)")
-    ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single",
+    ap.add_argument("--mode", choices=["single", "batch", "serve", "cpu-scaling"], default="single",
                     help="single: the driver's (l,d) line; batch: 64 uneven jobs batched vs one "
                          "job per launch; serve: Poisson arrivals, p50/p99 latency per rate")
     ap.add_argument("--rates", default="1,2,5,10,20,50,100,200")
@@ -417,6 +417,19 @@ def run_batch(args):
             m.motif_batch_search(plans, use_graph=False)
         t_batch_nograph = (time.perf_counter() - t0) / reps
         survivors = sum(int(r.size) for r in batch_res)
+        # Per-job view of both paths (the slowest plain jobs, and the batch's phase split).
+        per_job = []
+        for j, pl, r in zip(js, plans, plain_res):
+            t1 = time.perf_counter()
+            m.motif_search(pl)
+            dt = time.perf_counter() - t1
+            stp = m.motif_stats(pl)
+            per_job.append({"l": j.l, "d": j.d, "n": j.n, "t": j.t, "survivors": int(r.size),
+                            "plain_ms": 1e3 * dt, "search_ms": stp["search_ms"],
+                            "sort_ms": stp["sort_ms"]})
+        per_job.sort(key=lambda x: -x["plain_ms"])
+        m.motif_batch_search(plans, use_graph=True)
+        stb = m.motif_stats(plans[0])
         out[label] = {
             "jobs": len(js), "candidates": cands, "algorithmic_compares": compares,
             "survivors": survivors,
@@ -425,6 +438,12 @@ def run_batch(args):
             "plain_jobs_per_s": len(js) / t_plain, "batched_jobs_per_s": len(js) / t_batch,
             "plain_compares_per_s": compares / t_plain, "batched_compares_per_s": compares / t_batch,
             "batched_over_plain": t_plain / t_batch,
+            "batch_device_steps_ms": stb["search_ms"], "batch_device_sort_ms": stb["sort_ms"],
+            "batch_copy_to_host_ms": stb["queue_ms"],
+            "plain_device_ms": sum(x["search_ms"] + x["sort_ms"] for x in per_job),
+            "batched_over_plain_device": sum(x["search_ms"] + x["sort_ms"] for x in per_job)
+                                          / max(stb["search_ms"] + stb["sort_ms"], 1e-9),
+            "slowest_plain_jobs": per_job[:8],
         }
         for pl in plans:
             m.motif_plan_destroy(pl)
@@ -503,10 +522,46 @@ def run_serve(args):
     return 0
 
 
+def run_cpu_scaling(args):
+    """Speedup of the CPU oracle over its single thread as the thread count grows, on a fixed
+    sub-range of each (l,d) workload: the shape of the paper's Fig. 3/4 and Table II (multicore
+    speedups over one thread), measured on this machine's host cores."""
+    from oracle import oracle
+    from paper_1403_1313_gb300 import fmgen
+    cores = os.cpu_count() or 1
+    threads = sorted({1, 2, 4, 8, 16, 32, 64, cores} & set(range(1, 2 * cores + 1)))
+    rows = []
+    for (l, d) in ((11, 3), (12, 3), (13, 3), (14, 4), (15, 4)):
+        job = fmgen.fm_job(20, 600, l, d, 1000 + l)
+        lo = (4 ** l) // 3
+        size = 1 << 15
+        t0 = time.perf_counter()
+        ref, _ = oracle.search(job.rows(), l, d, lo=lo, hi=lo + size, threads=1)
+        base = time.perf_counter() - t0
+        # size the sample for about one second of single-thread work
+        size = int(max(size, size * 1.0 / max(base, 1e-6)))
+        t0 = time.perf_counter()
+        ref, _ = oracle.search(job.rows(), l, d, lo=lo, hi=lo + size, threads=1)
+        base = time.perf_counter() - t0
+        sp = {}
+        for th in threads:
+            t0 = time.perf_counter()
+            got, _ = oracle.search(job.rows(), l, d, lo=lo, hi=lo + size, threads=th)
+            dt = time.perf_counter() - t0
+            assert got.tolist() == ref.tolist()
+            sp[th] = base / dt
+        rows.append({"l": l, "d": d, "candidates": size, "t1_s": base, "speedup": sp})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"mode": "cpu-scaling", "cores": cores, "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "cpu-scaling":
+        return run_cpu_scaling(args)
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":

@@ -88,7 +88,8 @@ typedef struct {
   double search_ms;              /* device time of the search kernel, last search */
   double sort_ms;                /* device time of sort/dedup, last search */
   double total_ms;               /* host wall time of the last motif_search or served job */
-  double queue_ms;               /* served job: submit -> admission */
+  double queue_ms;               /* served job: submit -> admission; batched job: device-to-host
+                                    result copy time of its batch */
   int64_t device_bytes;          /* device memory held by the plan */
   int32_t smem_bytes;            /* dynamic shared memory per CTA of the search kernel */
   int32_t kernel;                /* kernel that ran (motif_kernel) */

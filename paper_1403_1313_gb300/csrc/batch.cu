@@ -144,9 +144,16 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     if (e == cudaSuccess)
       e = launch_init_steps(c->d_states, (int)ids.size(), c->d_ctl, 0, 0, 1, c->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (auto& x : ev) cudaEventCreate(&x);
+    cudaEventRecord(ev[0], c->stream);
     rc = run_table(c, kind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
                    timeout);
-    if (rc) return rc;
+    cudaEventRecord(ev[1], c->stream);
+    if (rc) {
+      for (auto& x : ev) cudaEventDestroy(x);
+      return rc;
+    }
     std::vector<JobState> st(ids.size());
     e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
                         cudaMemcpyDeviceToHost, c->stream);
@@ -179,6 +186,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       if (e != cudaSuccess) return status_from_cuda(e);
       sorted[i] = 1;
     }
+    cudaEventRecord(ev[2], c->stream);  // sorts done
     e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -200,8 +208,19 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         if (e != cudaSuccess) return status_from_cuda(e);
       }
     }
+    cudaEventRecord(ev[3], c->stream);
     e = cudaStreamSynchronize(c->stream);
+    float steps_ms = 0, sort_ms = 0, copy_ms = 0;
+    cudaEventElapsedTime(&steps_ms, ev[0], ev[1]);
+    cudaEventElapsedTime(&sort_ms, ev[1], ev[2]);
+    cudaEventElapsedTime(&copy_ms, ev[2], ev[3]);
+    for (auto& x : ev) cudaEventDestroy(x);
     if (e != cudaSuccess) return status_from_cuda(e);
+    for (size_t i = 0; i < ids.size(); ++i) {  // the group's device times, shared by its jobs
+      plans[ids[i]]->stats.search_ms = steps_ms;
+      plans[ids[i]]->stats.sort_ms = sort_ms;
+      plans[ids[i]]->stats.queue_ms = copy_ms;  // result copy to the host
+    }
   }
   for (int j = 0; j < njobs; ++j) {
     if (!redo[j]) continue;
@@ -263,6 +282,7 @@ extern "C" int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best)
     }
   }
   std::vector<Choice> cands;
+  if (p->l >= 8) cands.push_back({MOTIF_KERNEL_TILED, 256, 0, 0, 0, 4, 0});
   for (int ks = 2; ks <= kMaxKs; ++ks) {
     if (ks > p->l) break;
     for (int span : {1, 2})

@@ -492,16 +492,19 @@ __device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsig
 // and differ in the last 4 prefix bases (P2 = the lane index); each lane carries the 256
 // suffixes of its group.  Since Ham = Ham(P1) + Ham(P2) + Ham(suffix), per sequence:
 //   1. filter: the CTA computes h1 = Ham(P1, window) once per window; only windows with
-//      h1 <= d can match any of the tile's 65536 candidates, and they are compacted into a list
-//      with, per entry, the 256-bit mask of P2 values within d-h1 of the window (a row of the
-//      4-base ball table), stored word-major so that each warp reads the word of its 32 lanes;
-//   2. scan: 32 listed entries at a time, each warp transposes the 32 words of its lanes into
-//      one 32-bit mask per lane of the entries it hits (no POPC in this loop);
+//      h1 <= d can match any of the tile's 65536 candidates.  A window with h1 = d matches
+//      exactly one of them (its own last 8 bases), so its lane sets that bit in a 65536-bit map
+//      of the tile in shared memory.  The other windows are compacted into a list with, per
+//      entry, the 256-bit mask of P2 values within d-h1 of the window (a row of the 4-base ball
+//      table), stored word-major so that each warp reads the word of its 32 lanes;
+//   2. each lane ORs its 256 bits of the map into its matched mask and clears them; then,
+//      32 listed entries at a time, each warp transposes the 32 words of its lanes into one
+//      32-bit mask per lane of the entries it hits (no POPC in this loop);
 //   3. hits: per hit entry the lane computes h2 = Ham(P2, window) and ORs in the suffixes
 //      within d-h1-h2 of the window's last 4 bases.
-// A lane with no live candidate left idles; a warp with none skips the scan; the CTA stops when
-// no lane has a live candidate (the skip).  Every sequence is handled inside the tile, so this
-// pass accepts its survivors directly.
+// A lane with no live candidate left skips its hits; a warp with none skips the scan; the CTA
+// stops when no lane has a live candidate (the skip).  Every sequence is handled inside the
+// tile, so this pass accepts its survivors directly.
 
 // One hit of lane (P2E, P2O) on listed entry k: OR in the suffixes within d-h1-h2 of the
 // window's last 4 bases (h1 and the window's P2 planes are in the entry's head word).
@@ -534,7 +537,7 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 
 __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
                             unsigned long long tbase, uint32_t* head, uint16_t* vsuf,
-                            uint32_t* maskw, unsigned* s_cnt /* [2] */) {
+                            uint32_t* maskw, uint32_t* map, unsigned* s_cnt /* [2] */) {
   constexpr int KS = 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wcap = jd.wstride;
@@ -566,8 +569,12 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
         wE = w.x >> KS;
         wO = w.y >> KS;
         const int h1 = __popc(((wE >> 4) ^ P1E) | ((wO >> 4) ^ P1O));
-        keep = h1 <= jd.d;
         r1 = jd.d - h1;
+        if (r1 == 0) {  // one candidate: the window's own last 8 bases
+          const uint32_t v = (uint32_t)__ldg(crow + j) & 0xFFFFu;
+          atomicOr(map + (v >> 5), 1u << (v & 31u));
+        }
+        keep = r1 > 0;
       }
       const unsigned bal = __ballot_sync(kFull, keep);
       unsigned wb = 0;
@@ -596,16 +603,27 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     if (tid == 0) s_cnt[(s + 1) & 1] = 0;  // the next sequence's list count
     __syncthreads();
     const int K = (int)*cnt;
-    // 2. scan: 32 listed entries at a time; a warp transpose turns the entries' words for this
-    //    warp's 32 lanes into one 32-bit hit mask per lane.  3. OR in each hit's suffix ball.
+    const bool lane_live = any_set<KS>(alive);
+    // 2. take this lane's bits of the map (the P2 code of lane tid is tid) and clear them;
+    //    then scan 32 listed entries at a time: a warp transpose turns the entries' words for
+    //    this warp's 32 lanes into one 32-bit hit mask per lane.  3. OR in each hit's suffix ball.
     GroupMask<KS> matched;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) matched.w[i] = 0;
-    if (__any_sync(kFull, any_set<KS>(alive))) {
+    {
+      uint4* own = reinterpret_cast<uint4*>(map) + 2 * tid;
+      const uint4 m0 = own[0], m1 = own[1];
+      matched.w[0] = (uint64_t)m0.x | ((uint64_t)m0.y << 32);
+      matched.w[1] = (uint64_t)m0.z | ((uint64_t)m0.w << 32);
+      matched.w[2] = (uint64_t)m1.x | ((uint64_t)m1.y << 32);
+      matched.w[3] = (uint64_t)m1.z | ((uint64_t)m1.w << 32);
+      own[0] = make_uint4(0u, 0u, 0u, 0u);
+      own[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (__any_sync(kFull, lane_live)) {
       const uint32_t* mrow = maskw + warp * wcap;
       for (int k = 0; k < K; k += 32) {
         uint32_t x = k + lane < K ? mrow[k + lane] : 0u;
         x = warp_transpose32(x, lane);
+        if (!lane_live) x = 0;
         while (x) {
           const int i = __ffs(x) - 1;
           x &= x - 1;
@@ -706,6 +724,9 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       size_t moff = wc * 6;
       moff += 16 - moff % 16;
       uint32_t* maskw = reinterpret_cast<uint32_t*>(smem + moff);
+      // The tile map of single-candidate windows starts cleared; every tile leaves it cleared.
+      uint32_t* map = maskw + wc * 8;
+      for (int i = tid; i < 2048; i += blockDim.x) map[i] = 0u;
       for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -717,7 +738,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
         __syncthreads();
         const unsigned long long b = s_tbase;
         if (b >= p.work) break;
-        group_tiled(jd, st, p, b, head, vsuf, maskw, s_tcnt);
+        group_tiled(jd, st, p, b, head, vsuf, maskw, map, s_tcnt);
       }
       continue;
     }
@@ -952,10 +973,11 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
   b += (size_t)kHitCap * block * 4;
-  if (p == 4) {  // the prefix-tiled pass: list heads, suffix values, 8 mask words per entry
+  if (p == 4) {  // the prefix-tiled pass: list heads, suffix values, 8 mask words per entry,
+                 // and the 8 KB map of single-candidate windows
     size_t t = (size_t)wstride * 6;
     t += 16 - t % 16;
-    t += (size_t)wstride * 32;
+    t += (size_t)wstride * 32 + 8192;
     if (t > b) b = t;
   }
   return b;

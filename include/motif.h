@@ -58,6 +58,15 @@ typedef enum {
                              (l-8)-base prefix (needs l >= 8; falls back to GROUP otherwise) */
 } motif_kernel;
 
+/* How a search collects the accepted codes before returning them in ascending order (not in the
+ * paper, whose output is the surviving l-mers, Sec. III.A; a GPU design choice). */
+typedef enum {
+  MOTIF_OUTPUT_AUTO = 0,   /* BITMAP where the expected survivors are dense, else LIST */
+  MOTIF_OUTPUT_LIST = 1,   /* append codes to a list, then sort and deduplicate it */
+  MOTIF_OUTPUT_BITMAP = 2  /* set one bit per code of the range, then compact the set bits in
+                              order; needs (range length)/8 bytes of device memory */
+} motif_output;
+
 typedef struct motif_plan_s* motif_plan;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a device
@@ -74,6 +83,7 @@ typedef struct {
   int32_t compact_levels;   /* CAND kernel: sequences with a survivor queue; 0 = tuned */
   int32_t suffix_bases;     /* GROUP kernel: k, suffix bases enumerated in one lane; 0 = tuned */
   int32_t timeout_ms;       /* bound on every device-side and host-side wait; 0 = 60000 */
+  int32_t output;           /* motif_output */
   motif_alloc_fn alloc;     /* NULL = cudaMallocAsync / cudaFreeAsync on the plan's stream */
   motif_free_fn free;
   void* alloc_ctx;

@@ -29,6 +29,7 @@ __all__ = [
     "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
     "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED",
+    "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -40,6 +41,7 @@ OK, PENDING = 0, 1
 ERR_ARG, ERR_ALPHABET, ERR_CAPACITY, ERR_OOM = -1, -2, -3, -4
 ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_NOTFOUND = -5, -6, -7, -8, -9
 KERNEL_AUTO, KERNEL_CAND, KERNEL_GROUP, KERNEL_TILED = 0, 1, 2, 3
+OUTPUT_AUTO, OUTPUT_LIST, OUTPUT_BITMAP = 0, 1, 2
 
 PROBE_KINDS = ["POPC", "LOP3", "IMNMX", "SHF", "IADD", "IMAD", "POPC_LOP3", "CMP_SPLIT",
                "CMP_FOLD", "LDS64_DIV"]
@@ -53,7 +55,8 @@ class motif_opts(ctypes.Structure):
         ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int32), ("block", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32), ("cands_per_thread", ctypes.c_int32),
         ("compact_levels", ctypes.c_int32), ("suffix_bases", ctypes.c_int32),
-        ("timeout_ms", ctypes.c_int32), ("alloc", _ALLOC_FN), ("free", _FREE_FN),
+        ("timeout_ms", ctypes.c_int32), ("output", ctypes.c_int32), ("alloc", _ALLOC_FN),
+        ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p), ("range_lo", ctypes.c_uint64),
         ("range_hi", ctypes.c_uint64),
     ]
@@ -224,6 +227,18 @@ def motif_load_seqs_device(plan: Plan, d_seqs, stride: int | None = None) -> Non
     _check(_load().motif_load_seqs_device(plan, ctypes.c_void_p(ptr), stride), "motif_load_seqs_device")
 
 
+def _host_codes(capacity: int) -> np.ndarray:
+    # Uninitialised memory: the library writes every returned element.  (Zero-filled arrays come
+    # from calloc'd pages whose first touch by the device copy is far slower on some hosts.)
+    return np.empty(max(int(capacity), 1), dtype=np.uint64)
+
+
+def _trimmed(out: np.ndarray, count: int) -> np.ndarray:
+    """The first `count` codes; a copy only when that frees most of the buffer."""
+    count = int(count)
+    return out[:count] if 2 * count >= out.size else out[:count].copy()
+
+
 def motif_search(plan: Plan, capacity: int | None = None) -> np.ndarray:
     """Blocking search; returns the ascending accepted codes.  The output buffer starts at the
     plan's capacity hint (the size of its previous result) and grows on demand."""
@@ -231,7 +246,7 @@ def motif_search(plan: Plan, capacity: int | None = None) -> np.ndarray:
     if capacity is None:
         capacity = plan.capacity_hint
     while True:
-        out = np.zeros(max(capacity, 1), dtype=np.uint64)
+        out = _host_codes(capacity)
         cnt = ctypes.c_int64(0)
         st = lib.motif_search(plan, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), capacity,
                               ctypes.byref(cnt))
@@ -240,7 +255,7 @@ def motif_search(plan: Plan, capacity: int | None = None) -> np.ndarray:
             continue
         _check(st, "motif_search")
         plan.capacity_hint = max(plan.capacity_hint, int(cnt.value))
-        return out[:cnt.value].copy()
+        return _trimmed(out, cnt.value)
 
 
 def motif_search_device(plan: Plan, d_out, capacity: int, d_count) -> None:
@@ -287,7 +302,7 @@ def motif_batch_search(plans, use_graph: bool = True, capacity: int | None = Non
     k = len(plans)
     caps = [capacity if capacity is not None else p.capacity_hint for p in plans]
     while True:
-        outs = [np.zeros(max(c, 1), dtype=np.uint64) for c in caps]
+        outs = [_host_codes(c) for c in caps]
         handles = (ctypes.c_void_p * k)(*[p.handle for p in plans])
         ptrs = (ctypes.POINTER(ctypes.c_uint64) * k)(
             *[o.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) for o in outs])
@@ -303,7 +318,7 @@ def motif_batch_search(plans, use_graph: bool = True, capacity: int | None = Non
         _check(st, "motif_batch_search")
         for j, p in enumerate(plans):
             p.capacity_hint = max(p.capacity_hint, int(counts[j]))
-        return [outs[j][:counts[j]].copy() for j in range(k)]
+        return [_trimmed(outs[j], counts[j]) for j in range(k)]
 
 
 def motif_autotune(plan: Plan, budget_ms: int = 2000) -> motif_opts:
@@ -342,7 +357,7 @@ def motif_poll(job_id: int, timeout_ms: int = 0, capacity: int = 1 << 16):
     """Returns (codes, stats dict) when the job is done, or None while it is pending."""
     lib = _load()
     while True:
-        out = np.zeros(max(capacity, 1), dtype=np.uint64)
+        out = _host_codes(capacity)
         cnt = ctypes.c_int64(0)
         s = motif_stats_t()
         st = lib.motif_poll(job_id, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), capacity,
@@ -353,7 +368,7 @@ def motif_poll(job_id: int, timeout_ms: int = 0, capacity: int = 1 << 16):
             capacity = cnt.value
             continue
         _check(st, "motif_poll")
-        return out[:cnt.value].copy(), _stats_dict(s)
+        return _trimmed(out, cnt.value), _stats_dict(s)
 
 
 # ---- helpers -------------------------------------------------------------------------------------

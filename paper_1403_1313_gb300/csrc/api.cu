@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 
@@ -128,6 +129,22 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->qcap = p->qcap;
   jd->out = out; jd->out_cap = out_cap;
   jd->ball = p->kind == MOTIF_KERNEL_GROUP ? ball_table(p->device, p->p, p->stream) : nullptr;
+  jd->bitmap = p->bitmap ? p->d_bitmap : nullptr;
+  jd->bm_base = p->bm_base;
+}
+
+// Expected number of accepted codes of the plan's range for uniform i.i.d. bases: a window
+// matches a candidate with probability pw = sum_{k<=d} C(l,k) 3^k / 4^l, a sequence with
+// q = 1 - (1 - pw)^W, all n sequences with q^n.
+static double expected_survivors(const motif_plan_s* p) {
+  double term = 1.0, sum = 0.0;  // C(l,k) 3^k
+  for (int k = 0; k <= std::min(p->d, p->l); ++k) {
+    sum += term;
+    term = term * (p->l - k) / (k + 1) * 3.0;
+  }
+  const double pw = std::min(1.0, sum / std::pow(4.0, p->l));
+  const double q = pw >= 1.0 ? 1.0 : -std::expm1((double)p->W * std::log1p(-pw));
+  return (double)(p->hi - p->lo) * std::pow(q, p->n);
 }
 
 static void free_queues(motif_plan_s* p) {
@@ -184,6 +201,20 @@ int plan_configure(motif_plan_s* p) {
   const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
   p->tiled = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 && p->l >= 8 &&
              p->W <= 65535 && unit_lo % 256 == 0 && (chunk % 256 == 0 || units <= chunk);
+  // Output: a bitmap over the range (rounded out to whole 256-code groups) where it holds at
+  // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size.
+  const uint64_t bm_base = p->lo & ~255ull;
+  const uint64_t bm_bits = ((p->hi + 255) & ~255ull) - bm_base;
+  if (o.output < MOTIF_OUTPUT_AUTO || o.output > MOTIF_OUTPUT_BITMAP) return MOTIF_ERR_ARG;
+  bool bitmap = o.output == MOTIF_OUTPUT_BITMAP ||
+                (o.output == MOTIF_OUTPUT_AUTO && expected_survivors(p) * 2048.0 >= (double)bm_bits);
+  if (bm_bits > (1ull << 31)) {
+    if (o.output == MOTIF_OUTPUT_BITMAP) return MOTIF_ERR_ARG;
+    bitmap = false;
+  }
+  p->bitmap = bitmap && p->hi > p->lo;
+  p->bm_base = bm_base;
+  p->bm_words = p->bitmap ? bm_bits / 32 : 0;
   p->kind = kind;
   p->p = pv;
   p->span0 = span0;
@@ -210,6 +241,14 @@ void invalidate_graphs(motif_plan_s* p) {
   p->gs_scratch = nullptr;
 }
 
+void free_bitmap(motif_plan_s* p) {
+  if (p->d_bitmap) plan_free(p, p->d_bitmap, p->bm_alloc_words * 4);
+  if (p->d_bm_scratch) plan_free(p, p->d_bm_scratch, bitmap_scratch_words(p->bm_alloc_words) * 4);
+  p->d_bitmap = nullptr;
+  p->d_bm_scratch = nullptr;
+  p->bm_alloc_words = 0;
+}
+
 int plan_ensure_buffers(motif_plan_s* p) {
   if (!p->d_qidx[0]) {
     invalidate_graphs(p);
@@ -229,6 +268,17 @@ int plan_ensure_buffers(motif_plan_s* p) {
     p->d_out = (uint64_t*)plan_alloc(p, (size_t)(1 << 16) * 8);
     if (!p->d_out) return MOTIF_ERR_OOM;
     p->out_cap = 1 << 16;
+  }
+  if (p->bitmap && p->bm_alloc_words != p->bm_words) {
+    free_bitmap(p);
+    p->d_bitmap = (uint32_t*)plan_alloc(p, p->bm_words * 4);
+    p->d_bm_scratch = (unsigned*)plan_alloc(p, bitmap_scratch_words(p->bm_words) * 4);
+    p->desc_out = nullptr;  // the descriptor names the bitmap
+    if (!p->d_bitmap || !p->d_bm_scratch) {
+      free_bitmap(p);
+      return MOTIF_ERR_OOM;
+    }
+    p->bm_alloc_words = p->bm_words;
   }
   return MOTIF_OK;
 }
@@ -323,6 +373,10 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
     cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
     return status_from_cuda(e);
   }
+  if (p->bitmap) {
+    cudaError_t e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
   // Upload the descriptor when (out, cap) changed; it lives in pinned memory so the copy is
   // stream-ordered without blocking the host.
   if (p->desc_out != out || p->desc_cap != (int64_t)cap) {
@@ -365,6 +419,53 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
 __global__ void finalize_count_kernel(const int* err, const unsigned long long* count,
                                       int64_t* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *out = *err ? -1 : (int64_t)*count;
+}
+
+// Compacts the plan's bitmap into (out, cap) on its stream; the count goes to the job state.
+int compact_bitmap(motif_plan_s* p, uint64_t* out, int64_t cap) {
+  return status_from_cuda(launch_bitmap_compact(p->d_bitmap, p->bm_words, p->bm_base, out, cap,
+                                                p->d_bm_scratch, &p->d_state->out_count,
+                                                p->stream));
+}
+
+// motif_search with bitmap output: one search, then compactions of the same bitmap until the
+// plan's buffer holds every code (no second search), then the copy to the caller.
+int search_bitmap(motif_plan_s* p, uint64_t* out_codes, int64_t capacity, int64_t* out_count,
+                  cudaEvent_t* ev, double t0) {
+  cudaEventRecord(ev[0], p->stream);
+  int rc = enqueue_search(p, p->d_out, (uint64_t)p->out_cap, true);
+  if (rc) return rc;
+  cudaEventRecord(ev[1], p->stream);
+  cudaEventRecord(ev[2], p->stream);
+  unsigned long long found = 0;
+  for (;;) {
+    rc = compact_bitmap(p, p->d_out, p->out_cap);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(&found, &p->d_state->out_count, sizeof(found),
+                                    cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (found <= (unsigned long long)p->out_cap) break;
+    rc = ensure_out(p, (int64_t)found);
+    if (rc) return rc;
+  }
+  cudaEventRecord(ev[3], p->stream);
+  *out_count = (int64_t)found;
+  rc = fold_event_quads(p);
+  if (rc) return rc;
+  p->stats.survivors = found;
+  if ((int64_t)found > capacity) {
+    p->stats.total_ms = now_ms() - t0;
+    return MOTIF_ERR_CAPACITY;
+  }
+  if (found) {
+    cudaError_t e = cudaMemcpyAsync(out_codes, p->d_out, found * 8, cudaMemcpyDeviceToHost,
+                                    p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  p->stats.total_ms = now_ms() - t0;
+  return MOTIF_OK;
 }
 
 }  // namespace motif_api
@@ -457,6 +558,7 @@ void motif_plan_destroy(motif_plan p) {
   plan_free(p, p->d_total, sizeof(unsigned long long));
   plan_free(p, p->d_out, (size_t)p->out_cap * 8);
   plan_free(p, p->d_sort, p->sort_bytes);
+  free_bitmap(p);
   cudaStreamSynchronize(p->stream);
   for (cudaEvent_t ev : p->evq)
     if (ev) cudaEventDestroy(ev);
@@ -518,6 +620,7 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   unsigned long long found = 0;
   cudaEvent_t* ev = next_event_quad(p);
   if (!ev) return MOTIF_ERR_CUDA;
+  if (p->bitmap) return search_bitmap(p, out_codes, capacity, out_count, ev, t0);
   for (;;) {
     cudaEventRecord(ev[0], p->stream);
     rc = plan_ensure_buffers(p);
@@ -575,13 +678,24 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
   p->stats.grid = p->grid;
   p->stats.block = p->block;
   p->stats.smem_bytes = (int32_t)p->smem;
-  if (capacity > 4096) {
+  if (capacity > 4096 && !p->bitmap) {
     rc = ensure_sort(p, capacity);
     if (rc) return rc;
   }
   if (p->W <= 0 || p->hi <= p->lo) {
     cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
+  } else if (p->bitmap) {
+    cudaEvent_t* ev = next_event_quad(p);
+    if (!ev) return MOTIF_ERR_CUDA;
+    cudaEventRecord(ev[0], p->stream);
+    rc = enqueue_search(p, d_out_codes, (uint64_t)capacity, false);
+    if (rc) return rc;
+    cudaEventRecord(ev[1], p->stream);
+    cudaEventRecord(ev[2], p->stream);
+    rc = compact_bitmap(p, d_out_codes, capacity);
+    cudaEventRecord(ev[3], p->stream);
+    if (rc) return rc;
   } else {
     cudaEvent_t* ev = next_event_quad(p);
     if (!ev) return MOTIF_ERR_CUDA;

@@ -140,6 +140,10 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     if (grid <= 0) return MOTIF_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(c->d_jobs, descs.data(), sizeof(JobDesc) * ids.size(),
                                     cudaMemcpyHostToDevice, c->stream);
+    for (size_t i = 0; i < ids.size() && e == cudaSuccess; ++i) {
+      motif_plan_s* p = plans[ids[i]];
+      if (p->bitmap) e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, c->stream);
+    }
     // Zero the states; CTAs rotate their starting job so every job's tiles start at once.
     if (e == cudaSuccess)
       e = launch_init_steps(c->d_states, (int)ids.size(), c->d_ctl, 0, 0, 1, c->stream);
@@ -170,6 +174,13 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         redo[j] = 1;  // the plan's own buffer was too small: rerun this job alone below
         continue;
       }
+      if (p->bitmap) {  // compact the job's bitmap into its buffer (count into its state)
+        e = launch_bitmap_compact(p->d_bitmap, p->bm_words, p->bm_base, p->d_out, p->out_cap,
+                                  p->d_bm_scratch, &c->d_states[i].out_count, c->stream);
+        if (e != cudaSuccess) return status_from_cuda(e);
+        sorted[i] = 1;
+        continue;
+      }
       if (found > 4096) {
         const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
         if (need > p->sort_bytes) {
@@ -196,6 +207,10 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       const int j = ids[i];
       motif_plan_s* p = plans[j];
       const unsigned long long fc = st[i].out_count;
+      if (fc > (unsigned long long)p->out_cap) {  // a bitmap job outgrew the plan's buffer
+        redo[j] = 1;
+        continue;
+      }
       out_counts[j] = (int64_t)fc;
       p->stats.survivors = fc;
       p->stats.candidates = p->hi - p->lo;

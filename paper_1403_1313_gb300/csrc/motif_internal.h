@@ -35,6 +35,8 @@ struct JobDesc {
   uint64_t* out;             // accepted codes, appended
   uint64_t out_cap;
   const uint64_t* ball;      // GROUP: Hamming-ball table for ks (see ball_table_words)
+  uint32_t* bitmap;          // non-null: accepted codes set bit (code - bm_base) here instead of
+  uint64_t bm_base;          //   being appended to out (bm_base is a multiple of 64)
 };
 
 // Per-job device state, advanced by the last CTA of every step.
@@ -110,6 +112,13 @@ cudaError_t launch_count_group(const JobDesc* d_job, int ks, unsigned long long*
 // Sorts d_codes[0 .. *d_count) ascending and removes repeats in place (count updated) when
 // *d_count <= cap.  known_count >= 0 lets the host skip the path that cannot apply.
 size_t sort_scratch_bytes(int64_t cap, int sms);
+// Bitmap output: writes the codes base + i of the set bits i of bm (nwords 32-bit words) to out
+// in ascending order (at most cap of them) and their number to *count.  scratch holds
+// bitmap_scratch_words(nwords) words.
+uint64_t bitmap_scratch_words(uint64_t nwords);
+cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t base,
+                                  uint64_t* out, int64_t cap, unsigned* scratch,
+                                  unsigned long long* count, cudaStream_t s);
 cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, int64_t cap,
                                int key_bits, void* scratch, int sms, long long known_count,
                                cudaStream_t s);

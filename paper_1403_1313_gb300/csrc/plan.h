@@ -43,6 +43,13 @@ struct motif_plan_s {
   int64_t out_cap = 0;
   void* d_sort = nullptr;
   size_t sort_bytes = 0;
+  // Bitmap output (MOTIF_OUTPUT_BITMAP): one bit per code of [bm_base, bm_base + 32*bm_words),
+  // and the compaction's block counts.
+  bool bitmap = false;
+  uint64_t bm_base = 0, bm_words = 0;
+  uint32_t* d_bitmap = nullptr;
+  unsigned* d_bm_scratch = nullptr;
+  uint64_t bm_alloc_words = 0;
   motif::JobDesc* d_job = nullptr;
   motif::JobState* d_state = nullptr;
   motif::StepCtl* d_ctl = nullptr;
@@ -88,6 +95,7 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
 int plan_configure(motif_plan_s* p);
 // Allocates the survivor queues and the default output buffer on first use.
 int plan_ensure_buffers(motif_plan_s* p);
+void free_bitmap(motif_plan_s* p);
 // Drops the plan's cached graphs and descriptor upload (after a configuration change).
 void invalidate_graphs(motif_plan_s* p);
 

@@ -70,6 +70,12 @@ __device__ __forceinline__ int ld_volatile(const int32_t* p) {
 
 // Reserves `cnt` slots per lane at `counter` with one atomic per warp; returns this lane's
 // first slot.  Must be called by all 32 lanes.
+// Records one accepted code in the job's bitmap.
+__device__ __forceinline__ void bitmap_set(const JobDesc& jd, uint64_t code) {
+  const uint64_t b = code - jd.bm_base;
+  atomicOr(jd.bitmap + (b >> 5), 1u << (unsigned)(b & 31));
+}
+
 __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter,
                                                            unsigned cnt) {
   const int lane = threadIdx.x & 31;
@@ -197,7 +203,11 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
     alive = scan_cand<CPT>(stage + (size_t)(s - p.s0) * (wpad >> 1), wpad, jd.d, E, O, alive);
   __syncwarp();
   const unsigned cnt = __popc(alive);
-  if (p.s1 >= jd.n) {
+  if (p.s1 >= jd.n && jd.bitmap) {
+#pragma unroll
+    for (int c = 0; c < CPT; ++c)
+      if (alive & (1u << c)) bitmap_set(jd, p.chunk_base + off[c]);
+  } else if (p.s1 >= jd.n) {
     unsigned long long slot = warp_reserve(&st->out_count, cnt);
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
@@ -237,7 +247,9 @@ __device__ void cand_rest(const JobDesc& jd, JobState* st, const Pass& p,
     }
     if (!matched) return;  // the skip: no window of sequence s is within d
   }
-  if (lane == 0) {
+  if (lane == 0 && jd.bitmap) {
+    bitmap_set(jd, k);
+  } else if (lane == 0) {
     const unsigned long long slot = atomicAdd(&st->out_count, 1ull);
     if (slot < jd.out_cap) jd.out[slot] = k;
   }
@@ -381,11 +393,25 @@ template <int KS>
 __device__ __forceinline__ void group_output(const JobDesc& jd, JobState* st, uint64_t g,
                                              const GroupMask<KS>& alive) {
   constexpr int NW = GroupMask<KS>::NW;
+  const uint64_t first = g << (2 * KS);
+  if (jd.bitmap) {  // group bits are contiguous codes: OR the mask words in (first - bm_base is
+                    // a multiple of 64 for KS >= 3, of the 4 or 16 mask bits below that)
+    const uint64_t b = first - jd.bm_base;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      if (!alive.w[i]) continue;
+      if (KS >= 3)
+        atomicOr(reinterpret_cast<unsigned long long*>(jd.bitmap + ((b >> 5) + 2 * i)),
+                 (unsigned long long)alive.w[i]);
+      else
+        atomicOr(jd.bitmap + (b >> 5), (uint32_t)alive.w[i] << (unsigned)(b & 31));
+    }
+    return;
+  }
   unsigned cnt = 0;
 #pragma unroll
   for (int i = 0; i < NW; ++i) cnt += __popcll(alive.w[i]);
   unsigned long long slot = warp_reserve(&st->out_count, cnt);
-  const uint64_t first = g << (2 * KS);
 #pragma unroll
   for (int i = 0; i < NW; ++i) {
     uint64_t w = alive.w[i];

@@ -150,6 +150,38 @@ __global__ void __launch_bounds__(kRadixThreads) scan_kernel(unsigned* __restric
   }
 }
 
+// Exclusive scan of a digit-major histogram hist[digit * ctas + cta], taken in (digit, cta)
+// order: thread `digit` sums its row, the CTA scans the row totals, and each thread rewrites its
+// row as running offsets from its digit's base.  One CTA of kDigits threads.
+__global__ void __launch_bounds__(kDigits) hist_scan_kernel(unsigned* __restrict__ hist,
+                                                            int ctas,
+                                                            const unsigned long long* count,
+                                                            long long cap) {
+  __shared__ unsigned warp_tot[kDigits / 32];
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+  unsigned* row = hist + (size_t)d * ctas;
+  unsigned tot = 0;
+#pragma unroll 8
+  for (int c = 0; c < ctas; ++c) tot += row[c];
+  unsigned incl = tot;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  unsigned run = incl - tot;
+  for (int w = 0; w < warp; ++w) run += warp_tot[w];
+#pragma unroll 8
+  for (int c = 0; c < ctas; ++c) {
+    const unsigned x = row[c];
+    row[c] = run;
+    run += x;
+  }
+}
+
 __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
     const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, const unsigned long long* count,
     long long cap, int shift, const unsigned* __restrict__ offsets) {
@@ -268,12 +300,142 @@ int radix_ctas(int sms) { return sms > 0 ? 2 * sms : 256; }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------------
+// Bitmap output: compaction of the set bits, in order, into codes.
+//
+// The bitmap is cut into blocks of kBmWords words, one CTA each (8 warps x 256 words).  Pass 1
+// counts the set bits of every block, pass 2 scans the block counts (and stores the total), and
+// pass 3 writes the codes: each warp walks its nonzero words in order and its 32 lanes write
+// the set bits of one word at once, so the stores are coalesced where the bitmap is dense.
+
+constexpr int kBmThreads = 256;
+constexpr int kBmWordsPerLane = 8;
+constexpr int kBmWords = kBmThreads * kBmWordsPerLane;
+
+__global__ void __launch_bounds__(kBmThreads) bitmap_count_kernel(const uint32_t* __restrict__ bm,
+                                                                 uint64_t nwords,
+                                                                 unsigned* __restrict__ blk) {
+  __shared__ unsigned warp_tot[kBmThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t w0 = (uint64_t)blockIdx.x * kBmWords;
+  unsigned c = 0;
+  for (int i = threadIdx.x; i < kBmWords; i += kBmThreads)
+    if (w0 + i < nwords) c += __popc(bm[w0 + i]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if (lane == 0) warp_tot[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < kBmThreads / 32; ++w) t += warp_tot[w];
+    blk[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the nblk block counts in place (one CTA); *count receives the total.
+// Bitmaps hold at most 2^31 bits, so every offset fits 32 bits.
+__global__ void __launch_bounds__(kBmThreads) bitmap_scan_kernel(unsigned* __restrict__ blk,
+                                                                int nblk,
+                                                                unsigned long long* count) {
+  __shared__ unsigned warp_tot[kBmThreads / 32];
+  __shared__ unsigned carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblk; b0 += kBmThreads) {
+    const int i = b0 + threadIdx.x;
+    const unsigned x = i < nblk ? blk[i] : 0u;
+    unsigned incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int w = 0; w < kBmThreads / 32; ++w) {
+      if (w < warp) before += warp_tot[w];
+      total += warp_tot[w];
+    }
+    if (i < nblk) blk[i] = carry + before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = carry;
+}
+
+// Writes the codes base + bit of the set bits of every block at the block's offset (at most cap
+// codes in all).  Warp w of the block owns words [w*256, (w+1)*256) of it; lane k holds words
+// k, k+32, ... of that range.
+__global__ void __launch_bounds__(kBmThreads) bitmap_write_kernel(const uint32_t* __restrict__ bm,
+                                                                 uint64_t nwords, uint64_t base,
+                                                                 const unsigned* __restrict__ blk,
+                                                                 uint64_t* __restrict__ out,
+                                                                 long long cap) {
+  __shared__ unsigned warp_tot[kBmThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint64_t wbase = (uint64_t)blockIdx.x * kBmWords + (uint64_t)warp * (32 * kBmWordsPerLane);
+  uint32_t x[kBmWordsPerLane];
+  unsigned c = 0;
+#pragma unroll
+  for (int i = 0; i < kBmWordsPerLane; ++i) {
+    const uint64_t w = wbase + (uint64_t)i * 32 + lane;
+    x[i] = w < nwords ? bm[w] : 0u;
+    c += __popc(x[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if (lane == 0) warp_tot[warp] = c;
+  __syncthreads();
+  unsigned long long pos = blk[blockIdx.x];
+  for (int w = 0; w < warp; ++w) pos += warp_tot[w];
+#pragma unroll
+  for (int i = 0; i < kBmWordsPerLane; ++i) {
+    const unsigned cnt = __popc(x[i]);
+    unsigned excl = cnt;  // inclusive, then exclusive, prefix over the lanes' words
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, excl, o);
+      if (lane >= o) excl += y;
+    }
+    const unsigned tot = __shfl_sync(kFull, excl, 31);
+    excl -= cnt;
+    unsigned nz = __ballot_sync(kFull, x[i] != 0u);
+    while (nz) {  // the warp writes the set bits of one word at a time, lane = bit
+      const int src = __ffs(nz) - 1;
+      nz &= nz - 1;
+      const uint32_t xs = __shfl_sync(kFull, x[i], src);
+      const unsigned ps = __shfl_sync(kFull, excl, src);
+      if ((xs >> lane) & 1u) {
+        const unsigned long long q = pos + ps + __popc(xs & lt);
+        if (q < (unsigned long long)cap)
+          out[q] = base + ((wbase + (uint64_t)i * 32 + src) << 5) + lane;
+      }
+    }
+    pos += tot;
+  }
+}
+
 // Scratch layout: [keys: cap u64][hist: kDigits*ctas u32][per_cta raw: ctas][per_cta scan: ctas]
 size_t sort_scratch_bytes(int64_t cap, int sms) {
   const int ctas = radix_ctas(sms);
   size_t b = (size_t)(cap > 0 ? cap : 1) * 8;
   b += (size_t)kDigits * ctas * 4 + 2 * (size_t)ctas * 4 + 64;
   return b;
+}
+
+uint64_t bitmap_scratch_words(uint64_t nwords) { return (nwords + kBmWords - 1) / kBmWords + 1; }
+
+cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t base,
+                                  uint64_t* out, int64_t cap, unsigned* scratch,
+                                  unsigned long long* count, cudaStream_t s) {
+  const uint64_t nblk = (nwords + kBmWords - 1) / kBmWords;
+  if (nblk == 0 || nblk > (uint64_t)INT32_MAX) return cudaErrorInvalidValue;
+  bitmap_count_kernel<<<(unsigned)nblk, kBmThreads, 0, s>>>(bm, nwords, scratch);
+  bitmap_scan_kernel<<<1, kBmThreads, 0, s>>>(scratch, (int)nblk, count);
+  bitmap_write_kernel<<<(unsigned)nblk, kBmThreads, 0, s>>>(bm, nwords, base, scratch, out,
+                                                            (long long)cap);
+  note_launches(3);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, int64_t cap,
@@ -299,7 +461,7 @@ cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, i
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = pass * kRadixBits;
     radix_hist_kernel<<<ctas, kRadixThreads, 0, s>>>(a, d_count, cap, shift, hist);
-    scan_kernel<<<1, kRadixThreads, 0, s>>>(hist, kDigits * ctas, d_count, cap, 1);
+    hist_scan_kernel<<<1, kDigits, 0, s>>>(hist, ctas, d_count, cap);
     radix_scatter_kernel<<<ctas, kRadixThreads, 0, s>>>(a, b, d_count, cap, shift, hist);
     uint64_t* tmp = a; a = b; b = tmp;
   }
@@ -375,11 +537,11 @@ cudaError_t add_sort_nodes(cudaGraph_t g, cudaGraphNode_t dep, uint64_t* d_codes
   const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
   for (int pass = 0; pass < passes && e == cudaSuccess; ++pass) {
     int shift = pass * kRadixBits;
-    int len = kDigits * ctas, need = 1;
+    int nctas = ctas;
     void* ha[] = {(void*)&a, (void*)&d_count, (void*)&capv, (void*)&shift, (void*)&hist};
     e = add((void*)radix_hist_kernel, ctas, kRadixThreads, ha);
-    void* sa[] = {(void*)&hist, (void*)&len, (void*)&d_count, (void*)&capv, (void*)&need};
-    if (e == cudaSuccess) e = add((void*)scan_kernel, 1, kRadixThreads, sa);
+    void* sa[] = {(void*)&hist, (void*)&nctas, (void*)&d_count, (void*)&capv};
+    if (e == cudaSuccess) e = add((void*)hist_scan_kernel, 1, kDigits, sa);
     void* xa[] = {(void*)&a, (void*)&b, (void*)&d_count, (void*)&capv, (void*)&shift, (void*)&hist};
     if (e == cudaSuccess) e = add((void*)radix_scatter_kernel, ctas, kRadixThreads, xa);
     uint64_t* tmp = a; a = b; b = tmp;

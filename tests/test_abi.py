@@ -52,7 +52,7 @@ def test_status_codes_match_header(lib):
 
 def test_struct_sizes_match_c_layout():
     # motif_opts: pointer, 7 int32, 2 fn pointers, ctx pointer, 2 uint64.
-    assert ctypes.sizeof(m.motif_opts) == 8 + 7 * 4 + 4 + 3 * 8 + 2 * 8
+    assert ctypes.sizeof(m.motif_opts) == 8 + 8 * 4 + 3 * 8 + 2 * 8
     assert ctypes.sizeof(m.motif_stats_t) == 3 * 8 + 4 * 8 + 8 + 4 * 4 + 3 * 8
 
 

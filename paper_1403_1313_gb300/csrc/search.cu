@@ -606,29 +606,35 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
       unsigned wb = 0;
       if (lane == 0 && bal) wb = atomicAdd(cnt, (unsigned)__popc(bal));
       wb = __shfl_sync(kFull, wb, 0);
-      if (keep) {
-        const unsigned k = wb + __popc(bal & ((1u << lane) - 1u));
-        const uint64_t code = __ldg(crow + j);
-        const int v2 = (int)((code >> (2 * KS)) & 0xFFu);  // the window's P2 bases
-        const int rr = r1 < 4 ? r1 : 4;
-        head[k] = (uint32_t)j | ((uint32_t)(r1 < 15 ? r1 : 15) << 16) | ((wE & 15u) << 20) |
-                  ((wO & 15u) << 24);
-        vsuf[k] = (uint16_t)(code & 0xFFu);
-        const uint4* brow = reinterpret_cast<const uint4*>(jd.ball + ((size_t)v2 * (KS + 1) + rr) * 4);
-        const uint4 lo = __ldg(brow), hi = __ldg(brow + 1);
-        maskw[0 * wcap + k] = lo.x;
-        maskw[1 * wcap + k] = lo.y;
-        maskw[2 * wcap + k] = lo.z;
-        maskw[3 * wcap + k] = lo.w;
-        maskw[4 * wcap + k] = hi.x;
-        maskw[5 * wcap + k] = hi.y;
-        maskw[6 * wcap + k] = hi.z;
-        maskw[7 * wcap + k] = hi.w;
-      }
+      if (keep)
+        head[wb + __popc(bal & ((1u << lane) - 1u))] =
+            (uint32_t)j | ((uint32_t)(r1 < 15 ? r1 : 15) << 16) | ((wE & 15u) << 20) |
+            ((wO & 15u) << 24);
     }
     if (tid == 0) s_cnt[(s + 1) & 1] = 0;  // the next sequence's list count
     __syncthreads();
     const int K = (int)*cnt;
+    // One thread per listed window: its suffix code and the ball-table row of P2 values within
+    // min(r1, 4) of its P2, stored word-major.
+    for (int k = tid; k < K; k += blockDim.x) {
+      const uint32_t e = head[k];
+      const uint64_t code = __ldg(crow + (e & 0xFFFFu));
+      const uint32_t r1 = (e >> 16) & 15u;
+      const int v2 = (int)((code >> (2 * KS)) & 0xFFu);  // the window's P2 bases
+      vsuf[k] = (uint16_t)(code & 0xFFu);
+      const uint4* brow = reinterpret_cast<const uint4*>(
+          jd.ball + ((size_t)v2 * (KS + 1) + (r1 < 4u ? r1 : 4u)) * 4);
+      const uint4 lo = __ldg(brow), hi = __ldg(brow + 1);
+      maskw[0 * wcap + k] = lo.x;
+      maskw[1 * wcap + k] = lo.y;
+      maskw[2 * wcap + k] = lo.z;
+      maskw[3 * wcap + k] = lo.w;
+      maskw[4 * wcap + k] = hi.x;
+      maskw[5 * wcap + k] = hi.y;
+      maskw[6 * wcap + k] = hi.z;
+      maskw[7 * wcap + k] = hi.w;
+    }
+    __syncthreads();
     const bool lane_live = any_set<KS>(alive);
     // 2. take this lane's bits of the map (the P2 code of lane tid is tid) and clear them;
     //    then scan 32 listed entries at a time: a warp transpose turns the entries' words for

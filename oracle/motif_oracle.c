@@ -25,6 +25,11 @@
  * The tally `compares` is the canonical algorithmic window-compare count: per candidate and
  * per visited sequence, j+1 for a first match at window j, or W when no window matches.
  *
+ * oracle_skipbf_var takes sequences of different lengths t_s (each sequence has t_s - l + 1
+ * windows, none when t_s < l) and may mask characters outside ACGTacgt: a window that contains
+ * one never matches, so no l-mer over {A,C,G,T} is within d of it.  Its tally counts every
+ * window position, masked or not, the same way (j+1 at the first match, else t_s - l + 1).
+ *
  * oracle_skipbf_threads is the paper's multicore decomposition (Sec. IV.A, Fig. 1): the index
  * space is cut into one contiguous range per POSIX thread, each thread searches its range
  * against its own view of the windows, and the per-thread outputs are concatenated in order.
@@ -70,13 +75,13 @@ static int oracle_copy_seqs(int n, int t, const char* seqs, long long stride, ch
 }
 
 /* Skip-BF over candidate indices [lo, hi) (Sec. III.A, range form of Sec. IV.A).
- * seqs: n rows of t characters, row s at seqs + s*t, already upper-case.
+ * seqs: n rows at seqs + s*stride, already upper-case; row s has lens[s] characters (every row
+ * has t when lens is NULL); a 0 character is masked (no window containing it matches).
  * Accepted indices are written ascending to out[0 .. min(count, cap)); *count receives the
  * total accepted; *compares the canonical window-compare tally. */
-static void oracle_skipbf_core(int n, int t, int l, int d, const char* seqs, uint64_t lo,
-                               uint64_t hi, uint64_t* out, long long cap, long long* count,
-                               uint64_t* compares) {
-  const int W = t - l + 1; /* windows per sequence (Sec. III.A) */
+static void oracle_skipbf_rows(int n, long long stride, const int* lens, int t, int l, int d,
+                               const char* seqs, uint64_t lo, uint64_t hi, uint64_t* out,
+                               long long cap, long long* count, uint64_t* compares) {
   char lmer[64];
   long long found = 0;
   uint64_t tally = 0;
@@ -84,11 +89,16 @@ static void oracle_skipbf_core(int n, int t, int l, int d, const char* seqs, uin
     oracle_lmer_from_index(k, l, lmer);
     int survives = 1;
     for (int s = 0; s < n && survives; ++s) {
-      const char* row = seqs + (long long)s * t;
+      const char* row = seqs + (long long)s * stride;
+      const int W = (lens ? lens[s] : t) - l + 1; /* windows of this sequence (Sec. III.A) */
       int matched = 0;
       for (int j = 0; j < W; ++j) {
         int mismatches = 0;
         for (int i = 0; i < l; ++i) {
+          if (row[j + i] == 0) { /* a masked character: this window never matches */
+            mismatches = d + 1;
+            break;
+          }
           if (lmer[i] != row[j + i]) {
             ++mismatches;
             if (mismatches > d) break;
@@ -114,6 +124,13 @@ static void oracle_skipbf_core(int n, int t, int l, int d, const char* seqs, uin
   *compares = tally;
 }
 
+/* Equal lengths: n rows of t characters, row s at seqs + s*t. */
+static void oracle_skipbf_core(int n, int t, int l, int d, const char* seqs, uint64_t lo,
+                               uint64_t hi, uint64_t* out, long long cap, long long* count,
+                               uint64_t* compares) {
+  oracle_skipbf_rows(n, t, NULL, t, l, d, seqs, lo, hi, out, cap, count, compares);
+}
+
 static int oracle_check_args(int n, int t, int l, int d, const char* seqs, long long stride) {
   if (n < 1 || t < 1 || l < 1 || l > 31 || d < 0 || !seqs || stride < t) return ORACLE_ERR_ARG;
   return ORACLE_OK;
@@ -131,6 +148,33 @@ int oracle_skipbf_range(int n, int t, int l, int d, const char* seqs, long long 
   if (!buf) return ORACLE_ERR_OOM;
   rc = oracle_copy_seqs(n, t, seqs, stride, buf);
   if (rc == ORACLE_OK) oracle_skipbf_core(n, t, l, d, buf, lo, hi, out, cap, count, compares);
+  free(buf);
+  return rc;
+}
+
+/* Single-threaded skip-BF over [lo, hi) for sequences of different lengths: row s has
+ * lens[s] >= 0 characters at seqs + s*stride.  With mask_unknown, a character outside
+ * ACGTacgt masks the windows that contain it; without it, it is ORACLE_ERR_ALPHABET. */
+int oracle_skipbf_var(int n, const int* lens, int l, int d, const char* seqs, long long stride,
+                      int mask_unknown, uint64_t lo, uint64_t hi, uint64_t* out, long long cap,
+                      long long* count, uint64_t* compares) {
+  if (n < 1 || !lens || l < 1 || l > 31 || d < 0 || !seqs) return ORACLE_ERR_ARG;
+  const uint64_t space = 1ull << (2 * l);
+  if (hi > space || lo > hi || (cap > 0 && !out) || !count || !compares) return ORACLE_ERR_ARG;
+  if (stride < 1) return ORACLE_ERR_ARG;
+  for (int s = 0; s < n; ++s)
+    if (lens[s] < 0 || lens[s] > stride) return ORACLE_ERR_ARG;
+  char* buf = (char*)malloc((size_t)n * (size_t)stride);
+  if (!buf) return ORACLE_ERR_OOM;
+  int rc = ORACLE_OK;
+  for (int s = 0; s < n && rc == ORACLE_OK; ++s)
+    for (int j = 0; j < lens[s]; ++j) {
+      const char ch = oracle_norm(seqs[(long long)s * stride + j]);
+      if (!ch && !mask_unknown) { rc = ORACLE_ERR_ALPHABET; break; }
+      buf[(long long)s * stride + j] = ch;
+    }
+  if (rc == ORACLE_OK)
+    oracle_skipbf_rows(n, stride, lens, 0, l, d, buf, lo, hi, out, cap, count, compares);
   free(buf);
   return rc;
 }

@@ -50,6 +50,10 @@ def _load():
             lib.oracle_skipbf_threads.argtypes = [ctypes.c_int] * 4 + [
                 ctypes.c_char_p, ctypes.c_longlong, ctypes.c_uint64, ctypes.c_uint64,
                 ctypes.c_int, u64p, ctypes.c_longlong, i64p, u64p]
+            lib.oracle_skipbf_var.argtypes = [
+                ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                ctypes.c_char_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_uint64,
+                ctypes.c_uint64, u64p, ctypes.c_longlong, i64p, u64p]
             lib.oracle_lmer_from_index.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_char_p]
             lib.oracle_lmer_from_index.restype = None
             _lib = lib
@@ -97,6 +101,34 @@ def search(seqs, l: int, d: int, lo: int = 0, hi: int | None = None, threads: in
         else:
             rc = lib.oracle_skipbf_threads(n, t, l, d, buf, t, lo, hi, threads, ptr, cap,
                                            ctypes.byref(count), ctypes.byref(cmp))
+        if rc != 0:
+            raise OracleError(rc)
+        if count.value <= cap:
+            return out[:count.value].copy(), int(cmp.value)
+        cap = count.value
+
+
+def search_var(seqs, l: int, d: int, mask_unknown: bool = True, lo: int = 0,
+               hi: int | None = None):
+    """Skip-BF for sequences of different lengths (strings or bytes); with mask_unknown a window
+    containing a character outside ACGTacgt never matches.  Returns (codes, compares)."""
+    lib = _load()
+    rows = [s.encode() if isinstance(s, str) else bytes(s) for s in seqs]
+    if not rows:
+        raise ValueError("expected n >= 1 sequences")
+    stride = max(1, max(len(r) for r in rows))
+    buf = b"".join(r.ljust(stride, b"\0") for r in rows)
+    lens = (ctypes.c_int * len(rows))(*[len(r) for r in rows])
+    if hi is None:
+        hi = 4 ** l
+    count = ctypes.c_longlong(0)
+    cmp = ctypes.c_uint64(0)
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, dtype=np.uint64)
+        rc = lib.oracle_skipbf_var(len(rows), lens, l, d, buf, stride, 1 if mask_unknown else 0,
+                                   lo, hi, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   cap, ctypes.byref(count), ctypes.byref(cmp))
         if rc != 0:
             raise OracleError(rc)
         if count.value <= cap:

@@ -142,6 +142,30 @@ int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride);
  * motif_search_device, through *d_out_count = -1). */
 int motif_load_seqs_device(motif_plan p, const char* d_seqs, int64_t stride);
 
+/* Loads n sequences of their own lengths (the paper uses one length, Sec. IV.B, and names real
+ * and larger sequence data as future work, Sec. VI).  Row r holds lengths[r] characters,
+ * 0 <= lengths[r] <= min(t, stride), at seqs + r*stride; it has lengths[r] - l + 1 windows
+ * (none when shorter than l).  With mask_unknown != 0 a character outside ACGTacgt (such as N)
+ * masks every window that contains it: a masked window matches no candidate.  With
+ * mask_unknown == 0 such a character is MOTIF_ERR_ALPHABET.  A sequence without an unmasked
+ * window leaves nothing to accept (the search returns no codes).  motif_count_compares counts
+ * every window position of each row, masked or not; motif_count_work's unit tally counts the
+ * packed rows, in which masked and missing windows are copies of valid windows of the same row.
+ * Blocking.  Errors: MOTIF_ERR_ARG, MOTIF_ERR_ALPHABET, MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
+int motif_load_seqs_var(motif_plan p, const char* seqs, int64_t stride, const int32_t* lengths,
+                        int32_t mask_unknown);
+
+/* Parses FASTA text (not in the paper; the input format of real sequence data): a record
+ * starts with a line beginning with '>' (the header, not kept); the following lines up to the
+ * next header hold its residues; whitespace is dropped and lines beginning with ';' are
+ * comments.  The residues of all records are written back to back to seq_buf and their counts
+ * to lengths[0 .. records); *n_out and *total_out receive the numbers of records and residues.
+ * Host-only: no device work.  If max_seqs or buf_cap is too small the return is
+ * MOTIF_ERR_CAPACITY with *n_out and *total_out set (nothing else is promised): call again
+ * with larger buffers.  Residues before the first header are MOTIF_ERR_ARG. */
+int motif_fasta_parse(const char* text, int64_t text_len, char* seq_buf, int64_t buf_cap,
+                      int32_t* lengths, int32_t max_seqs, int32_t* n_out, int64_t* total_out);
+
 /* ---- search (Sec. III.A skip-BF; Sec. IV.A range split) -------------------------------- */
 
 /* Blocking search over the plan's candidate range.  Writes the accepted codes, ascending and

@@ -23,7 +23,8 @@ import numpy as np
 __all__ = [
     "MotifError", "MotifLibraryError", "Plan", "motif_opts", "motif_stats_t",
     "motif_server_opts", "motif_opts_default", "motif_plan_create", "motif_plan_destroy",
-    "motif_load_seqs", "motif_load_seqs_device", "motif_search", "motif_search_device",
+    "motif_load_seqs", "motif_load_seqs_device", "motif_load_seqs_var", "motif_fasta_parse",
+    "read_fasta", "motif_search", "motif_search_device",
     "motif_count_compares", "motif_count_work", "motif_kernel_launches", "motif_stats", "motif_batch_search", "motif_autotune",
     "motif_tune_cache_save", "motif_tune_cache_load", "motif_server_start", "motif_server_stop",
     "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
@@ -120,6 +121,11 @@ def _load():
             "motif_plan_destroy": (None, [P]),
             "motif_load_seqs": (ctypes.c_int, [P, ctypes.c_char_p, i64]),
             "motif_load_seqs_device": (ctypes.c_int, [P, P, i64]),
+            "motif_load_seqs_var": (ctypes.c_int, [P, ctypes.c_char_p, i64,
+                                                   ctypes.POINTER(i32), i32]),
+            "motif_fasta_parse": (ctypes.c_int, [ctypes.c_char_p, i64, ctypes.c_char_p, i64,
+                                                 ctypes.POINTER(i32), i32,
+                                                 ctypes.POINTER(i32), i64p]),
             "motif_search": (ctypes.c_int, [P, u64p, i64, i64p]),
             "motif_search_device": (ctypes.c_int, [P, P, i64, P]),
             "motif_count_compares": (ctypes.c_int, [P, u64p]),
@@ -225,6 +231,49 @@ def motif_load_seqs_device(plan: Plan, d_seqs, stride: int | None = None) -> Non
     else:
         ptr = int(d_seqs)
     _check(_load().motif_load_seqs_device(plan, ctypes.c_void_p(ptr), stride), "motif_load_seqs_device")
+
+
+def motif_load_seqs_var(plan: Plan, seqs, mask_unknown: bool = True) -> None:
+    """Sequences of their own lengths (str or bytes, each at most the plan's t); with
+    mask_unknown a character outside ACGTacgt masks the windows that contain it."""
+    rows = [r.encode() if isinstance(r, str) else bytes(r) for r in seqs]
+    if len(rows) != plan.n:
+        raise ValueError("%d sequences, plan expects %d" % (len(rows), plan.n))
+    stride = max(1, plan.t)
+    if any(len(r) > stride for r in rows):
+        raise ValueError("a sequence is longer than the plan's t = %d" % plan.t)
+    buf = b"".join(r.ljust(stride, b"A") for r in rows)
+    lens = (ctypes.c_int32 * len(rows))(*[len(r) for r in rows])
+    _check(_load().motif_load_seqs_var(plan, buf, stride, lens, 1 if mask_unknown else 0),
+           "motif_load_seqs_var")
+
+
+def motif_fasta_parse(text) -> list:
+    """The residues of every record of FASTA text, as a list of bytes (headers dropped)."""
+    data = text.encode() if isinstance(text, str) else bytes(text)
+    lib = _load()
+    n = ctypes.c_int32(0)
+    total = ctypes.c_int64(0)
+    st = lib.motif_fasta_parse(data, len(data), None, 0, None, 0, ctypes.byref(n),
+                               ctypes.byref(total))
+    if st not in (OK, ERR_CAPACITY):
+        _check(st, "motif_fasta_parse")
+    buf = ctypes.create_string_buffer(max(1, total.value))
+    lens = (ctypes.c_int32 * max(1, n.value))()
+    _check(lib.motif_fasta_parse(data, len(data), buf, total.value, lens, n.value,
+                                 ctypes.byref(n), ctypes.byref(total)), "motif_fasta_parse")
+    out, at = [], 0
+    raw = buf.raw
+    for i in range(n.value):
+        out.append(raw[at:at + lens[i]])
+        at += lens[i]
+    return out
+
+
+def read_fasta(path: str) -> list:
+    """motif_fasta_parse of a file's contents."""
+    with open(path, "rb") as f:
+        return motif_fasta_parse(f.read())
 
 
 def _host_codes(capacity: int) -> np.ndarray:

@@ -19,7 +19,7 @@ OBJ = os.path.join(CSRC, "_build")
 LIB = os.path.join(PKG, "libmotif.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "pack.cu", "search.cu", "sort.cu", "batch.cu", "serve.cu", "probe.cu",
-           "noalloc.cu"]
+           "io.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "plan.h"
 
@@ -131,6 +132,8 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->ball = p->kind == MOTIF_KERNEL_GROUP ? ball_table(p->device, p->p, p->stream) : nullptr;
   jd->bitmap = p->bitmap ? p->d_bitmap : nullptr;
   jd->bm_base = p->bm_base;
+  jd->valid = p->ragged ? p->d_valid : nullptr;
+  jd->wrow = p->ragged ? p->d_wrow : nullptr;
 }
 
 // Expected number of accepted codes of the plan's range for uniform i.i.d. bases: a window
@@ -542,6 +545,16 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
   return MOTIF_OK;
 }
 
+static void free_ragged(motif_plan p) {
+  plan_free(p, p->d_lens, sizeof(int32_t) * (size_t)p->n);
+  plan_free(p, p->d_wrow, sizeof(int32_t) * (size_t)p->n);
+  plan_free(p, p->d_valid, (size_t)p->n * (size_t)std::max(p->wstride, 0));
+  plan_free(p, p->d_empty, sizeof(int));
+  p->d_lens = p->d_wrow = nullptr;
+  p->d_valid = nullptr;
+  p->d_empty = nullptr;
+}
+
 void motif_plan_destroy(motif_plan p) {
   if (!p) return;
   DeviceGuard g(p->device);
@@ -559,6 +572,7 @@ void motif_plan_destroy(motif_plan p) {
   plan_free(p, p->d_out, (size_t)p->out_cap * 8);
   plan_free(p, p->d_sort, p->sort_bytes);
   free_bitmap(p);
+  free_ragged(p);
   cudaStreamSynchronize(p->stream);
   for (cudaEvent_t ev : p->evq)
     if (ev) cudaEventDestroy(ev);
@@ -568,6 +582,9 @@ void motif_plan_destroy(motif_plan p) {
 }
 
 static int load_common(motif_plan p, bool sync_check) {
+  if (p->ragged) p->desc_out = nullptr;  // the descriptor names the ragged-row buffers
+  p->ragged = false;
+  p->empty_row = false;
   cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) return status_from_cuda(e);
   e = launch_pack(p->d_chars, p->t, p->n, p->t, p->l, p->wstride, p->d_planes, p->d_codes,
@@ -598,6 +615,61 @@ int motif_load_seqs_device(motif_plan p, const char* d_seqs, int64_t stride) {
   return load_common(p, false);
 }
 
+int motif_load_seqs_var(motif_plan p, const char* seqs, int64_t stride, const int32_t* lengths,
+                        int32_t mask_unknown) {
+  if (!p || !seqs || !lengths || stride < 1) return MOTIF_ERR_ARG;
+  for (int r = 0; r < p->n; ++r)
+    if (lengths[r] < 0 || lengths[r] > p->t || lengths[r] > stride) return MOTIF_ERR_ARG;
+  DeviceGuard g(p->device);
+  p->loaded = false;
+  if (!p->d_lens) {
+    p->d_lens = (int32_t*)plan_alloc(p, sizeof(int32_t) * (size_t)p->n);
+    p->d_wrow = (int32_t*)plan_alloc(p, sizeof(int32_t) * (size_t)p->n);
+    p->d_valid = p->wstride > 0 ? (uint8_t*)plan_alloc(p, (size_t)p->n * p->wstride) : nullptr;
+    p->d_empty = (int*)plan_alloc(p, sizeof(int));
+    if (!p->d_lens || !p->d_wrow || (p->wstride > 0 && !p->d_valid) || !p->d_empty) {
+      free_ragged(p);
+      return MOTIF_ERR_OOM;
+    }
+  }
+  // Rows staged on the host at the plan's stride t (bytes past a row's length are never read
+  // as part of a valid window).
+  std::vector<char> rows((size_t)p->n * p->t, 'A');
+  std::vector<int32_t> wrow(p->n);
+  for (int r = 0; r < p->n; ++r) {
+    memcpy(rows.data() + (size_t)r * p->t, seqs + (size_t)r * stride, (size_t)lengths[r]);
+    wrow[r] = std::max(0, lengths[r] - p->l + 1);
+  }
+  cudaError_t e = cudaMemcpyAsync(p->d_chars, rows.data(), rows.size(), cudaMemcpyHostToDevice,
+                                  p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_lens, lengths, sizeof(int32_t) * p->n, cudaMemcpyHostToDevice,
+                        p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_wrow, wrow.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice,
+                        p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_empty, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess && p->wstride > 0)
+    e = launch_pack_var(p->d_chars, p->t, p->n, p->l, p->wstride, p->d_lens,
+                        mask_unknown ? 1 : 0, p->d_planes, p->d_codes, p->d_valid, p->d_err,
+                        p->d_empty, p->stream);
+  int flags[2] = {0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&flags[0], p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&flags[1], p->d_empty, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  if (flags[0]) return MOTIF_ERR_ALPHABET;
+  p->ragged = true;
+  p->empty_row = flags[1] != 0;
+  p->desc_out = nullptr;  // the descriptor names the ragged-row buffers
+  p->check_alpha = false;
+  p->loaded = true;
+  return MOTIF_OK;
+}
+
 int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* out_count) {
   if (!p || !out_count || capacity < 0 || (capacity > 0 && !out_codes)) return MOTIF_ERR_ARG;
   if (!p->loaded) return MOTIF_ERR_STATE;
@@ -611,7 +683,8 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   p->stats.block = p->block;
   p->stats.smem_bytes = (int32_t)p->smem;
   *out_count = 0;
-  if (p->W <= 0 || p->hi <= p->lo) {  // no windows or an empty range: nothing survives
+  if (p->W <= 0 || p->hi <= p->lo || p->empty_row) {  // no windows, an empty range, or a row
+                                                      // with no valid window: nothing survives
     p->stats.survivors = 0;
     p->stats.search_ms = p->stats.sort_ms = 0;
     p->stats.total_ms = now_ms() - t0;
@@ -682,7 +755,7 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
     rc = ensure_sort(p, capacity);
     if (rc) return rc;
   }
-  if (p->W <= 0 || p->hi <= p->lo) {
+  if (p->W <= 0 || p->hi <= p->lo || p->empty_row) {
     cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
   } else if (p->bitmap) {

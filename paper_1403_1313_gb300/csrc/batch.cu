@@ -113,7 +113,9 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
   std::map<std::pair<int, int>, std::vector<int>> groups;
   for (int j = 0; j < njobs; ++j) {
     motif_plan_s* p = plans[j];
-    if (statuses[j] != MOTIF_OK || p->W <= 0 || p->hi <= p->lo || p->nchunks == 0) continue;
+    if (statuses[j] != MOTIF_OK || p->W <= 0 || p->hi <= p->lo || p->nchunks == 0 ||
+        p->empty_row)
+      continue;
     if (plan_ensure_buffers(p) != MOTIF_OK || cudaStreamSynchronize(p->stream) != cudaSuccess) {
       statuses[j] = MOTIF_ERR_OOM;
       continue;

@@ -37,6 +37,8 @@ struct JobDesc {
   const uint64_t* ball;      // GROUP: Hamming-ball table for ks (see ball_table_words)
   uint32_t* bitmap;          // non-null: accepted codes set bit (code - bm_base) here instead of
   uint64_t bm_base;          //   being appended to out (bm_base is a multiple of 64)
+  const uint8_t* valid;      // ragged / masked rows: [n][wstride] window flags (null = all valid);
+  const int32_t* wrow;       //   per-row window counts (null = W); read by the tally kernel only
 };
 
 // Per-job device state, advanced by the last CTA of every step.
@@ -75,6 +77,13 @@ void note_launches(int n);
 unsigned long long launches_total();
 
 // ---- launchers (stream-ordered, no host synchronisation) ---------------------------------
+// Ragged rows (lens[s] characters each), optionally masking windows with characters outside
+// ACGTacgt; *d_err is set on such a character when mask_unknown is 0, *d_empty when some row has
+// no valid window.  Invalid positions are filled with copies of valid windows of their row.
+cudaError_t launch_pack_var(const char* d_chars, int64_t stride, int n, int l, int wstride,
+                            const int32_t* d_lens, int mask_unknown, uint2* planes,
+                            uint64_t* codes, uint8_t* valid, int* d_err, int* d_empty,
+                            cudaStream_t s);
 cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l, int wstride,
                         uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s);
 // Fills the Hamming-ball table for ks (ball_table_words(ks) words).

@@ -58,7 +58,100 @@ __global__ void pack_kernel(const char* __restrict__ chars, int64_t stride, int 
   }
 }
 
+// Ragged rows: row s holds lens[s] characters.  A window is valid when it lies inside its row
+// and, with masking, contains only ACGTacgt; its code and planes are written as above and its
+// flag to valid[].  Invalid positions (masked windows, windows past the row's end, padding) are
+// overwritten afterwards by fill_rows_kernel.
+__global__ void pack_var_kernel(const char* __restrict__ chars, int64_t stride, int n, int l,
+                                int wstride, const int32_t* __restrict__ lens, int mask_unknown,
+                                uint2* __restrict__ planes, uint64_t* __restrict__ codes,
+                                uint8_t* __restrict__ valid, int* err) {
+  const int64_t total = (int64_t)n * wstride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / wstride);
+    const int j = (int)(i - (int64_t)s * wstride);
+    const int W = lens[s] - l + 1;
+    uint64_t code = 0;
+    uint32_t E = 0, O = 0;
+    bool ok = j < W;
+    if (ok) {
+      const char* p = chars + (int64_t)s * stride + j;
+      for (int b = 0; b < l; ++b) {
+        int v = base_code(p[b]);
+        if (v < 0) {
+          if (!mask_unknown) atomicOr(err, 1);
+          ok = false;
+          v = 0;
+        }
+        code = (code << 2) | (uint64_t)v;
+        E = (E << 1) | (uint32_t)(v & 1);
+        O = (O << 1) | (uint32_t)(v >> 1);
+      }
+    }
+    planes[i] = make_uint2(E, O);
+    codes[i] = code;
+    valid[i] = ok ? 1 : 0;
+  }
+}
+
+// One warp per row: every invalid position takes the code and planes of the nearest valid
+// window before it (or of the row's first valid window when there is none before it).  A
+// window that is present twice matches exactly when it matches once, so the search kernels run
+// over the filled rows unchanged.  A row with no valid window sets *empty: no candidate can
+// match it.
+__global__ void fill_rows_kernel(int n, int wstride, const uint8_t* __restrict__ valid,
+                                 uint2* __restrict__ planes, uint64_t* __restrict__ codes,
+                                 int* empty) {
+  const int lane = threadIdx.x & 31;
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (s >= n) return;
+  const uint8_t* v = valid + (int64_t)s * wstride;
+  uint2* pl = planes + (int64_t)s * wstride;
+  uint64_t* co = codes + (int64_t)s * wstride;
+  int first = -1;
+  for (int b = 0; b < wstride && first < 0; b += 32) {
+    const unsigned bal = __ballot_sync(0xffffffffu, b + lane < wstride && v[b + lane]);
+    if (bal) first = b + __ffs(bal) - 1;
+  }
+  if (first < 0) {
+    if (lane == 0) atomicOr(empty, 1);
+    return;
+  }
+  int carry = first;  // the last valid window before the current chunk
+  for (int b = 0; b < wstride; b += 32) {
+    const int j = b + lane;
+    const bool ok = j < wstride && v[j];
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    const unsigned below = bal & ((1u << lane) - 1u);
+    const int src = below ? b + 31 - __clz(below) : carry;
+    if (j < wstride && !ok) {
+      pl[j] = pl[src];
+      co[j] = co[src];
+    }
+    if (bal) carry = b + 31 - __clz(bal);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack_var(const char* d_chars, int64_t stride, int n, int l, int wstride,
+                            const int32_t* d_lens, int mask_unknown, uint2* planes,
+                            uint64_t* codes, uint8_t* valid, int* d_err, int* d_empty,
+                            cudaStream_t s) {
+  const int block = 256;
+  const int64_t wins = (int64_t)n * wstride;
+  int grid = (int)((wins + block - 1) / block);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  pack_var_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, l, wstride, d_lens, mask_unknown,
+                                         planes, codes, valid, d_err);
+  const int rows_per_block = block / 32;
+  fill_rows_kernel<<<(n + rows_per_block - 1) / rows_per_block, block, 0, s>>>(
+      n, wstride, valid, planes, codes, d_empty);
+  note_launches(2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l, int wstride,
                         uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s) {

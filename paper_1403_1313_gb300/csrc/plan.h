@@ -68,6 +68,15 @@ struct motif_plan_s {
   int64_t graph_searches = 0;        // graph launches since the last fold (launch accounting)
   unsigned last_steps = 0;           // steps of the last folded search
 
+  // Ragged / masked input (motif_load_seqs_var): per-row lengths and window counts, window
+  // flags, and whether some row has no valid window (then nothing can be accepted).
+  bool ragged = false;
+  bool empty_row = false;
+  int32_t* d_lens = nullptr;
+  int32_t* d_wrow = nullptr;
+  uint8_t* d_valid = nullptr;
+  int* d_empty = nullptr;
+
   bool loaded = false;
   bool check_alpha = false;  // device-loaded characters not yet validated on the host
   motif_stats_t stats{};

@@ -889,16 +889,19 @@ __global__ void __launch_bounds__(256) count_kernel(const JobDesc* __restrict__ 
     uint32_t E, O;
     code_planes(k, E, O);
     for (int s = 0; s < jd.n; ++s) {
+      // Ragged or masked rows: this row's own window count, and only valid windows match.
       const uint2* row = jd.planes + (size_t)s * jd.wstride;
+      const uint8_t* ok = jd.valid ? jd.valid + (size_t)s * jd.wstride : nullptr;
+      const int W = jd.wrow ? jd.wrow[s] : jd.W;
       int j = 0;
-      for (; j < jd.W; ++j) {
+      for (; j < W; ++j) {
         const uint2 w = __ldg(row + j);
-        if (__popc((E ^ w.x) | (O ^ w.y)) <= jd.d) break;
+        if (__popc((E ^ w.x) | (O ^ w.y)) <= jd.d && (!ok || ok[j])) break;
       }
-      if (j < jd.W) {
+      if (j < W) {
         local += (unsigned long long)(j + 1);
       } else {
-        local += (unsigned long long)jd.W;
+        local += (unsigned long long)W;
         break;
       }
     }

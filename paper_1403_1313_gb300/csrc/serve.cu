@@ -506,7 +506,9 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   j->unit_hi = j->hi > j->lo ? ((j->hi - 1) >> shift) + 1 : j->unit_lo;
   const uint64_t units = j->unit_hi - j->unit_lo;
   j->chunk_units = std::max<uint64_t>(1, std::min(units, kServeChunkGroups));
-  j->nchunks = units == 0 || j->W <= 0 ? 0 : (units + j->chunk_units - 1) / j->chunk_units;
+  j->nchunks = units == 0 || j->W <= 0 || p->empty_row
+                   ? 0
+                   : (units + j->chunk_units - 1) / j->chunk_units;
   j->qcap = j->chunk_units;
   j->words = mask_words(j->pv);
   j->tiled = j->pv == 4 && j->l >= 8 && j->W <= 65535 && j->unit_lo % 256 == 0 &&

@@ -286,9 +286,8 @@ def run_ours(args):
     step_ms = st["search_ms_sum"] / max(st["searches"], 1)
     sort_ms = st["sort_ms_sum"] / max(st["searches"], 1)
     peak = POPC_PER_SM_CLK * sms * max_mhz * 1e6
-    kname = {m.KERNEL_GROUP: "GROUP", m.KERNEL_CAND: "CAND"}.get(st["kernel"], "?")
-    if kname == "GROUP" and kw.get("kernel", m.KERNEL_AUTO) in (m.KERNEL_AUTO, m.KERNEL_TILED) and l >= 8:
-        kname = "TILED"
+    kname = {m.KERNEL_GROUP: "GROUP", m.KERNEL_CAND: "CAND", m.KERNEL_TILED: "TILED"}.get(
+        st["kernel"], "?")
     achieved = compares / (step_ms / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "G window-compares/s (1 POPC each)", "frac": achieved / peak, "traffic": None,

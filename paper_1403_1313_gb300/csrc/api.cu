@@ -136,18 +136,22 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->wrow = p->ragged ? p->d_wrow : nullptr;
 }
 
-// Expected number of accepted codes of the plan's range for uniform i.i.d. bases: a window
-// matches a candidate with probability pw = sum_{k<=d} C(l,k) 3^k / 4^l, a sequence with
-// q = 1 - (1 - pw)^W, all n sequences with q^n.
-static double expected_survivors(const motif_plan_s* p) {
+// Probability, for uniform i.i.d. bases, that a candidate matches one sequence: a window
+// matches with pw = sum_{k<=d} C(l,k) 3^k / 4^l, some of the W windows with
+// q = 1 - (1 - pw)^W.
+static double match_probability(const motif_plan_s* p) {
   double term = 1.0, sum = 0.0;  // C(l,k) 3^k
   for (int k = 0; k <= std::min(p->d, p->l); ++k) {
     sum += term;
     term = term * (p->l - k) / (k + 1) * 3.0;
   }
   const double pw = std::min(1.0, sum / std::pow(4.0, p->l));
-  const double q = pw >= 1.0 ? 1.0 : -std::expm1((double)p->W * std::log1p(-pw));
-  return (double)(p->hi - p->lo) * std::pow(q, p->n);
+  return pw >= 1.0 ? 1.0 : -std::expm1((double)std::max(p->W, 0) * std::log1p(-pw));
+}
+
+// Expected number of accepted codes of the plan's range (all n sequences matched: q^n).
+static double expected_survivors(const motif_plan_s* p) {
+  return (double)(p->hi - p->lo) * std::pow(match_probability(p), p->n);
 }
 
 static void free_queues(motif_plan_s* p) {
@@ -201,9 +205,16 @@ int plan_configure(motif_plan_s* p) {
   invalidate_graphs(p);
   // The prefix-tiled first pass (GROUP, k = 4): 256 lanes per CTA whose groups share all but
   // their last 4 prefix bases, so tiles must start on multiples of 256 groups.
+  // AUTO leaves it out where a tile would walk through most sequences (q > 0.52) and there are
+  // too few tiles (< 64) to fill the GPU: the per-group passes run those faster alone.  A batch
+  // runs its jobs side by side, so there every eligible AUTO job stays tiled.
   const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
-  p->tiled = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 && p->l >= 8 &&
-             p->W <= 65535 && unit_lo % 256 == 0 && (chunk % 256 == 0 || units <= chunk);
+  const bool tiled_ok = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 &&
+                        p->l >= 8 && p->W <= 65535 && unit_lo % 256 == 0 &&
+                        (chunk % 256 == 0 || units <= chunk);
+  const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
+  p->tiled = tiled_ok && !(o.kernel == MOTIF_KERNEL_AUTO && few_long_tiles);
+  p->tiled_in_batch = tiled_ok;
   // Output: a bitmap over the range (rounded out to whole 256-code groups) where it holds at
   // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size.
   const uint64_t bm_base = p->lo & ~255ull;
@@ -678,7 +689,7 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   int rc = check_alphabet(p);
   if (rc) return rc;
   p->stats.candidates = p->hi - p->lo;
-  p->stats.kernel = p->kind;
+  p->stats.kernel = p->tiled ? MOTIF_KERNEL_TILED : p->kind;
   p->stats.grid = p->grid;
   p->stats.block = p->block;
   p->stats.smem_bytes = (int32_t)p->smem;
@@ -747,7 +758,7 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
   DeviceGuard g(p->device);
   int rc = MOTIF_OK;
   p->stats.candidates = p->hi - p->lo;
-  p->stats.kernel = p->kind;
+  p->stats.kernel = p->tiled ? MOTIF_KERNEL_TILED : p->kind;
   p->stats.grid = p->grid;
   p->stats.block = p->block;
   p->stats.smem_bytes = (int32_t)p->smem;

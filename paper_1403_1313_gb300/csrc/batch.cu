@@ -132,6 +132,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     for (size_t i = 0; i < ids.size(); ++i) {
       motif_plan_s* p = plans[ids[i]];
       fill_desc(p, &descs[i], p->d_out, (uint64_t)p->out_cap);
+      descs[i].tiled = p->tiled_in_batch ? 1 : 0;
       smem = std::max(smem, p->smem);
       max_steps = std::max<int>(max_steps, (int)std::min<uint64_t>(p->nchunks * p->n + 2, 1 << 30));
       block = p->block;

@@ -40,6 +40,7 @@ CONFIGS = {  # name: (l, d, n, t, seed)
     "l17d5": (17, 5, 20, 600, 3),
 }
 POPC_PER_SM_CLK = 16.0  # measured by the K4 probe (motif_probe_rate POPC) on GB300
+LOP3_PER_SM_CLK = 64.0  # measured by the K4 probe (motif_probe_rate LOP3) on GB300
 
 
 def parse():
@@ -49,7 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="l15d4")
-    ap.add_argument("--kernel", choices=["auto", "tiled", "group", "cand"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "tiled", "group", "cand", "bitslice"],
+                    default="auto")
     ap.add_argument("--suffix-bases", type=int, default=0)
     ap.add_argument("--cands-per-thread", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -215,6 +217,8 @@ def run_ours(args):
         kw["kernel"] = m.KERNEL_CAND
     elif args.kernel == "tiled":
         kw["kernel"] = m.KERNEL_TILED
+    elif args.kernel == "bitslice":
+        kw["kernel"] = m.KERNEL_BITSLICE
     if args.suffix_bases:
         kw["suffix_bases"] = args.suffix_bases
     if args.cands_per_thread:
@@ -286,8 +290,8 @@ def run_ours(args):
     step_ms = st["search_ms_sum"] / max(st["searches"], 1)
     sort_ms = st["sort_ms_sum"] / max(st["searches"], 1)
     peak = POPC_PER_SM_CLK * sms * max_mhz * 1e6
-    kname = {m.KERNEL_GROUP: "GROUP", m.KERNEL_CAND: "CAND", m.KERNEL_TILED: "TILED"}.get(
-        st["kernel"], "?")
+    kname = {m.KERNEL_GROUP: "GROUP", m.KERNEL_CAND: "CAND", m.KERNEL_TILED: "TILED",
+             m.KERNEL_BITSLICE: "BITSLICE"}.get(st["kernel"], "?")
     achieved = compares / (step_ms / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "G window-compares/s (1 POPC each)", "frac": achieved / peak, "traffic": None,
@@ -301,12 +305,11 @@ def run_ours(args):
                      "roofline_cand for the per-compare kernel" % kname) if kname != "CAND" else ""}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (POPC_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
-    roof_cand = None
-    if kname != "CAND" and args.cand_subrange > 0:
-        # The per-candidate kernel on a sub-range of the same workload (full per-compare cost).
-        ocand = m.torch_opts(stream=stream, kernel=m.KERNEL_CAND, cands_per_thread=2,
-                             range_lo=0, range_hi=min(cands, args.cand_subrange))
-        pc = m.motif_plan_create(n, t, l, d, ocand)
+    def per_candidate_leg(kernel, label):
+        """A per-candidate kernel on a sub-range of the same workload (full per-compare work)."""
+        o = m.torch_opts(stream=stream, kernel=kernel, cands_per_thread=2,
+                         range_lo=0, range_hi=min(cands, args.cand_subrange))
+        pc = m.motif_plan_create(n, t, l, d, o)
         with torch.cuda.stream(stream):
             m.motif_load_seqs_device(pc, d_chars)
             for _ in range(2):
@@ -318,13 +321,28 @@ def run_ours(args):
             for _ in range(5):
                 m.motif_search_device(pc, d_out, cap, d_cnt)
         stc = m.motif_stats(pc)
+        m.motif_plan_destroy(pc)
         c_ms = stc["search_ms_sum"] / max(stc["searches"], 1)
         c_ach = c_cmp / (c_ms / 1e3)
-        roof_cand = {"bound": "alu", "achieved": c_ach / 1e9, "peak": peak / 1e9,
-                     "unit": "G window-compares/s (1 POPC each)", "frac": c_ach / peak,
-                     "kernel": "step_kernel<CAND,2>", "step_kernel_ms": c_ms,
-                     "sample": "candidates [0, %d) of %s" % (min(cands, args.cand_subrange), workload)}
-        m.motif_plan_destroy(pc)
+        return {"bound": "alu", "achieved": c_ach / 1e9, "peak": peak / 1e9,
+                "unit": "G window-compares/s (1 POPC each)", "frac": c_ach / peak,
+                "kernel": "step_kernel<%s,2>" % label, "step_kernel_ms": c_ms,
+                "sample": "candidates [0, %d) of %s" % (min(cands, args.cand_subrange), workload)}
+
+    roof_cand = roof_bitslice = None
+    if kname != "CAND" and args.cand_subrange > 0:
+        roof_cand = per_candidate_leg(m.KERNEL_CAND, "CAND")
+    if args.cand_subrange > 0 and d <= 7:
+        # The bit-sliced compare against both rooflines: the POPC one above and its own, the
+        # LOP3 pipe at the counter's LOP3 per 32 compares (11 per three base positions, 5 per
+        # position left over; positions past 16 are counted as a second group).
+        roof_bitslice = per_candidate_leg(m.KERNEL_BITSLICE, "BITSLICE")
+        lop3 = sum(11 * (k // 3) + 5 * (k % 3) for k in (max(0, l - 16), min(l, 16)))
+        peak_lop3 = LOP3_PER_SM_CLK * sms * max_mhz * 1e6 * 32.0 / lop3
+        roof_bitslice.update({
+            "peak_lop3": peak_lop3 / 1e9, "frac_lop3": roof_bitslice["achieved"] * 1e9 / peak_lop3,
+            "peak_lop3_basis": "64 LOP3/clk/SM (K4 probe) x %d SMs x %.0f MHz x 32 / %d LOP3 "
+                               "per 32 compares" % (sms, max_mhz, lop3)})
 
     # End to end through the blocking C ABI with host buffers.
     e2e = None
@@ -360,6 +378,7 @@ def run_ours(args):
             "survivors": count,
             "roofline": roof,
             "roofline_cand": roof_cand,
+            "roofline_bitslice": roof_bitslice,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,

@@ -54,8 +54,11 @@ typedef enum {
   MOTIF_KERNEL_AUTO = 0,  /* the plan's tuned choice (TILED where it applies, else GROUP) */
   MOTIF_KERNEL_CAND = 1,  /* one candidate per lane: XOR, pair-fold, POPC, running min */
   MOTIF_KERNEL_GROUP = 2, /* one (l-k)-base prefix per lane, its 4^k suffixes as a bit mask */
-  MOTIF_KERNEL_TILED = 3  /* GROUP with k = 4 whose first pass tiles 256 lanes by a shared
+  MOTIF_KERNEL_TILED = 3, /* GROUP with k = 4 whose first pass tiles 256 lanes by a shared
                              (l-8)-base prefix (needs l >= 8; falls back to GROUP otherwise) */
+  MOTIF_KERNEL_BITSLICE = 4 /* CAND with the compare counted bit-sliced: 32 windows per step,
+                               a saturating counter in bit planes, no POPC (needs d <= 7; falls
+                               back to CAND otherwise) */
 } motif_kernel;
 
 /* How a search collects the accepted codes before returning them in ascending order (not in the

@@ -29,7 +29,7 @@ __all__ = [
     "motif_tune_cache_save", "motif_tune_cache_load", "motif_server_start", "motif_server_stop",
     "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
-    "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED",
+    "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED", "KERNEL_BITSLICE",
     "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP",
 ]
 
@@ -41,7 +41,7 @@ _lib = None
 OK, PENDING = 0, 1
 ERR_ARG, ERR_ALPHABET, ERR_CAPACITY, ERR_OOM = -1, -2, -3, -4
 ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_NOTFOUND = -5, -6, -7, -8, -9
-KERNEL_AUTO, KERNEL_CAND, KERNEL_GROUP, KERNEL_TILED = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_CAND, KERNEL_GROUP, KERNEL_TILED, KERNEL_BITSLICE = 0, 1, 2, 3, 4
 OUTPUT_AUTO, OUTPUT_LIST, OUTPUT_BITMAP = 0, 1, 2
 
 PROBE_KINDS = ["POPC", "LOP3", "IMNMX", "SHF", "IADD", "IMAD", "POPC_LOP3", "CMP_SPLIT",

@@ -116,9 +116,9 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->n = p->n; jd->t = p->t; jd->l = p->l; jd->d = p->d;
   jd->W = p->W; jd->wstride = p->wstride;
   jd->planes = p->d_planes; jd->codes = p->d_codes;
-  jd->kind = p->kind;
+  jd->kind = cand_like(p->kind) ? MOTIF_KERNEL_CAND : p->kind;
   jd->ks = p->kind == MOTIF_KERNEL_GROUP ? p->p : 0;
-  jd->cpt = p->kind == MOTIF_KERNEL_CAND ? p->p : 1;
+  jd->cpt = cand_like(p->kind) ? p->p : 1;
   jd->span0 = p->span0;
   jd->tiled = p->tiled ? 1 : 0;
   jd->lo = p->lo; jd->hi = p->hi;
@@ -168,10 +168,12 @@ static void free_queues(motif_plan_s* p) {
 int plan_configure(motif_plan_s* p) {
   const motif_opts& o = p->opts;
   // Kernel variant.
-  if (o.kernel < MOTIF_KERNEL_AUTO || o.kernel > MOTIF_KERNEL_TILED) return MOTIF_ERR_ARG;
+  if (o.kernel < MOTIF_KERNEL_AUTO || o.kernel > MOTIF_KERNEL_BITSLICE) return MOTIF_ERR_ARG;
   int kind = o.kernel == MOTIF_KERNEL_CAND ? MOTIF_KERNEL_CAND : MOTIF_KERNEL_GROUP;
+  if (o.kernel == MOTIF_KERNEL_BITSLICE)  // the bit-sliced counter holds distances up to 7
+    kind = p->d <= 7 ? MOTIF_KERNEL_BITSLICE : MOTIF_KERNEL_CAND;
   int pv;
-  if (kind == MOTIF_KERNEL_CAND) {
+  if (cand_like(kind)) {
     pv = o.cands_per_thread > 0 ? o.cands_per_thread : 2;
     if (pv != 1 && pv != 2 && pv != 4) return MOTIF_ERR_ARG;
   } else {
@@ -846,8 +848,8 @@ int motif_count_work(motif_plan p, uint64_t* compares, uint64_t* unit_steps) {
   if (rc) return rc;
   if (compares) *compares = c;
   if (!unit_steps) return MOTIF_OK;
-  if (p->kind == MOTIF_KERNEL_CAND || p->W <= 0 || p->hi <= p->lo) {
-    *unit_steps = p->kind == MOTIF_KERNEL_CAND ? c : 0;
+  if (cand_like(p->kind) || p->W <= 0 || p->hi <= p->lo) {
+    *unit_steps = cand_like(p->kind) ? c : 0;
     return MOTIF_OK;
   }
   JobDesc jd;

@@ -308,6 +308,8 @@ extern "C" int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best)
         cands.push_back({MOTIF_KERNEL_GROUP, 256, cps, 0, span, ks, 0});
   }
   for (int cpt : {1, 2, 4}) cands.push_back({MOTIF_KERNEL_CAND, 256, 0, cpt, 1, 0, 0});
+  if (p->d <= 7)
+    for (int cpt : {1, 2, 4}) cands.push_back({MOTIF_KERNEL_BITSLICE, 256, 0, cpt, 1, 0, 0});
   const motif_opts saved = p->opts;
   const uint64_t full_lo = p->lo, full_hi = p->hi;
   const uint64_t span_c = full_hi - full_lo;
@@ -319,7 +321,7 @@ extern "C" int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best)
     motif_opts o = saved;
     apply(&o, c);
     // Sub-range sized for the kernel's speed: the per-candidate kernel is ~50x slower.
-    const uint64_t want = c.kernel == MOTIF_KERNEL_CAND ? (1ull << 22) : (1ull << 26);
+    const uint64_t want = cand_like(c.kernel) ? (1ull << 22) : (1ull << 26);
     o.range_lo = full_lo;
     o.range_hi = full_lo + std::min<uint64_t>(span_c, want);
     p->opts = o;

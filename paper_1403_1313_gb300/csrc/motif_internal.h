@@ -12,6 +12,11 @@ constexpr int kWinAlign = 8;         // window rows padded to a multiple of 8 (f
 constexpr int kMaxKs = 4;            // GROUP kernel: at most 4 suffix bases (256-bit masks)
 constexpr int kPassNone = -1;
 
+// CAND and BITSLICE plans share their units (one candidate each), chunks and queues.
+inline bool cand_like(int kind) {
+  return kind == MOTIF_KERNEL_CAND || kind == MOTIF_KERNEL_BITSLICE;
+}
+
 // Per-job descriptor, written by the host before a job's first step and read-only on the device.
 struct JobDesc {
   int32_t n, t, l, d;
@@ -19,7 +24,8 @@ struct JobDesc {
   int32_t wstride;           // row stride of planes / codes in windows (multiple of kWinAlign)
   const uint2* planes;       // [n][wstride] compressed bit planes (E, O) of each window
   const uint64_t* codes;     // [n][wstride] packed 2l-bit code of each window
-  int32_t kind;              // MOTIF_KERNEL_CAND or MOTIF_KERNEL_GROUP
+  int32_t kind;              // unit semantics: MOTIF_KERNEL_CAND (also for BITSLICE plans) or
+                             // MOTIF_KERNEL_GROUP
   int32_t ks;                // GROUP: suffix bases per group (1..kMaxKs); CAND: 0
   int32_t cpt;               // CAND: candidates per lane in a fresh pass (1, 2 or 4)
   int32_t span0;             // sequences a fresh pass scans before the first compaction

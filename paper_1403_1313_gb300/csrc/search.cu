@@ -137,7 +137,8 @@ __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
 // one entry per warp in a REST pass.
 __device__ __forceinline__ unsigned long long tile_of(int kind, int p, int mode) {
   if (mode == kRest) return 1;
-  if (kind == MOTIF_KERNEL_CAND && mode == kFresh) return 32ull * p;
+  if ((kind == MOTIF_KERNEL_CAND || kind == MOTIF_KERNEL_BITSLICE) && mode == kFresh)
+    return 32ull * p;
   return 32;
 }
 
@@ -181,7 +182,123 @@ __device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int 
 }
 
 // FRESH / QUEUE tile: lane slot c of the warp owns item base + c*32 + lane.
+// ---------------------------------------------------------------------------------------------
+// BITSLICE: one candidate per lane slot, 64 windows per step counted bit-sliced.
+//
+// For each block of 32 windows and base position i the pass stages four 32-bit words, one per
+// base b of the candidate: bit j of word (i, b) is set when window j's base at position i is not
+// b.  The words of two neighbouring blocks sit side by side, so one 64-bit shared load gives a
+// lane the mismatch bits of its candidate's base against 64 windows.  They are added into
+// 3-bit saturating counters held as bit planes (c0, c1, c2 and a sticky overflow c3), three
+// positions at a time: a full adder turns three words into a sum and a carry (2 LOP3), which
+// are added to the counter (9 LOP3) -- no POPC.  Window j is within distance d when its counter
+// is at most d (d <= 7).
+
+// Staged words of one sequence: word (i, b, blk) at ((4 i + b) * nblkp + blk); nblkp, the block
+// count rounded up to even, pairs the blocks.  One warp per block.
+__device__ __forceinline__ void stage_bitslice(uint32_t* dst, const uint2* row, int W, int l,
+                                               int nblkp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int blk = warp; blk < nblkp; blk += nwarps) {
+    int j = blk * 32 + lane;
+    if (j >= W) j = W - 1;  // past the row: a copy of its last window (matches when it does)
+    const uint2 w = row[j];
+    for (int i = 0; i < l; ++i) {
+      const unsigned te = __ballot_sync(kFull, (w.x >> (l - 1 - i)) & 1u);
+      const unsigned to = __ballot_sync(kFull, (w.y >> (l - 1 - i)) & 1u);
+      if (lane < 4)
+        dst[(size_t)(4 * i + lane) * nblkp + blk] =
+            (te ^ ((lane & 1) ? kFull : 0u)) | (to ^ ((lane & 2) ? kFull : 0u));
+    }
+  }
+}
+
+// A bit-sliced counter of mismatches over 32 windows.
+struct SliceCount {
+  uint32_t c0, c1, c2, c3;
+  __device__ __forceinline__ void clear() { c0 = c1 = c2 = c3 = 0u; }
+  __device__ __forceinline__ void add1(uint32_t x) {  // + x
+    const uint32_t k = c1 & c0 & x;
+    c1 ^= c0 & x;
+    c0 ^= x;
+    c3 |= c2 & k;
+    c2 ^= k;
+  }
+  __device__ __forceinline__ void add3(uint32_t x1, uint32_t x2, uint32_t x3) {  // + x1+x2+x3
+    const uint32_t sum = x1 ^ x2 ^ x3;
+    const uint32_t cy = (x1 & x2) | (x1 & x3) | (x2 & x3);
+    add1(sum);
+    const uint32_t v = c2 & c1 & cy;  // + 2 cy
+    c2 ^= c1 & cy;
+    c1 ^= cy;
+    c3 |= v;
+  }
+  // Windows whose count is at most d (D0..D2: the bits of d as all-ones / all-zero masks).
+  __device__ __forceinline__ uint32_t within(uint32_t D0, uint32_t D1, uint32_t D2) const {
+    const uint32_t gt = (c2 & ~D2) | (~(c2 ^ D2) & ((c1 & ~D1) | (~(c1 ^ D1) & (c0 & ~D0))));
+    return ~c3 & ~gt;
+  }
+};
+
+// Adds positions [0, cnt) of one candidate against a block pair: `m` points at word (0, 0, pair)
+// of the sub-range, `bits` holds the candidate's bases (first base in its top two bits).
+__device__ __forceinline__ void bitslice_pair(const uint32_t* __restrict__ m, int nblkp,
+                                              uint32_t bits, int cnt, SliceCount& a,
+                                              SliceCount& b) {
+  const int step = 4 * nblkp;  // words between positions
+  int i = 0;
+  for (; i + 3 <= cnt; i += 3) {
+    const uint2 x1 = *reinterpret_cast<const uint2*>(m + (bits >> 30) * nblkp);
+    const uint2 x2 = *reinterpret_cast<const uint2*>(m + step + ((bits >> 28) & 3u) * nblkp);
+    const uint2 x3 = *reinterpret_cast<const uint2*>(m + 2 * step + ((bits >> 26) & 3u) * nblkp);
+    bits <<= 6;
+    m += 3 * step;
+    a.add3(x1.x, x2.x, x3.x);
+    b.add3(x1.y, x2.y, x3.y);
+  }
+  for (; i < cnt; ++i) {
+    const uint2 x = *reinterpret_cast<const uint2*>(m + (bits >> 30) * nblkp);
+    bits <<= 2;
+    m += step;
+    a.add1(x.x);
+    b.add1(x.y);
+  }
+}
+
+// Scans one staged sequence for up to CPT candidates (their codes); returns the subset of
+// `alive` that has a window within distance d.
 template <int CPT>
+__device__ __forceinline__ unsigned scan_bitslice(const uint32_t* __restrict__ stage, int nblkp,
+                                                  int l, int d, const uint64_t (&code)[CPT],
+                                                  unsigned alive) {
+  const uint32_t D0 = (d & 1) ? kFull : 0u, D1 = (d & 2) ? kFull : 0u, D2 = (d & 4) ? kFull : 0u;
+  const int nh = l > 16 ? l - 16 : 0;  // positions held in the code's high word
+  const int nl = l - nh;
+  uint32_t hi[CPT], lo[CPT];
+#pragma unroll
+  for (int c = 0; c < CPT; ++c) {
+    hi[c] = nh ? (uint32_t)(code[c] >> 32) << (32 - 2 * nh) : 0u;
+    lo[c] = (uint32_t)code[c] << (32 - 2 * nl);
+  }
+  unsigned matched = 0;
+  for (int bp = 0; bp < nblkp; bp += 2) {
+    const uint32_t* m = stage + bp;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      if (!(alive & ~matched & (1u << c))) continue;
+      SliceCount a, b;
+      a.clear();
+      b.clear();
+      if (nh) bitslice_pair(m, nblkp, hi[c], nh, a, b);
+      bitslice_pair(m + (size_t)4 * nh * nblkp, nblkp, lo[c], nl, a, b);
+      if (a.within(D0, D1, D2) | b.within(D0, D1, D2)) matched |= 1u << c;
+    }
+    if ((matched & alive) == alive) break;  // every live candidate has matched this sequence
+  }
+  return matched & alive;
+}
+
+template <int KIND, int CPT>
 __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
                           unsigned long long base, const uint4* stage) {
   const int lane = threadIdx.x & 31;
@@ -199,8 +316,19 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
     }
   }
   const int wpad = jd.wstride;
-  for (int s = p.s0; s < p.s1 && alive; ++s)
-    alive = scan_cand<CPT>(stage + (size_t)(s - p.s0) * (wpad >> 1), wpad, jd.d, E, O, alive);
+  if (KIND == MOTIF_KERNEL_BITSLICE) {
+    uint64_t code[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) code[c] = p.chunk_base + off[c];
+    const int nblkp = ((jd.W + 63) >> 6) << 1;  // blocks of 32 windows, an even number
+    const uint32_t* words = reinterpret_cast<const uint32_t*>(stage);
+    for (int s = p.s0; s < p.s1 && alive; ++s)
+      alive = scan_bitslice<CPT>(words + (size_t)(s - p.s0) * nblkp * 4 * jd.l, nblkp, jd.l,
+                                 jd.d, code, alive);
+  } else {
+    for (int s = p.s0; s < p.s1 && alive; ++s)
+      alive = scan_cand<CPT>(stage + (size_t)(s - p.s0) * (wpad >> 1), wpad, jd.d, E, O, alive);
+  }
   __syncwarp();
   const unsigned cnt = __popc(alive);
   if (p.s1 >= jd.n && jd.bitmap) {
@@ -728,6 +856,11 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       uint4* dst = reinterpret_cast<uint4*>(smem);
       const uint4* src = reinterpret_cast<const uint4*>(jd.planes + (size_t)p.s0 * wpad);
       for (int i = tid; i < nst * (wpad >> 1); i += blockDim.x) dst[i] = src[i];
+    } else if (KIND == MOTIF_KERNEL_BITSLICE) {
+      const int nblkp = ((jd.W + 63) >> 6) << 1;
+      for (int q = 0; q < nst; ++q)
+        stage_bitslice(reinterpret_cast<uint32_t*>(smem) + (size_t)q * nblkp * 4 * jd.l,
+                       jd.planes + (size_t)(p.s0 + q) * wpad, jd.W, jd.l, nblkp);
     } else {
       // The ball table stays in global memory (read through L1 only for the rare hits);
       // shared memory holds the staged prefix planes, suffix values and the hit lists.
@@ -790,10 +923,10 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       stop = __shfl_sync(kFull, stop, 0);
       if (stop) break;
       base = __shfl_sync(kFull, base, 0);
-      if (KIND == MOTIF_KERNEL_CAND) {
+      if (KIND == MOTIF_KERNEL_CAND || KIND == MOTIF_KERNEL_BITSLICE) {
         if (p.mode == kRest) cand_rest(jd, st, p, base);
-        else if (p.mode == kFresh) cand_tile<P>(jd, st, p, base, stage4);
-        else cand_tile<1>(jd, st, p, base, stage4);
+        else if (p.mode == kFresh) cand_tile<KIND, P>(jd, st, p, base, stage4);
+        else cand_tile<KIND, 1>(jd, st, p, base, stage4);
       } else {
         if (p.mode == kRest) group_rest<P>(jd, st, p, base, stage_ball);
         else group_tile<P>(jd, st, p, base, stage4, stage_sfx, stage_ball, hits);
@@ -988,6 +1121,12 @@ const void* step_function(int kind, int p) {
       case 2: return step_fn<MOTIF_KERNEL_CAND, 2>();
       case 4: return step_fn<MOTIF_KERNEL_CAND, 4>();
     }
+  } else if (kind == MOTIF_KERNEL_BITSLICE) {
+    switch (p) {
+      case 1: return step_fn<MOTIF_KERNEL_BITSLICE, 1>();
+      case 2: return step_fn<MOTIF_KERNEL_BITSLICE, 2>();
+      case 4: return step_fn<MOTIF_KERNEL_BITSLICE, 4>();
+    }
   } else if (kind == MOTIF_KERNEL_GROUP) {
     switch (p) {
       case 1: return step_fn<MOTIF_KERNEL_GROUP, 1>();
@@ -1005,6 +1144,9 @@ bool step_variant_ok(int kind, int p) { return step_function(kind, p) != nullptr
 
 size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
+  if (kind == MOTIF_KERNEL_BITSLICE)  // 4 words per base position (l <= 32) per 32 windows,
+                                      // an even number of blocks
+    return (size_t)kMaxStageSeqs * (((wstride + 63) / 64) * 2) * 4 * 32 * 4;
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
   b += (size_t)kHitCap * block * 4;
@@ -1022,9 +1164,10 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
 // share the kernels, and one caller's smaller request must not break another's launch.
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem) {
   static std::mutex mu;
-  static size_t set[3][kMaxKs + 1] = {};
+  static size_t set[MOTIF_KERNEL_BITSLICE + 1][kMaxKs + 1] = {};
   const void* f = step_function(kind, p);
-  if (!f || kind < 1 || kind > 2 || p < 1 || p > kMaxKs) return cudaErrorInvalidValue;
+  if (!f || kind < 1 || kind > MOTIF_KERNEL_BITSLICE || p < 1 || p > kMaxKs)
+    return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> g(mu);
   if (smem <= set[kind][p]) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

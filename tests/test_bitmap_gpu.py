@@ -26,6 +26,7 @@ VARIANTS = [
     ("group1", dict(kernel=m.KERNEL_GROUP, suffix_bases=1)),
     ("cand1", dict(kernel=m.KERNEL_CAND, cands_per_thread=1)),
     ("cand4", dict(kernel=m.KERNEL_CAND, cands_per_thread=4)),
+    ("bitslice2", dict(kernel=m.KERNEL_BITSLICE, cands_per_thread=2)),
 ]
 OUTPUTS = [("list", m.OUTPUT_LIST), ("bitmap", m.OUTPUT_BITMAP)]
 

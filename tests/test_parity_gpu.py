@@ -30,6 +30,9 @@ VARIANTS = [
     ("cand1", dict(kernel=m.KERNEL_CAND, cands_per_thread=1)),
     ("cand2", dict(kernel=m.KERNEL_CAND, cands_per_thread=2)),
     ("cand4", dict(kernel=m.KERNEL_CAND, cands_per_thread=4)),
+    ("bitslice1", dict(kernel=m.KERNEL_BITSLICE, cands_per_thread=1)),
+    ("bitslice2", dict(kernel=m.KERNEL_BITSLICE, cands_per_thread=2)),
+    ("bitslice4", dict(kernel=m.KERNEL_BITSLICE, cands_per_thread=4)),
 ]
 
 
@@ -287,3 +290,16 @@ def test_batch_matches_oracle(use_graph):
     for job, got in zip(jobs, outs):
         ref, _ = oracle.search(job.rows(), job.l, job.d)
         assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("l,d", [(9, 8), (12, 9)])
+def test_bitslice_beyond_its_counter_falls_back_to_cand(l, d):
+    """The bit-sliced counter holds distances up to 7; larger d runs the POPC compare."""
+    rows = rand_rows(random.Random(l * d), 3, 25)
+    plan = m.motif_plan_create(3, 25, l, d, _opts(kernel=m.KERNEL_BITSLICE))
+    m.motif_load_seqs(plan, rows)
+    got = m.motif_search(plan)
+    assert m.motif_stats(plan)["kernel"] == m.KERNEL_CAND
+    m.motif_plan_destroy(plan)
+    ref, _ = oracle.search(rows, l, d)
+    assert np.array_equal(got, ref)

@@ -74,9 +74,10 @@ def test_group_unit_steps_match_definition(l, d, k, seed):
     assert unit_steps == _group_tally(rows, l, d, k)
 
 
-def test_cand_unit_steps_equal_compares():
+@pytest.mark.parametrize("kernel", [m.KERNEL_CAND, m.KERNEL_BITSLICE])
+def test_cand_unit_steps_equal_compares(kernel):
     job = fmgen.fm_job(5, 60, 7, 2, 9)
-    plan = _plan(job.rows(), 7, 2, kernel=m.KERNEL_CAND)
+    plan = _plan(job.rows(), 7, 2, kernel=kernel)
     compares, unit_steps = m.motif_count_work(plan)
     m.motif_plan_destroy(plan)
     assert compares == unit_steps == oracle.search(job.rows(), 7, 2)[1]
@@ -87,7 +88,7 @@ def test_autotune_and_cache_roundtrip(tmp_path):
     plan = _plan(job.rows(), 11, 3)
     ref = m.motif_search(plan)
     best = m.motif_autotune(plan, 3000)
-    assert best.kernel in (m.KERNEL_CAND, m.KERNEL_GROUP, m.KERNEL_TILED)
+    assert best.kernel in (m.KERNEL_CAND, m.KERNEL_GROUP, m.KERNEL_TILED, m.KERNEL_BITSLICE)
     assert np.array_equal(m.motif_search(plan), ref)  # the tuned plan gives the same result
     path = str(tmp_path / "tune.json")
     m.motif_tune_cache_save(path)

@@ -181,21 +181,20 @@ __device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int 
   return matched & alive;
 }
 
-// FRESH / QUEUE tile: lane slot c of the warp owns item base + c*32 + lane.
 // ---------------------------------------------------------------------------------------------
-// BITSLICE: one candidate per lane slot, 64 windows per step counted bit-sliced.
+// BITSLICE: one candidate per lane slot, 128 windows per step counted bit-sliced.
 //
 // For each block of 32 windows and base position i the pass stages four 32-bit words, one per
 // base b of the candidate: bit j of word (i, b) is set when window j's base at position i is not
-// b.  The words of two neighbouring blocks sit side by side, so one 64-bit shared load gives a
-// lane the mismatch bits of its candidate's base against 64 windows.  They are added into
+// b.  The words of four neighbouring blocks sit side by side, so one 128-bit shared load gives
+// a lane the mismatch bits of its candidate's base against 128 windows.  They are added into
 // 3-bit saturating counters held as bit planes (c0, c1, c2 and a sticky overflow c3), three
 // positions at a time: a full adder turns three words into a sum and a carry (2 LOP3), which
 // are added to the counter (9 LOP3) -- no POPC.  Window j is within distance d when its counter
 // is at most d (d <= 7).
 
 // Staged words of one sequence: word (i, b, blk) at ((4 i + b) * nblkp + blk); nblkp, the block
-// count rounded up to even, pairs the blocks.  One warp per block.
+// count rounded up to a multiple of 4, groups the blocks in fours.  One warp per block.
 __device__ __forceinline__ void stage_bitslice(uint32_t* dst, const uint2* row, int W, int l,
                                                int nblkp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -240,28 +239,32 @@ struct SliceCount {
   }
 };
 
-// Adds positions [0, cnt) of one candidate against a block pair: `m` points at word (0, 0, pair)
-// of the sub-range, `bits` holds the candidate's bases (first base in its top two bits).
-__device__ __forceinline__ void bitslice_pair(const uint32_t* __restrict__ m, int nblkp,
+// Adds positions [0, cnt) of one candidate against four blocks: `m` points at word (0, 0, first
+// block) of the sub-range, `bits` holds the candidate's bases (first base in its top two bits).
+__device__ __forceinline__ void bitslice_quad(const uint32_t* __restrict__ m, int nblkp,
                                               uint32_t bits, int cnt, SliceCount& a,
-                                              SliceCount& b) {
+                                              SliceCount& b, SliceCount& c, SliceCount& e) {
   const int step = 4 * nblkp;  // words between positions
   int i = 0;
   for (; i + 3 <= cnt; i += 3) {
-    const uint2 x1 = *reinterpret_cast<const uint2*>(m + (bits >> 30) * nblkp);
-    const uint2 x2 = *reinterpret_cast<const uint2*>(m + step + ((bits >> 28) & 3u) * nblkp);
-    const uint2 x3 = *reinterpret_cast<const uint2*>(m + 2 * step + ((bits >> 26) & 3u) * nblkp);
+    const uint4 x1 = *reinterpret_cast<const uint4*>(m + (bits >> 30) * nblkp);
+    const uint4 x2 = *reinterpret_cast<const uint4*>(m + step + ((bits >> 28) & 3u) * nblkp);
+    const uint4 x3 = *reinterpret_cast<const uint4*>(m + 2 * step + ((bits >> 26) & 3u) * nblkp);
     bits <<= 6;
     m += 3 * step;
     a.add3(x1.x, x2.x, x3.x);
     b.add3(x1.y, x2.y, x3.y);
+    c.add3(x1.z, x2.z, x3.z);
+    e.add3(x1.w, x2.w, x3.w);
   }
   for (; i < cnt; ++i) {
-    const uint2 x = *reinterpret_cast<const uint2*>(m + (bits >> 30) * nblkp);
+    const uint4 x = *reinterpret_cast<const uint4*>(m + (bits >> 30) * nblkp);
     bits <<= 2;
     m += step;
     a.add1(x.x);
     b.add1(x.y);
+    c.add1(x.z);
+    e.add1(x.w);
   }
 }
 
@@ -281,23 +284,28 @@ __device__ __forceinline__ unsigned scan_bitslice(const uint32_t* __restrict__ s
     lo[c] = (uint32_t)code[c] << (32 - 2 * nl);
   }
   unsigned matched = 0;
-  for (int bp = 0; bp < nblkp; bp += 2) {
+  for (int bp = 0; bp < nblkp; bp += 4) {
     const uint32_t* m = stage + bp;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (!(alive & ~matched & (1u << c))) continue;
-      SliceCount a, b;
+      SliceCount a, b, cc, e;
       a.clear();
       b.clear();
-      if (nh) bitslice_pair(m, nblkp, hi[c], nh, a, b);
-      bitslice_pair(m + (size_t)4 * nh * nblkp, nblkp, lo[c], nl, a, b);
-      if (a.within(D0, D1, D2) | b.within(D0, D1, D2)) matched |= 1u << c;
+      cc.clear();
+      e.clear();
+      if (nh) bitslice_quad(m, nblkp, hi[c], nh, a, b, cc, e);
+      bitslice_quad(m + (size_t)4 * nh * nblkp, nblkp, lo[c], nl, a, b, cc, e);
+      if (a.within(D0, D1, D2) | b.within(D0, D1, D2) | cc.within(D0, D1, D2) |
+          e.within(D0, D1, D2))
+        matched |= 1u << c;
     }
     if ((matched & alive) == alive) break;  // every live candidate has matched this sequence
   }
   return matched & alive;
 }
 
+// FRESH / QUEUE tile: lane slot c of the warp owns item base + c*32 + lane.
 template <int KIND, int CPT>
 __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
                           unsigned long long base, const uint4* stage) {
@@ -320,7 +328,7 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
     uint64_t code[CPT];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) code[c] = p.chunk_base + off[c];
-    const int nblkp = ((jd.W + 63) >> 6) << 1;  // blocks of 32 windows, an even number
+    const int nblkp = ((jd.W + 127) >> 7) << 2;  // blocks of 32 windows, a multiple of 4
     const uint32_t* words = reinterpret_cast<const uint32_t*>(stage);
     for (int s = p.s0; s < p.s1 && alive; ++s)
       alive = scan_bitslice<CPT>(words + (size_t)(s - p.s0) * nblkp * 4 * jd.l, nblkp, jd.l,
@@ -857,7 +865,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       const uint4* src = reinterpret_cast<const uint4*>(jd.planes + (size_t)p.s0 * wpad);
       for (int i = tid; i < nst * (wpad >> 1); i += blockDim.x) dst[i] = src[i];
     } else if (KIND == MOTIF_KERNEL_BITSLICE) {
-      const int nblkp = ((jd.W + 63) >> 6) << 1;
+      const int nblkp = ((jd.W + 127) >> 7) << 2;
       for (int q = 0; q < nst; ++q)
         stage_bitslice(reinterpret_cast<uint32_t*>(smem) + (size_t)q * nblkp * 4 * jd.l,
                        jd.planes + (size_t)(p.s0 + q) * wpad, jd.W, jd.l, nblkp);
@@ -1145,8 +1153,8 @@ bool step_variant_ok(int kind, int p) { return step_function(kind, p) != nullptr
 size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
   if (kind == MOTIF_KERNEL_BITSLICE)  // 4 words per base position (l <= 32) per 32 windows,
-                                      // an even number of blocks
-    return (size_t)kMaxStageSeqs * (((wstride + 63) / 64) * 2) * 4 * 32 * 4;
+                                      // blocks in fours
+    return (size_t)kMaxStageSeqs * (((wstride + 127) / 128) * 4) * 4 * 32 * 4;
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
   b += (size_t)kHitCap * block * 4;

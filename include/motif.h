@@ -63,6 +63,18 @@ typedef enum {
 
 /* How a search collects the accepted codes before returning them in ascending order (not in the
  * paper, whose output is the surviving l-mers, Sec. III.A; a GPU design choice). */
+/* Which candidates a search enumerates. */
+typedef enum {
+  MOTIF_SEED_ALL = 0,           /* every index of the range (Sec. IV.A) */
+  MOTIF_SEED_NEIGHBOURHOOD = 1  /* only the l-mers within d of a window of the first sequence: the
+                                   others cannot match it, so the result is the same.  This is
+                                   the candidate pruning of Planted Motif Search, which the paper
+                                   lists among the exact methods (Sec. I.A) and as future work
+                                   (Sec. VI).  CAND and BITSLICE kernels; the table of difference
+                                   patterns (sum over k <= d of C(l,k) 3^k entries) may hold at
+                                   most 2^24 of them */
+} motif_seed;
+
 typedef enum {
   MOTIF_OUTPUT_AUTO = 0,   /* BITMAP where the expected survivors are dense, else LIST */
   MOTIF_OUTPUT_LIST = 1,   /* append codes to a list, then sort and deduplicate it */
@@ -92,6 +104,8 @@ typedef struct {
   void* alloc_ctx;
   uint64_t range_lo;        /* candidate sub-range [range_lo, range_hi) of [0, 4^l), the */
   uint64_t range_hi;        /* per-worker index range of Sec. IV.A; range_hi == 0: all */
+  int32_t seed;             /* motif_seed */
+  int32_t reserved;         /* 0 */
 } motif_opts;
 
 typedef struct {
@@ -202,6 +216,11 @@ int motif_count_compares(motif_plan p, uint64_t* out);
  * window within d, W for a sequence that leaves none alive, and nothing after it.  Either
  * pointer may be NULL. */
 int motif_count_work(motif_plan p, uint64_t* compares, uint64_t* unit_steps);
+
+/* For a plan with MOTIF_SEED_NEIGHBOURHOOD: *out receives how many candidates of its range lie
+ * within d of some window of the first loaded sequence (the candidates its search scans from
+ * the second sequence on).  Blocking.  MOTIF_ERR_STATE for other plans or before a load. */
+int motif_seed_count(motif_plan p, uint64_t* out);
 
 /* Statistics of the plan: the last search / served job, plus device times summed over every
  * search since the previous call (waits for the plan's stream). */

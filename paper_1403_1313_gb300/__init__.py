@@ -30,7 +30,8 @@ __all__ = [
     "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
     "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED", "KERNEL_BITSLICE",
-    "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP",
+    "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP", "SEED_ALL", "SEED_NEIGHBOURHOOD",
+    "motif_seed_count",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -43,6 +44,7 @@ ERR_ARG, ERR_ALPHABET, ERR_CAPACITY, ERR_OOM = -1, -2, -3, -4
 ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_NOTFOUND = -5, -6, -7, -8, -9
 KERNEL_AUTO, KERNEL_CAND, KERNEL_GROUP, KERNEL_TILED, KERNEL_BITSLICE = 0, 1, 2, 3, 4
 OUTPUT_AUTO, OUTPUT_LIST, OUTPUT_BITMAP = 0, 1, 2
+SEED_ALL, SEED_NEIGHBOURHOOD = 0, 1
 
 PROBE_KINDS = ["POPC", "LOP3", "IMNMX", "SHF", "IADD", "IMAD", "POPC_LOP3", "CMP_SPLIT",
                "CMP_FOLD", "LDS64_DIV"]
@@ -59,7 +61,7 @@ class motif_opts(ctypes.Structure):
         ("timeout_ms", ctypes.c_int32), ("output", ctypes.c_int32), ("alloc", _ALLOC_FN),
         ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p), ("range_lo", ctypes.c_uint64),
-        ("range_hi", ctypes.c_uint64),
+        ("range_hi", ctypes.c_uint64), ("seed", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -130,6 +132,7 @@ def _load():
             "motif_search_device": (ctypes.c_int, [P, P, i64, P]),
             "motif_count_compares": (ctypes.c_int, [P, u64p]),
             "motif_count_work": (ctypes.c_int, [P, u64p, u64p]),
+            "motif_seed_count": (ctypes.c_int, [P, u64p]),
             "motif_kernel_launches": (ctypes.c_uint64, []),
             "motif_stats": (ctypes.c_int, [P, ctypes.POINTER(motif_stats_t)]),
             "motif_batch_search": (ctypes.c_int, [i32, ctypes.POINTER(P), ctypes.POINTER(u64p), i64p, i64p, ctypes.POINTER(i32), i32]),
@@ -313,6 +316,12 @@ def motif_search_device(plan: Plan, d_out, capacity: int, d_count) -> None:
     pc = d_count.data_ptr() if hasattr(d_count, "data_ptr") else int(d_count)
     _check(_load().motif_search_device(plan, ctypes.c_void_p(po), capacity, ctypes.c_void_p(pc)),
            "motif_search_device")
+
+
+def motif_seed_count(plan: Plan) -> int:
+    v = ctypes.c_uint64(0)
+    _check(_load().motif_seed_count(plan, ctypes.byref(v)), "motif_seed_count")
+    return int(v.value)
 
 
 def motif_count_compares(plan: Plan) -> int:

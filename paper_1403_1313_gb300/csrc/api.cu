@@ -134,6 +134,38 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->bm_base = p->bm_base;
   jd->valid = p->ragged ? p->d_valid : nullptr;
   jd->wrow = p->ragged ? p->d_wrow : nullptr;
+  jd->seed = p->seeded ? p->d_seed : nullptr;
+  jd->seed_base = p->seed_base;
+}
+
+// Number of l-base difference patterns with at most d differing bases: sum C(l,k) 3^k.
+static uint64_t pattern_count(int l, int d) {
+  uint64_t term = 1, sum = 0;
+  for (int k = 0; k <= std::min(d, l); ++k) {
+    sum += term;
+    if (sum > (1ull << 40)) return sum;
+    term = term * (uint64_t)(l - k) / (uint64_t)(k + 1) * 3;
+  }
+  return sum;
+}
+
+// Every code-space XOR mask that changes at most d bases of an l-mer (each changed base gets
+// one of its 3 other values).
+static void difference_patterns(int l, int d, std::vector<uint64_t>& out) {
+  out.clear();
+  std::vector<int> pos;
+  // depth-first over increasing positions; each chosen position takes a nonzero 2-bit digit
+  struct Rec {
+    int l, d;
+    std::vector<uint64_t>* out;
+    void go(int from, int left, uint64_t mask) {
+      out->push_back(mask);
+      if (left == 0) return;
+      for (int i = from; i < l; ++i)
+        for (uint64_t v = 1; v <= 3; ++v) go(i + 1, left - 1, mask | (v << (2 * (l - 1 - i))));
+    }
+  } rec{l, d, &out};
+  rec.go(0, std::min(d, l), 0);
 }
 
 // Probability, for uniform i.i.d. bases, that a candidate matches one sequence: a window
@@ -217,6 +249,18 @@ int plan_configure(motif_plan_s* p) {
   const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
   p->tiled = tiled_ok && !(o.kernel == MOTIF_KERNEL_AUTO && few_long_tiles);
   p->tiled_in_batch = tiled_ok;
+  // Candidate seeding by the first sequence's d-neighbourhoods (per-candidate kernels only).
+  if (o.seed < MOTIF_SEED_ALL || o.seed > MOTIF_SEED_NEIGHBOURHOOD || o.reserved != 0)
+    return MOTIF_ERR_ARG;
+  p->seeded = o.seed == MOTIF_SEED_NEIGHBOURHOOD;
+  if (p->seeded) {
+    if (!cand_like(kind)) return MOTIF_ERR_ARG;
+    p->npat = pattern_count(p->l, p->d);
+    p->seed_base = p->lo & ~63ull;
+    const uint64_t bits = ((p->hi + 63) & ~63ull) - p->seed_base;
+    if (p->npat > (1ull << 24) || bits > (1ull << 36)) return MOTIF_ERR_ARG;
+    p->seed_words = std::max<uint64_t>(bits / 32, 1);
+  }
   // Output: a bitmap over the range (rounded out to whole 256-code groups) where it holds at
   // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size.
   const uint64_t bm_base = p->lo & ~255ull;
@@ -257,6 +301,27 @@ void invalidate_graphs(motif_plan_s* p) {
   p->gs_scratch = nullptr;
 }
 
+void free_seed(motif_plan_s* p) {
+  if (p->d_pat) plan_free(p, p->d_pat, p->pat_alloc * 8);
+  if (p->d_seed) plan_free(p, p->d_seed, p->seed_alloc_words * 4);
+  if (p->d_seed_scratch)
+    plan_free(p, p->d_seed_scratch, bitmap_scratch_words(p->seed_alloc_words) * 4);
+  if (p->d_seed_count) plan_free(p, p->d_seed_count, sizeof(unsigned long long));
+  p->d_pat = nullptr;
+  p->d_seed = nullptr;
+  p->d_seed_scratch = nullptr;
+  p->d_seed_count = nullptr;
+  p->seed_alloc_words = p->pat_alloc = 0;
+}
+
+int prepare_seed(motif_plan_s* p, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p->d_seed, 0, p->seed_words * 4, s);
+  if (e == cudaSuccess)
+    e = launch_seed_scatter(p->d_codes, p->W, p->d_pat, p->npat, p->lo, p->hi, p->d_seed,
+                            p->seed_base, s);
+  return status_from_cuda(e);
+}
+
 void free_bitmap(motif_plan_s* p) {
   if (p->d_bitmap) plan_free(p, p->d_bitmap, p->bm_alloc_words * 4);
   if (p->d_bm_scratch) plan_free(p, p->d_bm_scratch, bitmap_scratch_words(p->bm_alloc_words) * 4);
@@ -284,6 +349,26 @@ int plan_ensure_buffers(motif_plan_s* p) {
     p->d_out = (uint64_t*)plan_alloc(p, (size_t)(1 << 16) * 8);
     if (!p->d_out) return MOTIF_ERR_OOM;
     p->out_cap = 1 << 16;
+  }
+  if (p->seeded && (p->seed_alloc_words != p->seed_words || p->pat_alloc != p->npat)) {
+    free_seed(p);
+    std::vector<uint64_t> pat;
+    difference_patterns(p->l, p->d, pat);
+    p->d_pat = (uint64_t*)plan_alloc(p, pat.size() * 8);
+    p->d_seed = (uint32_t*)plan_alloc(p, p->seed_words * 4);
+    p->d_seed_scratch = (unsigned*)plan_alloc(p, bitmap_scratch_words(p->seed_words) * 4);
+    p->d_seed_count = (unsigned long long*)plan_alloc(p, sizeof(unsigned long long));
+    p->desc_out = nullptr;  // the descriptor names the seed bitmap
+    if (!p->d_pat || !p->d_seed || !p->d_seed_scratch || !p->d_seed_count) {
+      free_seed(p);
+      return MOTIF_ERR_OOM;
+    }
+    p->pat_alloc = pat.size();
+    p->seed_alloc_words = p->seed_words;
+    cudaError_t e = cudaMemcpyAsync(p->d_pat, pat.data(), pat.size() * 8,
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // `pat` is a local vector
+    if (e != cudaSuccess) return status_from_cuda(e);
   }
   if (p->bitmap && p->bm_alloc_words != p->bm_words) {
     free_bitmap(p);
@@ -392,6 +477,10 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   if (p->bitmap) {
     cudaError_t e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
+  }
+  if (p->seeded) {
+    rc = prepare_seed(p, p->stream);
+    if (rc) return rc;
   }
   // Upload the descriptor when (out, cap) changed; it lives in pinned memory so the copy is
   // stream-ordered without blocking the host.
@@ -585,6 +674,7 @@ void motif_plan_destroy(motif_plan p) {
   plan_free(p, p->d_out, (size_t)p->out_cap * 8);
   plan_free(p, p->d_sort, p->sort_bytes);
   free_bitmap(p);
+  free_seed(p);
   free_ragged(p);
   cudaStreamSynchronize(p->stream);
   for (cudaEvent_t ev : p->evq)
@@ -814,6 +904,29 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
   note_launches(1);
   finalize_count_kernel<<<1, 32, 0, p->stream>>>(p->d_err, &p->d_state->out_count, d_out_count);
   return status_from_cuda(cudaGetLastError());
+}
+
+int motif_seed_count(motif_plan p, uint64_t* out) {
+  if (!p || !out) return MOTIF_ERR_ARG;
+  if (!p->loaded || !p->seeded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  int rc = check_alphabet(p);
+  if (rc) return rc;
+  *out = 0;
+  if (p->W <= 0 || p->hi <= p->lo) return MOTIF_OK;
+  rc = plan_ensure_buffers(p);
+  if (rc) return rc;
+  rc = prepare_seed(p, p->stream);
+  if (rc) return rc;
+  unsigned long long n = 0;
+  cudaError_t e = launch_bitmap_count(p->d_seed, p->seed_words, p->d_seed_scratch,
+                                      p->d_seed_count, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&n, p->d_seed_count, sizeof(n), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  *out = n;
+  return MOTIF_OK;
 }
 
 int motif_count_compares(motif_plan p, uint64_t* out) {

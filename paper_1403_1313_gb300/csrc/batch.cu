@@ -146,6 +146,8 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     for (size_t i = 0; i < ids.size() && e == cudaSuccess; ++i) {
       motif_plan_s* p = plans[ids[i]];
       if (p->bitmap) e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, c->stream);
+      if (e == cudaSuccess && p->seeded && prepare_seed(p, c->stream) != MOTIF_OK)
+        e = cudaErrorUnknown;
     }
     // Zero the states; CTAs rotate their starting job so every job's tiles start at once.
     if (e == cudaSuccess)

@@ -45,6 +45,8 @@ struct JobDesc {
   uint64_t bm_base;          //   being appended to out (bm_base is a multiple of 64)
   const uint8_t* valid;      // ragged / masked rows: [n][wstride] window flags (null = all valid);
   const int32_t* wrow;       //   per-row window counts (null = W); read by the tally kernel only
+  const uint32_t* seed;      // non-null: only candidates whose bit (code - seed_base) is set are
+  uint64_t seed_base;        //   searched, from the second sequence on (fresh CAND passes)
 };
 
 // Per-job device state, advanced by the last CTA of every step.
@@ -131,6 +133,14 @@ size_t sort_scratch_bytes(int64_t cap, int sms);
 // in ascending order (at most cap of them) and their number to *count.  scratch holds
 // bitmap_scratch_words(nwords) words.
 uint64_t bitmap_scratch_words(uint64_t nwords);
+// Number of set bits of bm (nwords words) into *count (the first two kernels of the compaction).
+cudaError_t launch_bitmap_count(const uint32_t* bm, uint64_t nwords, unsigned* scratch,
+                                unsigned long long* count, cudaStream_t s);
+// Sets bit (c - base) of `seed` for every code c = codes0[j] ^ pat[r] (j < W, r < npat) that
+// lies in [lo, hi): the candidates within d of a window of the first sequence.
+cudaError_t launch_seed_scatter(const uint64_t* codes0, int W, const uint64_t* pat,
+                                uint64_t npat, uint64_t lo, uint64_t hi, uint32_t* seed,
+                                uint64_t base, cudaStream_t s);
 cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t base,
                                   uint64_t* out, int64_t cap, unsigned* scratch,
                                   unsigned long long* count, cudaStream_t s);

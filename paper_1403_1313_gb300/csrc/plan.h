@@ -69,6 +69,17 @@ struct motif_plan_s {
   int64_t graph_searches = 0;        // graph launches since the last fold (launch accounting)
   unsigned last_steps = 0;           // steps of the last folded search
 
+  // Candidates seeded by the d-neighbourhoods of the first sequence's windows
+  // (MOTIF_SEED_NEIGHBOURHOOD): the difference patterns, the seed bitmap over
+  // [seed_base, seed_base + 32*seed_words) and its count scratch.
+  bool seeded = false;
+  uint64_t npat = 0;
+  uint64_t* d_pat = nullptr;
+  uint32_t* d_seed = nullptr;
+  unsigned* d_seed_scratch = nullptr;
+  unsigned long long* d_seed_count = nullptr;
+  uint64_t seed_base = 0, seed_words = 0, seed_alloc_words = 0, pat_alloc = 0;
+
   // Ragged / masked input (motif_load_seqs_var): per-row lengths and window counts, window
   // flags, and whether some row has no valid window (then nothing can be accepted).
   bool ragged = false;
@@ -106,6 +117,9 @@ int plan_configure(motif_plan_s* p);
 // Allocates the survivor queues and the default output buffer on first use.
 int plan_ensure_buffers(motif_plan_s* p);
 void free_bitmap(motif_plan_s* p);
+void free_seed(motif_plan_s* p);
+// Builds the seed bitmap of a seeded plan for its loaded sequences (on stream s).
+int prepare_seed(motif_plan_s* p, cudaStream_t s);
 // Drops the plan's cached graphs and descriptor upload (after a configuration change).
 void invalidate_graphs(motif_plan_s* p);
 

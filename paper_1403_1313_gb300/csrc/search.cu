@@ -113,8 +113,9 @@ __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
   if (pass_seq == 0) {
     p.mode = jd.tiled ? kTiled : kFresh;
     p.work = p.chunk_units;
-    p.s0 = 0;
-    p.s1 = jd.tiled ? jd.n : (jd.span0 < jd.n ? jd.span0 : jd.n);
+    // A seeded search has already kept only candidates that match the first sequence.
+    p.s0 = jd.seed ? 1 : 0;
+    p.s1 = jd.tiled ? jd.n : (p.s0 + jd.span0 < jd.n ? p.s0 + jd.span0 : jd.n);
     p.qin = 0;
     p.qout = 0;
   } else {
@@ -320,7 +321,12 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
     if (item < p.work) {
       off[c] = p.mode == kFresh ? (uint32_t)item : jd.qidx[p.qin][item];
       code_planes(p.chunk_base + off[c], E[c], O[c]);
-      alive |= 1u << c;
+      bool seeded = true;
+      if (p.mode == kFresh && jd.seed) {
+        const uint64_t b = p.chunk_base + off[c] - jd.seed_base;
+        seeded = (__ldg(jd.seed + (b >> 5)) >> (b & 31)) & 1u;
+      }
+      if (seeded) alive |= 1u << c;
     }
   }
   const int wpad = jd.wstride;
@@ -1096,6 +1102,21 @@ __global__ void __launch_bounds__(256) count_group_kernel(const JobDesc* __restr
 }
 
 // Ball tables for ks = 1..kMaxKs: entry (v, r) = suffixes within distance r of v.
+__global__ void seed_kernel(const uint64_t* __restrict__ codes0, int W,
+                            const uint64_t* __restrict__ pat, uint64_t npat, uint64_t lo,
+                            uint64_t hi, uint32_t* seed, uint64_t base) {
+  const uint64_t total = (uint64_t)W * npat;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = i / npat;
+    const uint64_t c = __ldg(codes0 + j) ^ __ldg(pat + (i - j * npat));
+    if (c >= lo && c < hi) {
+      const uint64_t b = c - base;
+      atomicOr(seed + (b >> 5), 1u << (unsigned)(b & 31));
+    }
+  }
+}
+
 __global__ void ball_kernel(uint64_t* table, int ks) {
   const int nv = 1 << (2 * ks);
   const int nw = mask_words(ks);
@@ -1283,6 +1304,18 @@ cudaError_t launch_count_group(const JobDesc* d_job, int ks, unsigned long long*
     case 4: count_group_kernel<4><<<grid, block, 0, s>>>(d_job, d_total); break;
     default: return cudaErrorInvalidValue;
   }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_scatter(const uint64_t* codes0, int W, const uint64_t* pat,
+                                uint64_t npat, uint64_t lo, uint64_t hi, uint32_t* seed,
+                                uint64_t base, cudaStream_t s) {
+  if (W <= 0 || npat == 0) return cudaSuccess;
+  const uint64_t total = (uint64_t)W * npat;
+  const uint64_t blocks = (total + 255) / 256;
+  seed_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(codes0, W, pat, npat,
+                                                                         lo, hi, seed, base);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -425,6 +425,16 @@ size_t sort_scratch_bytes(int64_t cap, int sms) {
 
 uint64_t bitmap_scratch_words(uint64_t nwords) { return (nwords + kBmWords - 1) / kBmWords + 1; }
 
+cudaError_t launch_bitmap_count(const uint32_t* bm, uint64_t nwords, unsigned* scratch,
+                                unsigned long long* count, cudaStream_t s) {
+  const uint64_t nblk = (nwords + kBmWords - 1) / kBmWords;
+  if (nblk == 0 || nblk > (uint64_t)INT32_MAX) return cudaErrorInvalidValue;
+  bitmap_count_kernel<<<(unsigned)nblk, kBmThreads, 0, s>>>(bm, nwords, scratch);
+  bitmap_scan_kernel<<<1, kBmThreads, 0, s>>>(scratch, (int)nblk, count);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t base,
                                   uint64_t* out, int64_t cap, unsigned* scratch,
                                   unsigned long long* count, cudaStream_t s) {

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
                 "tune_cache_save", "tune_cache_load", "server_start", "server_stop", "submit",
                 "poll", "shard_range", "strerror", "encode", "decode", "probe_rate", "version",
                 "count_work", "kernel_launches", "load_seqs_var", "fasta_parse",
-                "sort_codes_noalloc"}
+                "sort_codes_noalloc", "seed_count"}
     assert set(names) >= {"motif_" + e for e in expected}, sorted(set(names))
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
@@ -53,7 +53,7 @@ def test_status_codes_match_header(lib):
 
 def test_struct_sizes_match_c_layout():
     # motif_opts: pointer, 7 int32, 2 fn pointers, ctx pointer, 2 uint64.
-    assert ctypes.sizeof(m.motif_opts) == 8 + 8 * 4 + 3 * 8 + 2 * 8
+    assert ctypes.sizeof(m.motif_opts) == 8 + 8 * 4 + 3 * 8 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(m.motif_stats_t) == 3 * 8 + 4 * 8 + 8 + 4 * 4 + 3 * 8
 
 

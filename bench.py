@@ -54,6 +54,9 @@ def parse():
                     default="auto")
     ap.add_argument("--suffix-bases", type=int, default=0)
     ap.add_argument("--cands-per-thread", type=int, default=0)
+    ap.add_argument("--seed", choices=["all", "neighbourhood"], default="all",
+                    help="candidates searched: all indices, or (CAND/BITSLICE) only those within d "
+                         "of a window of the first sequence")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -221,6 +224,8 @@ def run_ours(args):
         kw["kernel"] = m.KERNEL_BITSLICE
     if args.suffix_bases:
         kw["suffix_bases"] = args.suffix_bases
+    if args.seed == "neighbourhood":
+        kw["seed"] = m.SEED_NEIGHBOURHOOD
     if args.cands_per_thread:
         kw["cands_per_thread"] = args.cands_per_thread
     opts = m.torch_opts(stream=stream, **kw)
@@ -371,6 +376,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": workload, "l": l, "d": d, "n": n, "t": t, "seed": seed,
                        "candidates": cands, "kernel": roof["kernel"],
+                       "seed": args.seed,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "weak: one independent instance per GPU" if world > 1 else "1 GPU"},
             "window_compares_per_s": cps,

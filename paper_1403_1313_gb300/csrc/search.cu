@@ -113,9 +113,11 @@ __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
   if (pass_seq == 0) {
     p.mode = jd.tiled ? kTiled : kFresh;
     p.work = p.chunk_units;
-    // A seeded search has already kept only candidates that match the first sequence.
+    // A seeded search has already kept only candidates that match the first sequence; its
+    // fresh pass scans nothing and compacts them (few per warp) into the queue, so the second
+    // sequence runs on full warps.
     p.s0 = jd.seed ? 1 : 0;
-    p.s1 = jd.tiled ? jd.n : (p.s0 + jd.span0 < jd.n ? p.s0 + jd.span0 : jd.n);
+    p.s1 = jd.tiled ? jd.n : jd.seed ? 1 : (jd.span0 < jd.n ? jd.span0 : jd.n);
     p.qin = 0;
     p.qout = 0;
   } else {

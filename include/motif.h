@@ -208,8 +208,9 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
 int motif_count_compares(motif_plan p, uint64_t* out);
 
 /* Runs the counting forms of the search over the plan's range (blocking).  *compares receives
- * the canonical window-compare tally (as motif_count_compares).  *unit_steps receives the same
- * tally for the plan's kernel formulation: for MOTIF_KERNEL_CAND it equals *compares; for
+ * the canonical window-compare tally (as motif_count_compares; for seeded plans too, which skip
+ * the first sequence's compares).  *unit_steps receives the same tally for the plan's kernel
+ * formulation: for MOTIF_KERNEL_CAND and MOTIF_KERNEL_BITSLICE it equals *compares; for
  * MOTIF_KERNEL_GROUP it counts (group, window) prefix compares: per group of 4^k candidates
  * sharing their first l-k bases, sequences in input order, windows left to right up to and
  * including the first window after which every candidate of the group still alive has a

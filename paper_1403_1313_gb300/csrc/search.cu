@@ -414,17 +414,17 @@ __device__ __forceinline__ void or_ball(GroupMask<KS>& matched, const uint64_t* 
                                         int r) {
   constexpr int NW = GroupMask<KS>::NW;
   const uint64_t* row = ball + ((size_t)v * (KS + 1) + r) * NW;
-  if (GLOBAL && NW == 4) {  // 32-byte row: two 128-bit read-only loads
+  if constexpr (GLOBAL && NW == 4) {  // 32-byte row: two 128-bit read-only loads
     const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(row));
     const ulonglong2 y = __ldg(reinterpret_cast<const ulonglong2*>(row) + 1);
     matched.w[0] |= x.x;
     matched.w[1 % NW] |= x.y;
     matched.w[2 % NW] |= y.x;
     matched.w[3 % NW] |= y.y;
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int i = 0; i < NW; ++i) matched.w[i] |= GLOBAL ? __ldg(row + i) : row[i];
+    for (int i = 0; i < NW; ++i) matched.w[i] |= GLOBAL ? __ldg(row + i) : row[i];
+  }
 }
 
 template <int KS>
@@ -659,34 +659,32 @@ __device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsig
 // GROUP, prefix-tiled (k = 4, 256 lanes per CTA).
 //
 // The CTA owns 256 consecutive groups g = T*256 + lane: they share the first l-8 bases (P1)
-// and differ in the last 4 prefix bases (P2 = the lane index); each lane carries the 256
-// suffixes of its group.  Since Ham = Ham(P1) + Ham(P2) + Ham(suffix), per sequence:
+// and differ in the last 4 prefix bases (P2 = the lane index as a 4-base code); each lane
+// carries the 256 suffixes of its group.  Since Ham = Ham(P1) + Ham(P2) + Ham(suffix), per
+// sequence:
 //   1. filter: the CTA computes h1 = Ham(P1, window) once per window; only windows with
 //      h1 <= d can match any of the tile's 65536 candidates.  A window with h1 = d matches
 //      exactly one of them (its own last 8 bases), so its lane sets that bit in a 65536-bit map
-//      of the tile in shared memory.  The other windows are compacted into a list with, per
-//      entry, the 256-bit mask of P2 values within d-h1 of the window (a row of the 4-base ball
-//      table), stored word-major so that each warp reads the word of its 32 lanes;
-//   2. each lane ORs its 256 bits of the map into its matched mask and clears them; then,
-//      32 listed entries at a time, each warp transposes the 32 words of its lanes into one
-//      32-bit mask per lane of the entries it hits (no POPC in this loop);
+//      of the tile in shared memory.  The other windows are compacted into a list of head words
+//      (r1 = d - h1, the window's P2 and suffix codes);
+//   2. after one barrier each lane ORs its 256 bits of the map into its matched mask and clears
+//      them; then, 32 listed entries at a time, each warp loads its 32-bit word of each entry's
+//      4-base ball-table row (the P2 values within min(r1, 4) of the window's) and transposes
+//      the 32 words into one 32-bit mask per lane of the entries it hits (no POPC in this loop);
 //   3. hits: per hit entry the lane computes h2 = Ham(P2, window) and ORs in the suffixes
-//      within d-h1-h2 of the window's last 4 bases.
+//      within r1 - h2 of the window's last 4 bases.
 // A lane with no live candidate left skips its hits; a warp with none skips the scan; the CTA
 // stops when no lane has a live candidate (the skip).  Every sequence is handled inside the
 // tile, so this pass accepts its survivors directly.
 
-// One hit of lane (P2E, P2O) on listed entry k: OR in the suffixes within d-h1-h2 of the
-// window's last 4 bases (h1 and the window's P2 planes are in the entry's head word).
-__device__ __forceinline__ void tiled_hit(GroupMask<4>& matched, uint32_t k, const uint32_t* head,
-                                          const uint16_t* vsuf, uint32_t P2E, uint32_t P2O,
+// One hit of the lane whose P2 code is p2 on a listed entry with head word e: OR in the
+// suffixes within r1 - h2 of the window's last 4 bases.
+__device__ __forceinline__ void tiled_hit(GroupMask<4>& matched, uint32_t e, uint32_t p2,
                                           const uint64_t* ball) {
-  const uint32_t h = head[k];
-  const int r1 = (int)((h >> 16) & 15u);
-  const uint32_t w2E = (h >> 20) & 15u, w2O = (h >> 24) & 15u;
-  int r = r1 - __popc((P2E ^ w2E) | (P2O ^ w2O));
+  const uint32_t x = ((e >> 12) ^ p2) & 0xFFu;  // the window's P2 code against the lane's
+  int r = (int)(e & 15u) - __popc((x | (x >> 1)) & 0x55u);
   r = r < 4 ? r : 4;
-  or_ball<4, true>(matched, ball, vsuf[k], r);
+  or_ball<4, true>(matched, ball, (int)((e >> 4) & 0xFFu), r);
 }
 
 // 32x32 bit-matrix transpose across the warp: on entry lane i holds row i; on exit lane j holds
@@ -705,9 +703,11 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
   return x;
 }
 
+// Head word of a listed window: bits 0-3 r1 = d - h1 (clamped to 15), bits 4-11 the suffix
+// code, bits 12-19 the P2 code.
 __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
-                            unsigned long long tbase, uint32_t* head, uint16_t* vsuf,
-                            uint32_t* maskw, uint32_t* map, unsigned* s_cnt /* [2] */) {
+                            unsigned long long tbase, uint32_t* head, uint32_t* map,
+                            unsigned* s_cnt /* [2] */) {
   constexpr int KS = 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wcap = jd.wstride;
@@ -718,8 +718,7 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
   for (int i = 0; i < 4; ++i) alive.w[i] = 0;
   if (item < p.work) range_mask<KS>(g, jd.lo, jd.hi, alive);
   uint32_t E, O;
-  code_planes(g, E, O);  // prefix planes (l-4 bases); the low 4 bits are P2
-  const uint32_t P2E = E & 15u, P2O = O & 15u;
+  code_planes(g, E, O);  // prefix planes (l-4 bases); the lane's P2 code is tid
   const uint32_t P1E = E >> 4, P1O = O >> 4;  // identical in every lane of the tile
   if (tid == 0) s_cnt[0] = 0;
   int live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
@@ -732,53 +731,26 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     for (int b = 0; b < jd.W; b += 256) {
       const int j = b + tid;
       bool keep = false;
-      uint32_t wE = 0, wO = 0;
-      int r1 = 0;
+      uint32_t e = 0;
       if (j < jd.W) {
         const uint2 w = __ldg(row + j);
-        wE = w.x >> KS;
-        wO = w.y >> KS;
-        const int h1 = __popc(((wE >> 4) ^ P1E) | ((wO >> 4) ^ P1O));
-        r1 = jd.d - h1;
-        if (r1 == 0) {  // one candidate: the window's own last 8 bases
-          const uint32_t v = (uint32_t)__ldg(crow + j) & 0xFFFFu;
-          atomicOr(map + (v >> 5), 1u << (v & 31u));
+        const int r1 = jd.d - __popc(((w.x >> 8) ^ P1E) | ((w.y >> 8) ^ P1O));
+        if (r1 >= 0) {
+          const uint32_t v = (uint32_t)__ldg(crow + j) & 0xFFFFu;  // P2 code << 8 | suffix
+          if (r1 == 0) atomicOr(map + (v >> 5), 1u << (v & 31u));   // one candidate
+          keep = r1 > 0;
+          e = (uint32_t)(r1 < 15 ? r1 : 15) | (v << 4);
         }
-        keep = r1 > 0;
       }
       const unsigned bal = __ballot_sync(kFull, keep);
       unsigned wb = 0;
       if (lane == 0 && bal) wb = atomicAdd(cnt, (unsigned)__popc(bal));
       wb = __shfl_sync(kFull, wb, 0);
-      if (keep)
-        head[wb + __popc(bal & ((1u << lane) - 1u))] =
-            (uint32_t)j | ((uint32_t)(r1 < 15 ? r1 : 15) << 16) | ((wE & 15u) << 20) |
-            ((wO & 15u) << 24);
+      if (keep) head[wb + __popc(bal & ((1u << lane) - 1u))] = e;
     }
     if (tid == 0) s_cnt[(s + 1) & 1] = 0;  // the next sequence's list count
     __syncthreads();
     const int K = (int)*cnt;
-    // One thread per listed window: its suffix code and the ball-table row of P2 values within
-    // min(r1, 4) of its P2, stored word-major.
-    for (int k = tid; k < K; k += blockDim.x) {
-      const uint32_t e = head[k];
-      const uint64_t code = __ldg(crow + (e & 0xFFFFu));
-      const uint32_t r1 = (e >> 16) & 15u;
-      const int v2 = (int)((code >> (2 * KS)) & 0xFFu);  // the window's P2 bases
-      vsuf[k] = (uint16_t)(code & 0xFFu);
-      const uint4* brow = reinterpret_cast<const uint4*>(
-          jd.ball + ((size_t)v2 * (KS + 1) + (r1 < 4u ? r1 : 4u)) * 4);
-      const uint4 lo = __ldg(brow), hi = __ldg(brow + 1);
-      maskw[0 * wcap + k] = lo.x;
-      maskw[1 * wcap + k] = lo.y;
-      maskw[2 * wcap + k] = lo.z;
-      maskw[3 * wcap + k] = lo.w;
-      maskw[4 * wcap + k] = hi.x;
-      maskw[5 * wcap + k] = hi.y;
-      maskw[6 * wcap + k] = hi.z;
-      maskw[7 * wcap + k] = hi.w;
-    }
-    __syncthreads();
     const bool lane_live = any_set<KS>(alive);
     // 2. take this lane's bits of the map (the P2 code of lane tid is tid) and clear them;
     //    then scan 32 listed entries at a time: a warp transpose turns the entries' words for
@@ -795,15 +767,21 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
       own[1] = make_uint4(0u, 0u, 0u, 0u);
     }
     if (__any_sync(kFull, lane_live)) {
-      const uint32_t* mrow = maskw + warp * wcap;
+      const uint32_t* ball32 = reinterpret_cast<const uint32_t*>(jd.ball);
       for (int k = 0; k < K; k += 32) {
-        uint32_t x = k + lane < K ? mrow[k + lane] : 0u;
+        // this warp's word (its 32 lanes) of the ball row (P2_w, min(r1, 4)) of entry k+lane
+        uint32_t x = 0;
+        if (k + lane < K) {
+          const uint32_t e = head[k + lane];
+          const uint32_t r1 = e & 15u;
+          x = __ldg(ball32 + (((e >> 12) & 0xFFu) * (KS + 1) + (r1 < 4u ? r1 : 4u)) * 8u + warp);
+        }
         x = warp_transpose32(x, lane);
         if (!lane_live) x = 0;
         while (x) {
           const int i = __ffs(x) - 1;
           x &= x - 1;
-          tiled_hit(matched, (uint32_t)(k + i), head, vsuf, P2E, P2O, jd.ball);
+          tiled_hit(matched, head[k + i], (uint32_t)tid, jd.ball);
         }
       }
     }
@@ -898,15 +876,10 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
     __syncthreads();
 
     if (KIND == MOTIF_KERNEL_GROUP && P == 4 && p.mode == kTiled) {
-      // CTA-wide tiles of 256 groups.
-      const size_t wc = (size_t)wpad;
-      uint32_t* head = reinterpret_cast<uint32_t*>(smem);
-      uint16_t* vsuf = reinterpret_cast<uint16_t*>(smem + wc * 4);
-      size_t moff = wc * 6;
-      moff += 16 - moff % 16;
-      uint32_t* maskw = reinterpret_cast<uint32_t*>(smem + moff);
-      // The tile map of single-candidate windows starts cleared; every tile leaves it cleared.
-      uint32_t* map = maskw + wc * 8;
+      // CTA-wide tiles of 256 groups: the tile map of single-candidate windows (8 KB; it starts
+      // cleared and every tile leaves it cleared), then the list heads.
+      uint32_t* map = reinterpret_cast<uint32_t*>(smem);
+      uint32_t* head = map + 2048;
       for (int i = tid; i < 2048; i += blockDim.x) map[i] = 0u;
       for (;;) {
         __syncthreads();
@@ -919,7 +892,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
         __syncthreads();
         const unsigned long long b = s_tbase;
         if (b >= p.work) break;
-        group_tiled(jd, st, p, b, head, vsuf, maskw, map, s_tcnt);
+        group_tiled(jd, st, p, b, head, map, s_tcnt);
       }
       continue;
     }
@@ -1181,11 +1154,9 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   size_t b = (size_t)kMaxStageSeqs * wstride * 10;
   b += 16 - b % 16;
   b += (size_t)kHitCap * block * 4;
-  if (p == 4) {  // the prefix-tiled pass: list heads, suffix values, 8 mask words per entry,
-                 // and the 8 KB map of single-candidate windows
-    size_t t = (size_t)wstride * 6;
-    t += 16 - t % 16;
-    t += (size_t)wstride * 32 + 8192;
+  if (p == 4) {  // the prefix-tiled pass: the 8 KB map of single-candidate windows and the
+                 // list heads
+    const size_t t = 8192 + (size_t)wstride * 4;
     if (t > b) b = t;
   }
   return b;

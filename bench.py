@@ -41,6 +41,9 @@ CONFIGS = {  # name: (l, d, n, t, seed)
 }
 POPC_PER_SM_CLK = 16.0  # measured by the K4 probe (motif_probe_rate POPC) on GB300
 LOP3_PER_SM_CLK = 64.0  # measured by the K4 probe (motif_probe_rate LOP3) on GB300
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the tiled pass on the
+# (15,4) n=20 t=600 seed-2 workload (one --set full capture of the current kernel): 295.2 KB + 0 B.
+TILED_L15D4_DRAM_BYTES = 295168
 
 
 def parse():
@@ -298,8 +301,14 @@ def run_ours(args):
     kname = {m.KERNEL_GROUP: "GROUP", m.KERNEL_CAND: "CAND", m.KERNEL_TILED: "TILED",
              m.KERNEL_BITSLICE: "BITSLICE"}.get(st["kernel"], "?")
     achieved = compares / (step_ms / 1e3)
+    # DRAM traffic per launch of the timed kernel, from an ncu capture of the tiled pass on the
+    # default workload (dram__bytes_read.sum + dram__bytes_write.sum of its first step launch);
+    # other kernels and workloads were not captured: null.
+    traffic = (TILED_L15D4_DRAM_BYTES if (kname == "TILED" and workload == "l15d4_n20_t600_seed2"
+                                          and args.seed == "all") else None)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-            "unit": "G window-compares/s (1 POPC each)", "frac": achieved / peak, "traffic": None,
+            "unit": "G window-compares/s (1 POPC each)", "frac": achieved / peak,
+            "traffic": traffic,
             "kernel": "step_kernel<%s>" % kname,
             "peak_basis": "16 POPC/clk/SM (K4 probe) x %d SMs x %.0f MHz (max SM clock)" % (sms, max_mhz),
             "step_kernel_ms": step_ms, "sort_ms": sort_ms,
@@ -376,7 +385,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": workload, "l": l, "d": d, "n": n, "t": t, "seed": seed,
                        "candidates": cands, "kernel": roof["kernel"],
-                       "seed": args.seed,
+                       "candidate_seeding": args.seed,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "weak: one independent instance per GPU" if world > 1 else "1 GPU"},
             "window_compares_per_s": cps,

@@ -1,12 +1,19 @@
 """Multi-worker search: the index-range split of Sec. IV.A across processes.
 
-Each rank searches one contiguous range of the candidate index space (sizes in proportion to
-optional weights, e.g. measured throughput), holding its own copy of the sequences — the paper's
-per-thread first/last l-mer assignment, one process per GPU.  The only exchange is one
-variable-size gather of the accepted codes: counts first, then the codes padded to the largest
-count.  Ranges are contiguous and each rank's codes ascend, so concatenating in rank order gives
-the globally ascending result.  Works over any torch.distributed backend: NCCL with CUDA
-tensors on GPUs, gloo with CPU tensors elsewhere.
+Static split (sharded_search): each rank searches one contiguous range of the candidate index
+space (sizes in proportion to optional weights, e.g. measured throughput), holding its own copy
+of the sequences — the paper's per-thread first/last l-mer assignment, one process per GPU.  The
+only exchange is one variable-size gather of the accepted codes: counts first, then the codes
+padded to the largest count.  Ranges are contiguous and each rank's codes ascend, so
+concatenating in rank order gives the globally ascending result.
+
+Dynamic split (dynamic_sharded_search): the skip makes the work of a range depend on the data,
+so ranks instead claim fixed-size chunks of the index space one at a time from a shared counter
+in the process group's key-value store (an atomic add) until none are left, then gather their
+(chunk, codes) pairs; concatenating the chunks in index order gives the ascending result.
+
+Both work over any torch.distributed backend: NCCL with CUDA tensors on GPUs, gloo with CPU
+tensors elsewhere.
 """
 from __future__ import annotations
 
@@ -61,3 +68,36 @@ def sharded_search(seqs, l: int, d: int, rank: int, world: int, weights=None, se
     if world == 1:
         return local
     return gather_codes(local, group)
+
+
+def dynamic_sharded_search(seqs, l: int, d: int, store, key: str, chunk: int = 1 << 24,
+                           search_fn=None, group=None) -> np.ndarray:
+    """Searches chunks of [0, 4^l) claimed from `store` (a torch.distributed Store shared by the
+    ranks, e.g. dist.distributed_c10d._get_default_store()) under the counter `key` (unique per
+    search), then all-gathers and returns the global ascending result on every rank.
+
+    search_fn(seqs, l, d, lo, hi) -> ascending codes in [lo, hi); default: the CUDA path."""
+    import torch.distributed as dist
+    if chunk < 1:
+        raise ValueError("chunk must be positive")
+    fn = search_fn or _rank_search_gpu
+    space = 4 ** l
+    nchunks = (space + chunk - 1) // chunk
+    mine = []  # (chunk index, codes)
+    while True:
+        i = int(store.add(key, 1)) - 1  # claim the next unclaimed chunk
+        if i >= nchunks:
+            break
+        lo = i * chunk
+        hi = min(space, lo + chunk)
+        mine.append((i, np.asarray(fn(seqs, l, d, lo, hi), dtype=np.uint64)))
+    if not dist.is_initialized() or dist.get_world_size(group) == 1:
+        parts = mine
+    else:
+        everyone = [None] * dist.get_world_size(group)
+        dist.all_gather_object(everyone, mine, group=group)
+        parts = [p for r in everyone for p in r]
+    parts.sort(key=lambda x: x[0])
+    if len(parts) != nchunks or any(i != k for k, (i, _) in enumerate(parts)):
+        raise RuntimeError("chunks were lost or claimed twice")
+    return np.concatenate([c for _, c in parts]) if parts else np.zeros(0, np.uint64)

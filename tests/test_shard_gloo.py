@@ -71,3 +71,47 @@ def test_missing_rank_fails_fast(tmp_path):
         p.join(timeout=120)
     assert all(not p.is_alive() for p in ctx.processes)
     assert (tmp_path / "rank0.err").exists() or not (tmp_path / "rank0.npy").exists()
+
+
+def _dyn_worker(rank, world, port, l, d, seed, chunk, out_dir):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1403_1313_gb300 import fmgen
+    from paper_1403_1313_gb300.shard import dynamic_sharded_search
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=30))
+    store = dist.distributed_c10d._get_default_store()
+    job = fmgen.fm_job(6, 90, l, d, seed)
+    claimed = []
+
+    def counting(seqs, l_, d_, lo, hi):
+        claimed.append((lo, hi))
+        return _oracle_range(seqs, l_, d_, lo, hi)
+
+    res = dynamic_sharded_search(job.rows(), l, d, store, "motif-chunks-%d" % seed, chunk=chunk,
+                                 search_fn=counting)
+    np.save(os.path.join(out_dir, "dyn%d.npy" % rank), res)
+    np.save(os.path.join(out_dir, "claims%d.npy" % rank), np.array(claimed, dtype=np.int64).reshape(-1, 2))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("chunk", [1000, 4 ** 8 // 3, 4 ** 8])
+def test_dynamic_chunks_gather_equals_single(tmp_path, chunk):
+    from oracle import oracle
+    from paper_1403_1313_gb300 import fmgen
+    l, d, seed = 8, 2, 91
+    mp.start_processes(_dyn_worker, args=(2, _free_port(), l, d, seed, chunk, str(tmp_path)),
+                       nprocs=2, join=True, start_method="spawn")
+    job = fmgen.fm_job(6, 90, l, d, seed)
+    ref, _ = oracle.search(job.rows(), l, d)
+    for r in range(2):
+        assert np.array_equal(np.load(tmp_path / ("dyn%d.npy" % r)), ref)
+    # Every chunk was claimed exactly once, by one rank or the other.
+    claims = np.concatenate([np.load(tmp_path / ("claims%d.npy" % r)) for r in range(2)])
+    claims = claims[np.argsort(claims[:, 0])]
+    nchunks = (4 ** l + chunk - 1) // chunk
+    assert len(claims) == nchunks
+    assert claims[0, 0] == 0 and claims[-1, 1] == 4 ** l
+    assert np.all(claims[1:, 0] == claims[:-1, 1])

@@ -118,6 +118,16 @@ def test_sharded_search_single_process_matches():
     assert np.array_equal(np.concatenate(parts), ref)
 
 
+def test_dynamic_sharded_search_single_process_matches():
+    import torch.distributed as dist
+    from paper_1403_1313_gb300.shard import dynamic_sharded_search
+    job = fmgen.fm_job(6, 90, 9, 2, 13)
+    ref, _ = oracle.search(job.rows(), 9, 2)
+    store = dist.HashStore()
+    got = dynamic_sharded_search(job.seqs, 9, 2, store, "chunks", chunk=30000)
+    assert np.array_equal(got, ref)
+
+
 def test_device_path_capacity_overflow_reports_count():
     torch = pytest.importorskip("torch")
     rows = ["ACGTACGTAC", "TTGACCATGA"]

@@ -13,6 +13,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -43,13 +44,19 @@ struct Job {
   int64_t out_cap = 0;
   void* sort = nullptr;
   size_t sort_bytes = 0;
+  // Bitmap output for dense results (the plan's choice): one bit per code of
+  // [bm_base, bm_base + 32*bm_words), compacted in order when the job finishes.
+  uint32_t* bitmap = nullptr;
+  unsigned* bm_scratch = nullptr;
+  uint64_t bm_base = 0, bm_words = 0;
   int64_t footprint = 0;
   const uint64_t* ball = nullptr;     // Hamming-ball table for pv on the server's device
   cudaEvent_t ready = nullptr;        // recorded after the window copies (submit stream)
   double t_submit = 0, t_admit = 0, t_done = 0, gpu_ms = 0;
   int status = MOTIF_OK;
   bool done = false;
-  std::vector<uint64_t> result;
+  std::unique_ptr<uint64_t[]> result;  // the accepted codes (uninitialised until written)
+  int64_t result_size = 0;
 };
 
 struct Server {
@@ -113,8 +120,12 @@ void release_run_buffers(Server* S, Job* j) {
   }
   sfree(S, j->out);
   sfree(S, j->sort);
+  sfree(S, j->bitmap);
+  sfree(S, j->bm_scratch);
   j->out = nullptr;
   j->sort = nullptr;
+  j->bitmap = nullptr;
+  j->bm_scratch = nullptr;
 }
 
 // Everything, including the job's private window copies.
@@ -127,10 +138,14 @@ void release_buffers(Server* S, Job* j) {
   }
   sfree(S, j->out);
   sfree(S, j->sort);
+  sfree(S, j->bitmap);
+  sfree(S, j->bm_scratch);
   sfree(S, j->planes);
   sfree(S, j->codes);
   j->out = nullptr;
   j->sort = nullptr;
+  j->bitmap = nullptr;
+  j->bm_scratch = nullptr;
   j->planes = nullptr;
   j->codes = nullptr;
   if (j->ready) cudaEventDestroy(j->ready);
@@ -138,7 +153,8 @@ void release_buffers(Server* S, Job* j) {
 }
 
 int64_t footprint_of(const Job* j) {
-  return (int64_t)(2 * j->qcap * (4 + 8 * (uint64_t)j->words) + 8 * (uint64_t)(1 << 16));
+  return (int64_t)(2 * j->qcap * (4 + 8 * (uint64_t)j->words) + 8 * (uint64_t)(1 << 16) +
+                   4 * j->bm_words);
 }
 
 bool allocate_job(Server* S, Job* j) {
@@ -149,7 +165,14 @@ bool allocate_job(Server* S, Job* j) {
   }
   j->out_cap = 1 << 16;
   j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
-  return j->out != nullptr;
+  if (!j->out) return false;
+  if (j->bm_words) {  // cleared on the scheduler's stream, before the job's first step
+    j->bitmap = (uint32_t*)salloc(S, j->bm_words * 4);
+    j->bm_scratch = (unsigned*)salloc(S, bitmap_scratch_words(j->bm_words) * 4);
+    if (!j->bitmap || !j->bm_scratch) return false;
+    if (cudaMemsetAsync(j->bitmap, 0, j->bm_words * 4, S->stream) != cudaSuccess) return false;
+  }
+  return true;
 }
 
 void fill_job_desc(const Job* j, JobDesc* jd) {
@@ -166,6 +189,8 @@ void fill_job_desc(const Job* j, JobDesc* jd) {
   jd->qcap = j->qcap;
   jd->out = j->out; jd->out_cap = (uint64_t)j->out_cap;
   jd->ball = j->ball;
+  jd->bitmap = j->bitmap;
+  jd->bm_base = j->bm_base;
 }
 
 int max_active(const Server* S) { return S->o.max_active > 0 ? S->o.max_active : 64; }
@@ -237,8 +262,41 @@ int upload_table(Server* S, const std::vector<int>& old_slot) {
   return status_from_cuda(e);
 }
 
+// Copies a finished job's `count` ascending codes from its output buffer to the host.
+int copy_result(Server* S, Job* j, unsigned long long fc) {
+  j->result.reset(fc ? new (std::nothrow) uint64_t[fc] : nullptr);
+  j->result_size = (int64_t)fc;
+  if (fc && !j->result) return MOTIF_ERR_OOM;
+  cudaError_t e = cudaSuccess;
+  if (fc) e = cudaMemcpyAsync(j->result.get(), j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  return status_from_cuda(e);
+}
+
+// Bitmap output: compacts the job's bitmap in order into its output buffer (grown, and the
+// compaction repeated, when the codes do not fit) and copies the codes to the host.
+int finish_bitmap_job(Server* S, Job* j, int slot) {
+  unsigned long long fc = 0;
+  for (;;) {
+    cudaError_t e = launch_bitmap_compact(j->bitmap, j->bm_words, j->bm_base, j->out, j->out_cap,
+                                          j->bm_scratch, &S->d_states[slot].out_count, S->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&fc, &S->d_states[slot].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
+                          S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    if (fc <= (unsigned long long)j->out_cap) break;
+    sfree(S, j->out);
+    j->out_cap = (int64_t)fc;
+    j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
+    if (!j->out) return MOTIF_ERR_OOM;
+  }
+  return copy_result(S, j, fc);
+}
+
 // Sorts a finished job's codes and copies them to the host.
 int finish_job(Server* S, Job* j, int slot, unsigned long long found) {
+  if (j->bitmap) return finish_bitmap_job(S, j, slot);
   if (found > 4096) {
     const size_t need = sort_scratch_bytes(j->out_cap, S->sms);
     j->sort = salloc(S, need);
@@ -252,12 +310,8 @@ int finish_job(Server* S, Job* j, int slot, unsigned long long found) {
     e = cudaMemcpyAsync(&fc, &S->d_states[slot].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
                         S->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-  if (e == cudaSuccess) {
-    j->result.resize(fc);
-    if (fc) e = cudaMemcpyAsync(j->result.data(), j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-  }
-  return status_from_cuda(e);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  return copy_result(S, j, fc);
 }
 
 void scheduler(Server* S) {
@@ -513,6 +567,10 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   j->words = mask_words(j->pv);
   j->tiled = j->pv == 4 && j->l >= 8 && j->W <= 65535 && j->unit_lo % 256 == 0 &&
              (j->chunk_units % 256 == 0 || units <= j->chunk_units);
+  if (p->bitmap) {  // the plan's output choice: dense results go to a bitmap over the range
+    j->bm_base = p->bm_base;
+    j->bm_words = p->bm_words;
+  }
   j->rest = (uint64_t)256 * S->sms;
   if (j->nchunks > 0) {
     std::lock_guard<std::mutex> sg(S->submit_mu);
@@ -578,19 +636,19 @@ extern "C" int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity,
   if (!j->done && timeout_ms > 0)
     S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return j->done; });
   if (!j->done) return MOTIF_PENDING;
-  *out_count = (int64_t)j->result.size();
+  *out_count = j->result_size;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->candidates = j->hi - j->lo;
-    stats->survivors = j->result.size();
+    stats->survivors = (uint64_t)j->result_size;
     stats->queue_ms = j->t_admit > 0 ? j->t_admit - j->t_submit : 0;
     stats->total_ms = j->t_done - j->t_submit;
     stats->search_ms = j->gpu_ms;
     stats->device_bytes = j->footprint;
     stats->kernel = j->kind;
   }
-  if (j->status == MOTIF_OK && (int64_t)j->result.size() > capacity) return MOTIF_ERR_CAPACITY;
-  if (!j->result.empty()) memcpy(out_codes, j->result.data(), j->result.size() * 8);
+  if (j->status == MOTIF_OK && j->result_size > capacity) return MOTIF_ERR_CAPACITY;
+  if (j->result_size > 0) memcpy(out_codes, j->result.get(), (size_t)j->result_size * 8);
   const int st = j->status;
   S->jobs.erase(it);
   delete j;  // the scheduler released its device buffers when it retired the job

@@ -96,3 +96,34 @@ def test_served_matches_blocking_search_larger(server):
         m.motif_load_seqs(plan, job.seqs)
         assert np.array_equal(got, m.motif_search(plan))
         m.motif_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_dense_jobs_take_the_bitmap(server, use_graph):
+    """Jobs whose codes the plan collects in a bitmap (forced, or chosen for dense results) are
+    served through an ordered compaction, mixed with list jobs; one job has 262144 codes, more
+    than a served job's first output buffer holds."""
+    m.motif_server_start(max_active=8, step_tiles=64, use_graph=use_graph)
+    rng = random.Random(17)
+    cases = []
+    for j in range(8):
+        l = rng.randint(6, 10)
+        d = rng.randint(2, 4)
+        t = rng.randint(30, 120)
+        rows = ["".join(rng.choice("ACGT") for _ in range(t)) for _ in range(rng.randint(2, 5))]
+        cases.append((rows, l, d, [m.OUTPUT_AUTO, m.OUTPUT_LIST, m.OUTPUT_BITMAP][j % 3]))
+    every = ["".join(rng.choice("ACGT") for _ in range(20)) for _ in range(3)]
+    cases.append((every, 9, 9, m.OUTPUT_AUTO))  # all 4^9 codes survive: dense, AUTO -> bitmap
+    ids = []
+    for rows, l, d, output in cases:
+        o = m.motif_opts_default()
+        o.output = output
+        plan = m.motif_plan_create(len(rows), len(rows[0]), l, d, o)
+        m.motif_load_seqs(plan, rows)
+        ids.append(m.motif_submit(plan))
+        m.motif_plan_destroy(plan)
+    for jid, (rows, l, d, _) in zip(ids, cases):
+        got = m.motif_poll(jid, timeout_ms=120000, capacity=1 << 19)
+        assert got is not None
+        ref, _ = oracle.search(rows, l, d, threads=8)
+        assert np.array_equal(got[0], ref)

@@ -319,9 +319,9 @@ def run_ours(args):
                      "roofline_cand for the per-compare kernel" % kname) if kname != "CAND" else ""}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (POPC_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
-    def per_candidate_leg(kernel, label):
+    def per_candidate_leg(kernel, label, cpt):
         """A per-candidate kernel on a sub-range of the same workload (full per-compare work)."""
-        o = m.torch_opts(stream=stream, kernel=kernel, cands_per_thread=2,
+        o = m.torch_opts(stream=stream, kernel=kernel, cands_per_thread=cpt,
                          range_lo=0, range_hi=min(cands, args.cand_subrange))
         pc = m.motif_plan_create(n, t, l, d, o)
         with torch.cuda.stream(stream):
@@ -340,18 +340,20 @@ def run_ours(args):
         c_ach = c_cmp / (c_ms / 1e3)
         return {"bound": "alu", "achieved": c_ach / 1e9, "peak": peak / 1e9,
                 "unit": "G window-compares/s (1 POPC each)", "frac": c_ach / peak,
-                "kernel": "step_kernel<%s,2>" % label, "step_kernel_ms": c_ms,
+                "kernel": "step_kernel<%s,%d>" % (label, cpt), "step_kernel_ms": c_ms,
                 "sample": "candidates [0, %d) of %s" % (min(cands, args.cand_subrange), workload)}
 
     roof_cand = roof_bitslice = None
     if kname != "CAND" and args.cand_subrange > 0:
-        roof_cand = per_candidate_leg(m.KERNEL_CAND, "CAND")
+        roof_cand = per_candidate_leg(m.KERNEL_CAND, "CAND", 2)
     if args.cand_subrange > 0 and d <= 7:
         # The bit-sliced compare against both rooflines: the POPC one above and its own, the
         # LOP3 pipe at the counter's LOP3 per 32 compares (11 per three base positions, 5 per
         # position left over; positions past 16 are counted as a second group).
-        roof_bitslice = per_candidate_leg(m.KERNEL_BITSLICE, "BITSLICE")
-        lop3 = sum(11 * (k // 3) + 5 * (k % 3) for k in (max(0, l - 16), min(l, 16)))
+        roof_bitslice = per_candidate_leg(m.KERNEL_BITSLICE, "BITSLICE", 1)
+        def counter_lop3(k):  # 15 per 7 positions, 11 per 3, 5 per 1
+            return 15 * (k // 7) + 11 * ((k % 7) // 3) + 5 * ((k % 7) % 3)
+        lop3 = sum(counter_lop3(k) for k in (max(0, l - 16), min(l, 16)))
         peak_lop3 = LOP3_PER_SM_CLK * sms * max_mhz * 1e6 * 32.0 / lop3
         roof_bitslice.update({
             "peak_lop3": peak_lop3 / 1e9, "frac_lop3": roof_bitslice["achieved"] * 1e9 / peak_lop3,

@@ -205,8 +205,8 @@ int plan_configure(motif_plan_s* p) {
   if (o.kernel == MOTIF_KERNEL_BITSLICE)  // the bit-sliced counter holds distances up to 7
     kind = p->d <= 7 ? MOTIF_KERNEL_BITSLICE : MOTIF_KERNEL_CAND;
   int pv;
-  if (cand_like(kind)) {
-    pv = o.cands_per_thread > 0 ? o.cands_per_thread : 2;
+  if (cand_like(kind)) {  // BITSLICE holds more state per candidate: one per lane by default
+    pv = o.cands_per_thread > 0 ? o.cands_per_thread : (kind == MOTIF_KERNEL_BITSLICE ? 1 : 2);
     if (pv != 1 && pv != 2 && pv != 4) return MOTIF_ERR_ARG;
   } else {
     pv = o.suffix_bases > 0 ? o.suffix_bases : 4;

@@ -191,10 +191,10 @@ __device__ __forceinline__ unsigned scan_cand(const uint4* __restrict__ w4, int 
 // base b of the candidate: bit j of word (i, b) is set when window j's base at position i is not
 // b.  The words of four neighbouring blocks sit side by side, so one 128-bit shared load gives
 // a lane the mismatch bits of its candidate's base against 128 windows.  They are added into
-// 3-bit saturating counters held as bit planes (c0, c1, c2 and a sticky overflow c3), three
-// positions at a time: a full adder turns three words into a sum and a carry (2 LOP3), which
-// are added to the counter (9 LOP3) -- no POPC.  Window j is within distance d when its counter
-// is at most d (d <= 7).
+// 3-bit saturating counters held as bit planes (c0, c1, c2 and a sticky overflow c3), seven
+// positions at a time: four full adders (8 LOP3) reduce seven words to a 3-bit number, which
+// one ripple adds to the counter (7 LOP3); leftover positions go three (11 LOP3) or one (5 LOP3)
+// at a time -- no POPC.  Window j is within distance d when its counter is at most d (d <= 7).
 
 // Staged words of one sequence: word (i, b, blk) at ((4 i + b) * nblkp + blk); nblkp, the block
 // count rounded up to a multiple of 4, groups the blocks in fours.  One warp per block.
@@ -235,6 +235,22 @@ struct SliceCount {
     c1 ^= cy;
     c3 |= v;
   }
+  // + x1+...+x7: four full adders reduce the seven words to a 3-bit number (y0 + 2 y1 + 4 y2),
+  // added with one ripple.
+  __device__ __forceinline__ void add7(uint32_t x1, uint32_t x2, uint32_t x3, uint32_t x4,
+                                       uint32_t x5, uint32_t x6, uint32_t x7) {
+    const uint32_t s1 = x1 ^ x2 ^ x3, k1 = (x1 & x2) | (x1 & x3) | (x2 & x3);
+    const uint32_t s2 = x4 ^ x5 ^ x6, k2 = (x4 & x5) | (x4 & x6) | (x5 & x6);
+    const uint32_t y0 = s1 ^ s2 ^ x7, k3 = (s1 & s2) | (s1 & x7) | (s2 & x7);
+    const uint32_t y1 = k1 ^ k2 ^ k3, y2 = (k1 & k2) | (k1 & k3) | (k2 & k3);
+    const uint32_t r0 = c0 & y0;
+    c0 ^= y0;
+    const uint32_t r1 = (c1 & y1) | (c1 & r0) | (y1 & r0);
+    c1 ^= y1 ^ r0;
+    const uint32_t r2 = (c2 & y2) | (c2 & r1) | (y2 & r1);
+    c2 ^= y2 ^ r1;
+    c3 |= r2;
+  }
   // Windows whose count is at most d (D0..D2: the bits of d as all-ones / all-zero masks).
   __device__ __forceinline__ uint32_t within(uint32_t D0, uint32_t D1, uint32_t D2) const {
     const uint32_t gt = (c2 & ~D2) | (~(c2 ^ D2) & ((c1 & ~D1) | (~(c1 ^ D1) & (c0 & ~D0))));
@@ -249,6 +265,18 @@ __device__ __forceinline__ void bitslice_quad(const uint32_t* __restrict__ m, in
                                               SliceCount& b, SliceCount& c, SliceCount& e) {
   const int step = 4 * nblkp;  // words between positions
   int i = 0;
+  for (; i + 7 <= cnt; i += 7) {
+    uint4 x[7];
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+      x[u] = *reinterpret_cast<const uint4*>(m + u * step + ((bits >> (30 - 2 * u)) & 3u) * nblkp);
+    bits <<= 14;
+    m += 7 * step;
+    a.add7(x[0].x, x[1].x, x[2].x, x[3].x, x[4].x, x[5].x, x[6].x);
+    b.add7(x[0].y, x[1].y, x[2].y, x[3].y, x[4].y, x[5].y, x[6].y);
+    c.add7(x[0].z, x[1].z, x[2].z, x[3].z, x[4].z, x[5].z, x[6].z);
+    e.add7(x[0].w, x[1].w, x[2].w, x[3].w, x[4].w, x[5].w, x[6].w);
+  }
   for (; i + 3 <= cnt; i += 3) {
     const uint4 x1 = *reinterpret_cast<const uint4*>(m + (bits >> 30) * nblkp);
     const uint4 x2 = *reinterpret_cast<const uint4*>(m + step + ((bits >> 28) & 3u) * nblkp);

@@ -193,11 +193,13 @@ int motif_fasta_parse(const char* text, int64_t text_len, char* seq_buf, int64_t
  * MOTIF_ERR_CAPACITY, MOTIF_ERR_OOM, MOTIF_ERR_CUDA, MOTIF_ERR_TIMEOUT. */
 int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* out_count);
 
-/* Asynchronous search on the plan's stream with device-resident output: the search kernel
- * appends accepted codes into d_out_codes (capacity entries), the sort/dedup kernels order
- * them in place, and *d_out_count (one int64 in device memory) receives the number of
- * accepted codes.  If that number exceeds capacity, only the count is meaningful (retry with
- * more room); -1 means an invalid character was loaded.  No host synchronisation. */
+/* Asynchronous search on the plan's stream with device-resident output: with LIST output the
+ * search kernel appends accepted codes into d_out_codes (capacity entries) and the sort/dedup
+ * kernels order them in place; with BITMAP output the ordered compaction writes them there.
+ * *d_out_count (one int64 in device memory) receives the number of accepted codes.  If that
+ * number exceeds capacity, only the count is meaningful for LIST output (retry with more
+ * room); BITMAP output still holds the first `capacity` codes in ascending order.  -1 means
+ * an invalid character was loaded.  No host synchronisation. */
 int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
                         int64_t* d_out_count);
 

@@ -96,9 +96,9 @@ cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l
                         uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s);
 // Fills the Hamming-ball table for ks (ball_table_words(ks) words).
 cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s);
-// Step kernel variants: kind = MOTIF_KERNEL_CAND with p = candidates per lane (1, 2, 4), or
-// MOTIF_KERNEL_GROUP with p = ks (1..4).  Every job of one launch must use the same variant.
-bool step_variant_ok(int kind, int p);
+// Step kernel variants: kind = MOTIF_KERNEL_CAND or MOTIF_KERNEL_BITSLICE with p = candidates
+// per lane (1, 2, 4), or MOTIF_KERNEL_GROUP with p = ks (1..4).  Every job of one launch must use
+// the same variant.
 size_t step_smem_bytes(int kind, int p, int wstride, int block);
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem);
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem);

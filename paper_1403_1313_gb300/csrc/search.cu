@@ -1172,8 +1172,6 @@ const void* step_function(int kind, int p) {
 
 }  // namespace
 
-bool step_variant_ok(int kind, int p) { return step_function(kind, p) != nullptr; }
-
 size_t step_smem_bytes(int kind, int p, int wstride, int block) {
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
   if (kind == MOTIF_KERNEL_BITSLICE)  // 4 words per base position (l <= 32) per 32 windows,

@@ -437,6 +437,11 @@ def run_batch(args):
         batch_res = m.motif_batch_search(plans, use_graph=True)
         assert all(np.array_equal(a, b) for a, b in zip(plain_res, batch_res)), "batch != plain"
         reps = max(1, args.steps)
+        for _ in range(max(3, args.warmup)):  # untimed: graphs, sort scratch, host buffer pools
+            for pl in plans:
+                m.motif_search(pl)
+            m.motif_batch_search(plans, use_graph=True)
+            m.motif_batch_search(plans, use_graph=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):

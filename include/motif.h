@@ -115,8 +115,8 @@ typedef struct {
   double search_ms;              /* device time of the search kernel, last search */
   double sort_ms;                /* device time of sort/dedup, last search */
   double total_ms;               /* host wall time of the last motif_search or served job */
-  double queue_ms;               /* served job: submit -> admission; batched job: device-to-host
-                                    result copy time of its batch */
+  double queue_ms;               /* served job: submit -> admission; batched job: the part of its
+                                    batch's device-to-host result copies that outlasts the sorts */
   int64_t device_bytes;          /* device memory held by the plan */
   int32_t smem_bytes;            /* dynamic shared memory per CTA of the search kernel */
   int32_t kernel;                /* kernel that ran (motif_kernel) */
@@ -235,11 +235,14 @@ uint64_t motif_kernel_launches(void);
 /* ---- batching: many uneven jobs in one persistent launch -------------------------------- */
 
 /* Runs `njobs` loaded plans together in one persistent launch of the batched kernel, which
- * pulls candidate tiles of every job from one device tile queue; use_graph != 0 captures the
- * launch sequence in a CUDA graph and replays it.  Per job j the results follow motif_search's
- * rules on out_codes[j] / capacities[j] / out_counts[j]; statuses[j] receives job j's status.
- * Returns MOTIF_OK when every job succeeded, else the first failing status.  Blocking; the
- * work runs on the first plan's stream. */
+ * pulls candidate tiles of every job from one device tile queue; use_graph != 0 runs the step
+ * loop as one CUDA graph (a conditional while node), instantiated once per batch shape and kept
+ * for later batches.  Per job j the results follow motif_search's rules on out_codes[j] /
+ * capacities[j] / out_counts[j]; statuses[j] receives job j's status.  Returns MOTIF_OK when
+ * every job succeeded, else the first failing status.  Blocking: it waits for each plan's
+ * stream, then works on the library's per-device batch streams, where job j's result copy
+ * overlaps the sorts of the jobs after it (out_codes in pinned host memory let the copies run
+ * asynchronously at full link rate; pageable buffers are correct but serialise them). */
 int motif_batch_search(int32_t njobs, const motif_plan* plans, uint64_t* const* out_codes,
                        const int64_t* capacities, int64_t* out_counts, int32_t* statuses,
                        int32_t use_graph);

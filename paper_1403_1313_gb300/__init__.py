@@ -279,10 +279,28 @@ def read_fasta(path: str) -> list:
         return motif_fasta_parse(f.read())
 
 
+_PINNED = None  # torch, once it is known to have a CUDA device; False where it has none
+
+
 def _host_codes(capacity: int) -> np.ndarray:
-    # Uninitialised memory: the library writes every returned element.  (Zero-filled arrays come
-    # from calloc'd pages whose first touch by the device copy is far slower on some hosts.)
-    return np.empty(max(int(capacity), 1), dtype=np.uint64)
+    """An uninitialised host buffer for `capacity` codes (the library writes every returned one).
+
+    Taken from torch's caching pinned-host allocator: the device copy runs at full link rate,
+    and a block freed by an earlier result comes back with its pages already mapped.  A freshly
+    allocated pageable array instead pays the operating system's first touch of every page inside
+    the copy (about 8 ms for 195 MB on a GB300 host, against 1 ms into mapped memory).  The
+    returned array keeps its block alive; dropping the array gives the block back."""
+    global _PINNED
+    n = max(int(capacity), 1)
+    if _PINNED is None:
+        try:
+            import torch
+            _PINNED = torch if torch.cuda.is_available() else False
+        except ImportError:
+            _PINNED = False
+    if _PINNED:
+        return _PINNED.empty(n, dtype=_PINNED.int64, pin_memory=True).numpy().view(np.uint64)
+    return np.empty(n, dtype=np.uint64)
 
 
 def _trimmed(out: np.ndarray, count: int) -> np.ndarray:
@@ -360,7 +378,11 @@ def motif_batch_search(plans, use_graph: bool = True, capacity: int | None = Non
     k = len(plans)
     caps = [capacity if capacity is not None else p.capacity_hint for p in plans]
     while True:
-        outs = [_host_codes(c) for c in caps]
+        # one host block for every job's buffer (one allocation, not k); each result is a view
+        sizes = [max(int(c), 1) for c in caps]
+        block = _host_codes(sum(sizes))
+        ends = np.cumsum(sizes)
+        outs = [block[e - n:e] for e, n in zip(ends, sizes)]
         handles = (ctypes.c_void_p * k)(*[p.handle for p in plans])
         ptrs = (ctypes.POINTER(ctypes.c_uint64) * k)(
             *[o.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) for o in outs])

@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "plan.h"
@@ -22,31 +23,59 @@ using namespace motif;
 
 namespace motif_batch {
 
-// Per-device stream and job-table buffers reused across batch calls.
+// Per-device streams, job-table buffers and step graphs reused across batch calls.
 struct BatchCtx {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // steps, then each job's sort / compaction
+  cudaStream_t count_stream = nullptr; // each job's final count, once its sort is done
+  cudaStream_t copy_stream = nullptr;  // each job's codes to the host, once its count is known
   JobDesc* d_jobs = nullptr;
   JobState* d_states = nullptr;
   StepCtl* d_ctl = nullptr;
+  unsigned long long* h_counts = nullptr;  // pinned: the final count of each job
+  std::vector<cudaEvent_t> sorted, counted;
+  // Instantiated step graphs by (kind, p, jobs, grid, block, smem, max_steps); they name d_jobs,
+  // d_states and d_ctl, so they are dropped when those are re-allocated.
+  std::map<std::tuple<int, int, int, int, int, size_t, int>, cudaGraphExec_t> graphs;
   int cap = 0;
 };
 std::mutex g_mu;
 BatchCtx g_ctx[64];
 
+void drop_graphs(BatchCtx& c) {
+  for (auto& kv : c.graphs) cudaGraphExecDestroy(kv.second);
+  c.graphs.clear();
+}
+
 int ensure_ctx(int dev, int njobs, BatchCtx** out) {
   if (dev < 0 || dev >= 64) return MOTIF_ERR_ARG;
   BatchCtx& c = g_ctx[dev];
-  if (!c.stream && cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess)
-    return MOTIF_ERR_CUDA;
+  for (cudaStream_t* s : {&c.stream, &c.count_stream, &c.copy_stream})
+    if (!*s && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess)
+      return MOTIF_ERR_CUDA;
   if (njobs > c.cap) {
+    drop_graphs(c);
     if (c.d_jobs) cudaFree(c.d_jobs);
     if (c.d_states) cudaFree(c.d_states);
+    if (c.h_counts) cudaFreeHost(c.h_counts);
+    c.d_jobs = nullptr;
+    c.d_states = nullptr;
+    c.h_counts = nullptr;
+    c.cap = 0;
     if (!c.d_ctl && cudaMalloc(&c.d_ctl, sizeof(StepCtl)) != cudaSuccess) return MOTIF_ERR_OOM;
     const int cap = std::max(njobs, 64);
     if (cudaMalloc(&c.d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
-        cudaMalloc(&c.d_states, sizeof(JobState) * cap) != cudaSuccess) {
-      c.cap = 0;
+        cudaMalloc(&c.d_states, sizeof(JobState) * cap) != cudaSuccess ||
+        cudaHostAlloc((void**)&c.h_counts, sizeof(unsigned long long) * cap, 0) != cudaSuccess)
       return MOTIF_ERR_OOM;
+    while ((int)c.sorted.size() < cap) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return MOTIF_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return MOTIF_ERR_CUDA;
+      }
+      c.sorted.push_back(a);
+      c.counted.push_back(b);
     }
     c.cap = cap;
   }
@@ -63,15 +92,26 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
                      max_steps, true, timeout_ms, s, nullptr);
   }
   // One graph launch: init, then a while loop of step launches that ends when every job is
-  // done (or after max_steps steps).
+  // done (or after max_steps steps).  The instantiated graph is kept for later batches of the
+  // same shape.
+  const auto key = std::make_tuple(kind, pv, njobs, grid, block, smem, max_steps);
   cudaGraphExec_t exec = nullptr;
-  cudaError_t e = build_step_graph(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block,
-                                   smem, (unsigned)max_steps, 1, &exec);
+  cudaError_t e = cudaSuccess;
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    exec = it->second;
+  } else {
+    e = build_step_graph(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem,
+                         (unsigned)max_steps, 1, &exec);
+    if (e == cudaSuccess) {
+      if (c->graphs.size() >= 16) drop_graphs(*c);
+      c->graphs[key] = exec;
+    }
+  }
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   StepCtl ctl{};
   if (e == cudaSuccess) e = cudaMemcpy(&ctl, c->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
-  if (exec) cudaGraphExecDestroy(exec);
   if (e != cudaSuccess) return status_from_cuda(e);
   note_launches(1 + (int)ctl.steps);
   (void)timeout_ms;
@@ -155,21 +195,28 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     if (e != cudaSuccess) return status_from_cuda(e);
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     for (auto& x : ev) cudaEventCreate(&x);
+    // Leaves nothing in flight (copies into the caller's buffers included) before returning.
+    auto fail = [&](int status) {
+      cudaStreamSynchronize(c->stream);
+      cudaStreamSynchronize(c->count_stream);
+      cudaStreamSynchronize(c->copy_stream);
+      for (auto& x : ev) cudaEventDestroy(x);
+      return status;
+    };
     cudaEventRecord(ev[0], c->stream);
     rc = run_table(c, kind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
                    timeout);
     cudaEventRecord(ev[1], c->stream);
-    if (rc) {
-      for (auto& x : ev) cudaEventDestroy(x);
-      return rc;
-    }
+    if (rc) return fail(rc);
     std::vector<JobState> st(ids.size());
     e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return status_from_cuda(e);
-    // Sort/dedup every job's codes in its own buffer (counts live in the batch state array),
-    // read all final counts with one copy, then copy the codes with one final wait.
+    if (e != cudaSuccess) return fail(status_from_cuda(e));
+    // Sort/dedup (or compact) every job's codes in its own buffer on the batch stream.  Once a
+    // job's sort is done its final count goes to pinned memory on the count stream; the host
+    // waits for one count at a time and queues that job's codes to the host on the copy stream,
+    // so the copies overlap the sorts of the jobs after them.
     std::vector<char> sorted(ids.size(), 0);
     for (size_t i = 0; i < ids.size(); ++i) {
       const int j = ids[i];
@@ -182,36 +229,38 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       if (p->bitmap) {  // compact the job's bitmap into its buffer (count into its state)
         e = launch_bitmap_compact(p->d_bitmap, p->bm_words, p->bm_base, p->d_out, p->out_cap,
                                   p->d_bm_scratch, &c->d_states[i].out_count, c->stream);
-        if (e != cudaSuccess) return status_from_cuda(e);
-        sorted[i] = 1;
-        continue;
-      }
-      if (found > 4096) {
-        const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
-        if (need > p->sort_bytes) {
-          plan_free(p, p->d_sort, p->sort_bytes);
-          p->d_sort = plan_alloc(p, need);
-          cudaStreamSynchronize(p->stream);  // the scratch is used on the batch stream
-          p->sort_bytes = p->d_sort ? need : 0;
-          p->gs_scratch = nullptr;  // any cached sort graph names the old scratch
-          if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
+      } else {
+        if (found > 4096) {
+          const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
+          if (need > p->sort_bytes) {
+            plan_free(p, p->d_sort, p->sort_bytes);
+            p->d_sort = plan_alloc(p, need);
+            cudaStreamSynchronize(p->stream);  // the scratch is used on the batch stream
+            p->sort_bytes = p->d_sort ? need : 0;
+            p->gs_scratch = nullptr;  // any cached sort graph names the old scratch
+            if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
+          }
         }
+        e = launch_sort_unique(p->d_out, &c->d_states[i].out_count, p->out_cap, 2 * p->l,
+                               p->d_sort, p->sms, (long long)found, c->stream);
       }
-      e = launch_sort_unique(p->d_out, &c->d_states[i].out_count, p->out_cap, 2 * p->l,
-                             p->d_sort, p->sms, (long long)found, c->stream);
-      if (e != cudaSuccess) return status_from_cuda(e);
+      if (e == cudaSuccess) e = cudaEventRecord(c->sorted[i], c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->count_stream, c->sorted[i], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&c->h_counts[i], &c->d_states[i].out_count, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, c->count_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(c->counted[i], c->count_stream);
+      if (e != cudaSuccess) return fail(status_from_cuda(e));
       sorted[i] = 1;
     }
     cudaEventRecord(ev[2], c->stream);  // sorts done
-    e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
-                        cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return status_from_cuda(e);
     for (size_t i = 0; i < ids.size(); ++i) {
       if (!sorted[i]) continue;
       const int j = ids[i];
       motif_plan_s* p = plans[j];
-      const unsigned long long fc = st[i].out_count;
+      e = cudaEventSynchronize(c->counted[i]);
+      if (e != cudaSuccess) return fail(status_from_cuda(e));
+      const unsigned long long fc = c->h_counts[i];
       if (fc > (unsigned long long)p->out_cap) {  // a bitmap job outgrew the plan's buffer
         redo[j] = 1;
         continue;
@@ -224,18 +273,23 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         continue;
       }
       if (fc) {
-        e = cudaMemcpyAsync(out_codes[j], p->d_out, fc * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return status_from_cuda(e);
+        e = cudaStreamWaitEvent(c->copy_stream, c->sorted[i], 0);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(out_codes[j], p->d_out, fc * 8, cudaMemcpyDeviceToHost,
+                              c->copy_stream);
+        if (e != cudaSuccess) return fail(status_from_cuda(e));
       }
     }
-    cudaEventRecord(ev[3], c->stream);
-    e = cudaStreamSynchronize(c->stream);
+    cudaEventRecord(ev[3], c->copy_stream);
+    e = cudaStreamSynchronize(c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     float steps_ms = 0, sort_ms = 0, copy_ms = 0;
     cudaEventElapsedTime(&steps_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&sort_ms, ev[1], ev[2]);
-    cudaEventElapsedTime(&copy_ms, ev[2], ev[3]);
+    cudaEventElapsedTime(&copy_ms, ev[2], ev[3]);  // the copy time not hidden under the sorts
+    copy_ms = std::max(copy_ms, 0.0f);
+    if (e != cudaSuccess) return fail(status_from_cuda(e));
     for (auto& x : ev) cudaEventDestroy(x);
-    if (e != cudaSuccess) return status_from_cuda(e);
     for (size_t i = 0; i < ids.size(); ++i) {  // the group's device times, shared by its jobs
       plans[ids[i]]->stats.search_ms = steps_ms;
       plans[ids[i]]->stats.sort_ms = sort_ms;

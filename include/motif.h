@@ -105,7 +105,10 @@ typedef struct {
   uint64_t range_lo;        /* candidate sub-range [range_lo, range_hi) of [0, 4^l), the */
   uint64_t range_hi;        /* per-worker index range of Sec. IV.A; range_hi == 0: all */
   int32_t seed;             /* motif_seed */
-  int32_t reserved;         /* 0 */
+  int32_t seq_block;        /* prefix-tiled pass with BITMAP output: sequences per work item
+                               (a tile and a block of sequences, ANDed into the bitmap); 0 =
+                               chosen so the items fill the GPU, -1 = one item walks a tile
+                               through every sequence */
 } motif_opts;
 
 typedef struct {

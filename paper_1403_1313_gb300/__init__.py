@@ -61,7 +61,7 @@ class motif_opts(ctypes.Structure):
         ("timeout_ms", ctypes.c_int32), ("output", ctypes.c_int32), ("alloc", _ALLOC_FN),
         ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p), ("range_lo", ctypes.c_uint64),
-        ("range_hi", ctypes.c_uint64), ("seed", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("range_hi", ctypes.c_uint64), ("seed", ctypes.c_int32), ("seq_block", ctypes.c_int32),
     ]
 
 

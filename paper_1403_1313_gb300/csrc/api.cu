@@ -121,6 +121,7 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
   jd->cpt = cand_like(p->kind) ? p->p : 1;
   jd->span0 = p->span0;
   jd->tiled = p->tiled ? 1 : 0;
+  jd->seq_block = p->tiled ? p->seq_block : 0;
   jd->lo = p->lo; jd->hi = p->hi;
   jd->unit_lo = p->unit_lo; jd->unit_hi = p->unit_hi;
   jd->chunk_units = p->chunk_units; jd->nchunks = p->nchunks;
@@ -237,30 +238,6 @@ int plan_configure(motif_plan_s* p) {
   p->want_qcap = chunk;
   p->want_qwords = words;
   invalidate_graphs(p);
-  // The prefix-tiled first pass (GROUP, k = 4): 256 lanes per CTA whose groups share all but
-  // their last 4 prefix bases, so tiles must start on multiples of 256 groups.
-  // AUTO leaves it out where a tile would walk through most sequences (q > 0.52) and there are
-  // too few tiles (< 64) to fill the GPU: the per-group passes run those faster alone.  A batch
-  // runs its jobs side by side, so there every eligible AUTO job stays tiled.
-  const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
-  const bool tiled_ok = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 &&
-                        p->l >= 8 && p->W <= 65535 && unit_lo % 256 == 0 &&
-                        (chunk % 256 == 0 || units <= chunk);
-  const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
-  p->tiled = tiled_ok && !(o.kernel == MOTIF_KERNEL_AUTO && few_long_tiles);
-  p->tiled_in_batch = tiled_ok;
-  // Candidate seeding by the first sequence's d-neighbourhoods (per-candidate kernels only).
-  if (o.seed < MOTIF_SEED_ALL || o.seed > MOTIF_SEED_NEIGHBOURHOOD || o.reserved != 0)
-    return MOTIF_ERR_ARG;
-  p->seeded = o.seed == MOTIF_SEED_NEIGHBOURHOOD;
-  if (p->seeded) {
-    if (!cand_like(kind)) return MOTIF_ERR_ARG;
-    p->npat = pattern_count(p->l, p->d);
-    p->seed_base = p->lo & ~63ull;
-    const uint64_t bits = ((p->hi + 63) & ~63ull) - p->seed_base;
-    if (p->npat > (1ull << 24) || bits > (1ull << 36)) return MOTIF_ERR_ARG;
-    p->seed_words = std::max<uint64_t>(bits / 32, 1);
-  }
   // Output: a bitmap over the range (rounded out to whole 256-code groups) where it holds at
   // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size.
   const uint64_t bm_base = p->lo & ~255ull;
@@ -275,6 +252,46 @@ int plan_configure(motif_plan_s* p) {
   p->bitmap = bitmap && p->hi > p->lo;
   p->bm_base = bm_base;
   p->bm_words = p->bitmap ? bm_bits / 32 : 0;
+  // The prefix-tiled first pass (GROUP, k = 4): 256 lanes per CTA whose groups share all but
+  // their last 4 prefix bases, so tiles must start on multiples of 256 groups.
+  const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
+  const bool tiled_ok = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 &&
+                        p->l >= 8 && p->W <= 65535 && unit_lo % 256 == 0 &&
+                        (chunk % 256 == 0 || units <= chunk);
+  // With bitmap output the expected survivors (at least 1/2048 of the range: 32 per tile of
+  // 65536 codes) keep every tile alive to the last sequence, so the skip saves nothing there and
+  // a tile splits into (tile, sequence block) items at no extra work; the blocks are sized so
+  // that the items cover the grid four times over.
+  if (o.seq_block < -1) return MOTIF_ERR_ARG;
+  p->seq_block = 0;
+  if (tiled_ok && p->bitmap && o.seq_block != -1) {
+    if (o.seq_block > 0) {
+      p->seq_block = std::min(o.seq_block, p->n);
+    } else {
+      const uint64_t tiles = (std::min(units, chunk) + 255) / 256;
+      const uint64_t blocks =
+          std::min<uint64_t>(p->n, (4ull * per_sm * p->sms + tiles - 1) / tiles);
+      if (blocks > 1) p->seq_block = (int)((p->n + blocks - 1) / blocks);
+    }
+  }
+  // AUTO leaves the tiled pass out where a tile would walk through most sequences (q > 0.52)
+  // and there are too few tiles (< 64) to fill the GPU, unless the tiles split into sequence
+  // blocks: the per-group passes run those faster alone.  A batch runs its jobs side by side, so
+  // there every eligible AUTO job stays tiled.
+  const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
+  p->tiled = tiled_ok && !(o.kernel == MOTIF_KERNEL_AUTO && few_long_tiles && p->seq_block == 0);
+  p->tiled_in_batch = tiled_ok;
+  // Candidate seeding by the first sequence's d-neighbourhoods (per-candidate kernels only).
+  if (o.seed < MOTIF_SEED_ALL || o.seed > MOTIF_SEED_NEIGHBOURHOOD) return MOTIF_ERR_ARG;
+  p->seeded = o.seed == MOTIF_SEED_NEIGHBOURHOOD;
+  if (p->seeded) {
+    if (!cand_like(kind)) return MOTIF_ERR_ARG;
+    p->npat = pattern_count(p->l, p->d);
+    p->seed_base = p->lo & ~63ull;
+    const uint64_t bits = ((p->hi + 63) & ~63ull) - p->seed_base;
+    if (p->npat > (1ull << 24) || bits > (1ull << 36)) return MOTIF_ERR_ARG;
+    p->seed_words = std::max<uint64_t>(bits / 32, 1);
+  }
   p->kind = kind;
   p->p = pv;
   p->span0 = span0;
@@ -474,8 +491,9 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
     cudaError_t e = cudaMemsetAsync(p->d_state, 0, sizeof(JobState), p->stream);
     return status_from_cuda(e);
   }
-  if (p->bitmap) {
-    cudaError_t e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, p->stream);
+  if (p->bitmap) {  // all ones where (tile, sequence block) items AND their survivors in
+    const int fill = p->tiled && p->seq_block > 0 ? 0xFF : 0;
+    cudaError_t e = cudaMemsetAsync(p->d_bitmap, fill, p->bm_words * 4, p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
   }
   if (p->seeded) {

@@ -33,6 +33,7 @@ struct BatchCtx {
   StepCtl* d_ctl = nullptr;
   unsigned long long* h_counts = nullptr;  // pinned: the final count of each job
   std::vector<cudaEvent_t> sorted, counted;
+  cudaEvent_t copies_done = nullptr;
   // Instantiated step graphs by (kind, p, jobs, grid, block, smem, max_steps); they name d_jobs,
   // d_states and d_ctl, so they are dropped when those are re-allocated.
   std::map<std::tuple<int, int, int, int, int, size_t, int>, cudaGraphExec_t> graphs;
@@ -52,6 +53,9 @@ int ensure_ctx(int dev, int njobs, BatchCtx** out) {
   for (cudaStream_t* s : {&c.stream, &c.count_stream, &c.copy_stream})
     if (!*s && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess)
       return MOTIF_ERR_CUDA;
+  if (!c.copies_done &&
+      cudaEventCreateWithFlags(&c.copies_done, cudaEventDisableTiming) != cudaSuccess)
+    return MOTIF_ERR_CUDA;
   if (njobs > c.cap) {
     drop_graphs(c);
     if (c.d_jobs) cudaFree(c.d_jobs);
@@ -173,6 +177,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       motif_plan_s* p = plans[ids[i]];
       fill_desc(p, &descs[i], p->d_out, (uint64_t)p->out_cap);
       descs[i].tiled = p->tiled_in_batch ? 1 : 0;
+      descs[i].seq_block = p->tiled_in_batch ? p->seq_block : 0;
       smem = std::max(smem, p->smem);
       max_steps = std::max<int>(max_steps, (int)std::min<uint64_t>(p->nchunks * p->n + 2, 1 << 30));
       block = p->block;
@@ -185,7 +190,9 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
                                     cudaMemcpyHostToDevice, c->stream);
     for (size_t i = 0; i < ids.size() && e == cudaSuccess; ++i) {
       motif_plan_s* p = plans[ids[i]];
-      if (p->bitmap) e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, c->stream);
+      if (p->bitmap)  // all ones where (tile, sequence block) items AND their survivors in
+        e = cudaMemsetAsync(p->d_bitmap, descs[i].seq_block > 0 ? 0xFF : 0, p->bm_words * 4,
+                            c->stream);
       if (e == cudaSuccess && p->seeded && prepare_seed(p, c->stream) != MOTIF_OK)
         e = cudaErrorUnknown;
     }
@@ -217,8 +224,18 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     // job's sort is done its final count goes to pinned memory on the count stream; the host
     // waits for one count at a time and queues that job's codes to the host on the copy stream,
     // so the copies overlap the sorts of the jobs after them.
-    std::vector<char> sorted(ids.size(), 0);
+    // Largest results first, so that the longest copies start earliest: a list job's size is its
+    // count before dedup, a bitmap job's (counted only when compacted) the caller's capacity.
+    std::vector<size_t> order(ids.size());
+    std::vector<unsigned long long> size_of(ids.size());
     for (size_t i = 0; i < ids.size(); ++i) {
+      order[i] = i;
+      size_of[i] = plans[ids[i]]->bitmap ? (unsigned long long)capacities[ids[i]] : st[i].out_count;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return size_of[a] > size_of[b]; });
+    std::vector<char> sorted(ids.size(), 0);
+    for (const size_t i : order) {
       const int j = ids[i];
       motif_plan_s* p = plans[j];
       const unsigned long long found = st[i].out_count;
@@ -254,7 +271,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       sorted[i] = 1;
     }
     cudaEventRecord(ev[2], c->stream);  // sorts done
-    for (size_t i = 0; i < ids.size(); ++i) {
+    for (const size_t i : order) {
       if (!sorted[i]) continue;
       const int j = ids[i];
       motif_plan_s* p = plans[j];
@@ -280,14 +297,15 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         if (e != cudaSuccess) return fail(status_from_cuda(e));
       }
     }
-    cudaEventRecord(ev[3], c->copy_stream);
-    e = cudaStreamSynchronize(c->copy_stream);
+    // The copies' end, timed on the batch stream (events of two streams do not share a timeline).
+    e = cudaEventRecord(c->copies_done, c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->copies_done, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     float steps_ms = 0, sort_ms = 0, copy_ms = 0;
     cudaEventElapsedTime(&steps_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&sort_ms, ev[1], ev[2]);
     cudaEventElapsedTime(&copy_ms, ev[2], ev[3]);  // the copy time not hidden under the sorts
-    copy_ms = std::max(copy_ms, 0.0f);
     if (e != cudaSuccess) return fail(status_from_cuda(e));
     for (auto& x : ev) cudaEventDestroy(x);
     for (size_t i = 0; i < ids.size(); ++i) {  // the group's device times, shared by its jobs

@@ -30,6 +30,10 @@ struct JobDesc {
   int32_t cpt;               // CAND: candidates per lane in a fresh pass (1, 2 or 4)
   int32_t span0;             // sequences a fresh pass scans before the first compaction
   int32_t tiled;             // GROUP k=4: fresh passes use the prefix-tiled form (see search.cu)
+  int32_t seq_block;         // tiled with bitmap output: 0 = a work item is one tile walked
+                             //   through every sequence (with the skip); k > 0 = a work item is
+                             //   (tile, block of k sequences), whose survivors are ANDed into
+                             //   the bitmap (which then starts as all ones)
   uint64_t lo, hi;           // candidate range [lo, hi)
   uint64_t unit_lo, unit_hi; // work units of the range: candidates (CAND) or groups (GROUP)
   uint64_t chunk_units;      // units per chunk (bounds the queues)

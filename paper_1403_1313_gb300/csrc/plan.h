@@ -23,6 +23,7 @@ struct motif_plan_s {
   int span0 = 2;
   bool tiled = false;        // GROUP k=4 fresh passes use the prefix-tiled form
   bool tiled_in_batch = false;  // ... and inside a batch (where few, long tiles run side by side)
+  int seq_block = 0;         // tiled with bitmap output: sequences per (tile, block) item; 0 = none
   int block = 256, grid = 0;
   size_t smem = 0;
   uint64_t lo = 0, hi = 0;   // candidate range

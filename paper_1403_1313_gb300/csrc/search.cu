@@ -113,6 +113,11 @@ __device__ Pass make_pass(const JobDesc& jd, const JobState* st) {
   if (pass_seq == 0) {
     p.mode = jd.tiled ? kTiled : kFresh;
     p.work = p.chunk_units;
+    if (jd.tiled && jd.seq_block > 0) {  // (sequence block, tile) items, 256 groups each
+      const unsigned long long tiles = (p.chunk_units + 255) / 256;
+      const unsigned long long blocks = (jd.n + jd.seq_block - 1) / jd.seq_block;
+      p.work = tiles * blocks * 256;
+    }
     // A seeded search has already kept only candidates that match the first sequence; its
     // fresh pass scans nothing and compacts them (few per warp) into the queue, so the second
     // sequence runs on full warps.
@@ -733,24 +738,36 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 
 // Head word of a listed window: bits 0-3 r1 = d - h1 (clamped to 15), bits 4-11 the suffix
 // code, bits 12-19 the P2 code.
+// ANDs the survivors of one (tile, sequence block) item into the bitmap, one 64-bit word per
+// 64 codes; a group's words all lie inside the bitmap, which covers whole groups of the range.
+__device__ __forceinline__ void group_and_bitmap(const JobDesc& jd, uint64_t g,
+                                                 const GroupMask<4>& alive) {
+  unsigned long long* w =
+      reinterpret_cast<unsigned long long*>(jd.bitmap) + (((g << 8) - jd.bm_base) >> 6);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (~alive.w[i]) atomicAnd(w + i, (unsigned long long)alive.w[i]);
+}
+
 __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
-                            unsigned long long tbase, uint32_t* head, uint32_t* map,
-                            unsigned* s_cnt /* [2] */) {
+                            unsigned long long tbase, int s_begin, int s_end, uint32_t* head,
+                            uint32_t* map, unsigned* s_cnt /* [2] */) {
   constexpr int KS = 4;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wcap = jd.wstride;
   const unsigned long long item = tbase + tid;
+  const bool in_chunk = item < p.chunk_units;
   const uint64_t g = p.chunk_base + item;
   GroupMask<KS> alive;
 #pragma unroll
   for (int i = 0; i < 4; ++i) alive.w[i] = 0;
-  if (item < p.work) range_mask<KS>(g, jd.lo, jd.hi, alive);
+  if (in_chunk) range_mask<KS>(g, jd.lo, jd.hi, alive);
   uint32_t E, O;
   code_planes(g, E, O);  // prefix planes (l-4 bases); the lane's P2 code is tid
   const uint32_t P1E = E >> 4, P1O = O >> 4;  // identical in every lane of the tile
-  if (tid == 0) s_cnt[0] = 0;
+  if (tid == 0) s_cnt[s_begin & 1] = 0;
   int live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
-  for (int s = 0; s < jd.n && live; ++s) {
+  for (int s = s_begin; s < s_end && live; ++s) {
     unsigned* cnt = s_cnt + (s & 1);
     // 1. filter the windows by the shared prefix (the list count was zeroed before the
     //    barrier that precedes this phase)
@@ -818,7 +835,11 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     // One barrier: the list may be rebuilt, and the tile stops once no lane has a live candidate.
     live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
   }
-  group_output<KS>(jd, st, g, alive);
+  if (jd.seq_block > 0) {
+    if (in_chunk) group_and_bitmap(jd, g, alive);
+  } else {
+    group_output<KS>(jd, st, g, alive);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -920,7 +941,14 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
         __syncthreads();
         const unsigned long long b = s_tbase;
         if (b >= p.work) break;
-        group_tiled(jd, st, p, b, head, map, s_tcnt);
+        if (jd.seq_block > 0) {  // item b / 256 = (sequence block, tile), blocks outermost
+          const unsigned long long tiles = (p.chunk_units + 255) / 256, u = b >> 8;
+          const int s_begin = (int)(u / tiles) * jd.seq_block;
+          const int s_end = s_begin + jd.seq_block < jd.n ? s_begin + jd.seq_block : jd.n;
+          group_tiled(jd, st, p, (u % tiles) << 8, s_begin, s_end, head, map, s_tcnt);
+        } else {
+          group_tiled(jd, st, p, b, 0, jd.n, head, map, s_tcnt);
+        }
       }
       continue;
     }

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <condition_variable>
 #include <deque>
+#include <iterator>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -31,6 +32,7 @@ struct Job {
   int n = 0, t = 0, l = 0, d = 0, W = 0, wstride = 0;
   int kind = MOTIF_KERNEL_GROUP, pv = 4, span0 = 2, sms = 0;
   bool tiled = false;
+  int seq_block = 0;  // tiled with bitmap output: sequences per (tile, block) item
   size_t smem = 0;
   uint64_t lo = 0, hi = 0, unit_lo = 0, unit_hi = 0, chunk_units = 0, nchunks = 0, rest = 0;
   uint2* planes = nullptr;
@@ -55,7 +57,8 @@ struct Job {
   double t_submit = 0, t_admit = 0, t_done = 0, gpu_ms = 0;
   int status = MOTIF_OK;
   bool done = false;
-  std::unique_ptr<uint64_t[]> result;  // the accepted codes (uninitialised until written)
+  uint64_t* result = nullptr;  // the accepted codes, in a pinned block of the server's pool
+  size_t result_cap = 0;       // codes the block holds
   int64_t result_size = 0;
 };
 
@@ -82,7 +85,51 @@ struct Server {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // Pinned host blocks for results, by capacity in codes (guarded by mu): a result is copied at
+  // full link rate into pages that are already mapped, and motif_poll gives its block back.
+  std::multimap<size_t, uint64_t*> host_free;
+  size_t host_free_bytes = 0;
 };
+
+constexpr size_t kHostPoolBytes = (size_t)2 << 30;  // pinned result blocks kept for reuse
+
+// A pinned block for at least `n` codes: a pooled one at most twice that size, else a new one of
+// the next power of two.  Null when pinned memory is exhausted.
+uint64_t* host_take(Server* S, size_t n, size_t* cap) {
+  auto it = S->host_free.lower_bound(n);
+  if (it != S->host_free.end() && it->first <= 2 * n) {
+    uint64_t* b = it->second;
+    *cap = it->first;
+    S->host_free_bytes -= it->first * 8;
+    S->host_free.erase(it);
+    return b;
+  }
+  size_t c = 1024;
+  while (c < n) c <<= 1;
+  uint64_t* b = nullptr;
+  if (cudaHostAlloc((void**)&b, c * 8, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *cap = c;
+  return b;
+}
+
+void host_give(Server* S, uint64_t* b, size_t cap) {
+  if (!b) return;
+  while (S->host_free_bytes + cap * 8 > kHostPoolBytes && !S->host_free.empty()) {
+    auto big = std::prev(S->host_free.end());  // evict the largest pooled blocks first
+    S->host_free_bytes -= big->first * 8;
+    cudaFreeHost(big->second);
+    S->host_free.erase(big);
+  }
+  if (cap * 8 > kHostPoolBytes) {
+    cudaFreeHost(b);
+    return;
+  }
+  S->host_free.emplace(cap, b);
+  S->host_free_bytes += cap * 8;
+}
 
 std::mutex g_life;  // guards g_srv creation / destruction
 Server* g_srv = nullptr;
@@ -170,7 +217,10 @@ bool allocate_job(Server* S, Job* j) {
     j->bitmap = (uint32_t*)salloc(S, j->bm_words * 4);
     j->bm_scratch = (unsigned*)salloc(S, bitmap_scratch_words(j->bm_words) * 4);
     if (!j->bitmap || !j->bm_scratch) return false;
-    if (cudaMemsetAsync(j->bitmap, 0, j->bm_words * 4, S->stream) != cudaSuccess) return false;
+    // all ones where (tile, sequence block) items AND their survivors in
+    if (cudaMemsetAsync(j->bitmap, j->seq_block > 0 ? 0xFF : 0, j->bm_words * 4, S->stream) !=
+        cudaSuccess)
+      return false;
   }
   return true;
 }
@@ -182,6 +232,7 @@ void fill_job_desc(const Job* j, JobDesc* jd) {
   jd->planes = j->planes; jd->codes = j->codes;
   jd->kind = j->kind; jd->ks = j->pv; jd->cpt = 1; jd->span0 = j->span0;
   jd->tiled = j->tiled ? 1 : 0;
+  jd->seq_block = j->seq_block;
   jd->lo = j->lo; jd->hi = j->hi; jd->unit_lo = j->unit_lo; jd->unit_hi = j->unit_hi;
   jd->chunk_units = j->chunk_units; jd->nchunks = j->nchunks; jd->rest_threshold = j->rest;
   jd->qidx[0] = j->qidx[0]; jd->qidx[1] = j->qidx[1];
@@ -262,13 +313,15 @@ int upload_table(Server* S, const std::vector<int>& old_slot) {
   return status_from_cuda(e);
 }
 
-// Copies a finished job's `count` ascending codes from its output buffer to the host.
+// Copies a finished job's `count` ascending codes from its output buffer to a pinned host block.
 int copy_result(Server* S, Job* j, unsigned long long fc) {
-  j->result.reset(fc ? new (std::nothrow) uint64_t[fc] : nullptr);
   j->result_size = (int64_t)fc;
-  if (fc && !j->result) return MOTIF_ERR_OOM;
+  if (fc) {
+    j->result = host_take(S, fc, &j->result_cap);
+    if (!j->result) return MOTIF_ERR_OOM;
+  }
   cudaError_t e = cudaSuccess;
-  if (fc) e = cudaMemcpyAsync(j->result.get(), j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream);
+  if (fc) e = cudaMemcpyAsync(j->result, j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
   return status_from_cuda(e);
 }
@@ -506,8 +559,11 @@ extern "C" int motif_server_stop(void) {
   cudaStreamSynchronize(S->stream);
   for (auto& kv : S->jobs) {
     release_buffers(S, kv.second);
+    if (kv.second->result) cudaFreeHost(kv.second->result);
     delete kv.second;
   }
+  for (auto& kv : S->host_free) cudaFreeHost(kv.second);
+  S->host_free.clear();
   cudaStreamSynchronize(S->stream);
   if (S->exec) cudaGraphExecDestroy(S->exec);
   if (S->graph) cudaGraphDestroy(S->graph);
@@ -570,6 +626,7 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   if (p->bitmap) {  // the plan's output choice: dense results go to a bitmap over the range
     j->bm_base = p->bm_base;
     j->bm_words = p->bm_words;
+    j->seq_block = j->tiled && p->tiled_in_batch ? p->seq_block : 0;
   }
   j->rest = (uint64_t)256 * S->sms;
   if (j->nchunks > 0) {
@@ -648,8 +705,9 @@ extern "C" int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity,
     stats->kernel = j->kind;
   }
   if (j->status == MOTIF_OK && j->result_size > capacity) return MOTIF_ERR_CAPACITY;
-  if (j->result_size > 0) memcpy(out_codes, j->result.get(), (size_t)j->result_size * 8);
+  if (j->result_size > 0) memcpy(out_codes, j->result, (size_t)j->result_size * 8);
   const int st = j->status;
+  host_give(S, j->result, j->result_cap);
   S->jobs.erase(it);
   delete j;  // the scheduler released its device buffers when it retired the job
   return st;

@@ -133,7 +133,7 @@ def test_full_size_sampled_l15d4():
 def test_seed_argument_rules():
     rows = _rows(random.Random(3), 2, 30)
     for kw in (dict(kernel=m.KERNEL_GROUP), dict(kernel=m.KERNEL_TILED), dict(kernel=m.KERNEL_AUTO),
-               dict(kernel=m.KERNEL_CAND, reserved=1)):
+               dict(kernel=m.KERNEL_CAND, seq_block=-2)):
         with pytest.raises(m.MotifError) as e:
             _plan(rows, 8, 2, **kw)
         assert e.value.status == m.ERR_ARG

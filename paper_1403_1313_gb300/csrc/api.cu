@@ -281,6 +281,15 @@ int plan_configure(motif_plan_s* p) {
   const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
   p->tiled = tiled_ok && !(o.kernel == MOTIF_KERNEL_AUTO && few_long_tiles && p->seq_block == 0);
   p->tiled_in_batch = tiled_ok;
+  // A split search runs on the step kernel variant that has the split; its occupancy decides the
+  // grid.
+  p->lkind = launch_kind(kind, pv, p->tiled && p->seq_block > 0);
+  if (p->lkind != kind) {
+    if (step_kernel_attrs(p->lkind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
+    int ps = step_max_ctas_per_sm(p->lkind, pv, block, smem);
+    if (ps <= 0) return MOTIF_ERR_ARG;
+    per_sm = o.ctas_per_sm > 0 ? std::min(ps, o.ctas_per_sm) : ps;
+  }
   // Candidate seeding by the first sequence's d-neighbourhoods (per-candidate kernels only).
   if (o.seed < MOTIF_SEED_ALL || o.seed > MOTIF_SEED_NEIGHBOURHOOD) return MOTIF_ERR_ARG;
   p->seeded = o.seed == MOTIF_SEED_NEIGHBOURHOOD;
@@ -523,12 +532,12 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   if (no_graph) {
     cudaError_t e = launch_init_steps(p->d_state, 1, p->d_ctl, 0, 0, 0, p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
-    return run_steps(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
+    return run_steps(p->lkind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
                      max_steps_of(p), poll, timeout_of(p), p->stream, nullptr);
   }
   // One graph launch runs every step: init, then a while loop whose body is the step kernel.
   if (!p->g_steps) {
-    cudaError_t e = build_step_graph(p->kind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid,
+    cudaError_t e = build_step_graph(p->lkind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid,
                                      p->block, p->smem, (unsigned)max_steps_of(p), 0, &p->g_steps);
     if (e != cudaSuccess) {
       p->g_steps = nullptr;

@@ -183,8 +183,12 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       block = p->block;
       timeout = std::max(timeout, p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 60000);
     }
-    if (step_kernel_attrs(kind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
-    grid = step_max_ctas_per_sm(kind, pv, block, smem) * plans[ids[0]]->sms;
+    // The split-capable kernel variant only where a job of the table is split.
+    bool split = false;
+    for (const JobDesc& jd : descs) split = split || jd.seq_block > 0;
+    const int lkind = launch_kind(kind, pv, split);
+    if (step_kernel_attrs(lkind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
+    grid = step_max_ctas_per_sm(lkind, pv, block, smem) * plans[ids[0]]->sms;
     if (grid <= 0) return MOTIF_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(c->d_jobs, descs.data(), sizeof(JobDesc) * ids.size(),
                                     cudaMemcpyHostToDevice, c->stream);
@@ -211,7 +215,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       return status;
     };
     cudaEventRecord(ev[0], c->stream);
-    rc = run_table(c, kind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
+    rc = run_table(c, lkind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
                    timeout);
     cudaEventRecord(ev[1], c->stream);
     if (rc) return fail(rc);

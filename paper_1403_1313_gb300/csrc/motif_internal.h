@@ -101,8 +101,17 @@ cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l
 // Fills the Hamming-ball table for ks (ball_table_words(ks) words).
 cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s);
 // Step kernel variants: kind = MOTIF_KERNEL_CAND or MOTIF_KERNEL_BITSLICE with p = candidates
-// per lane (1, 2, 4), or MOTIF_KERNEL_GROUP with p = ks (1..4).  Every job of one launch must use
-// the same variant.
+// per lane (1, 2, 4), MOTIF_KERNEL_GROUP with p = ks (1..4), or kKindTiledSplit with p = 4.
+// Every job of one launch must use the same variant.
+//
+// kKindTiledSplit is a launch-only kind: the GROUP k = 4 kernel that also runs tiled passes split
+// into (tile, sequence block) items (JobDesc::seq_block > 0).  Its jobs' descriptors keep
+// MOTIF_KERNEL_GROUP; launches that hold no split job use the plain GROUP kernel, whose
+// whole-tile loop compiles without the split's code.
+constexpr int kKindTiledSplit = MOTIF_KERNEL_BITSLICE + 1;
+inline int launch_kind(int kind, int p, bool split) {
+  return split && kind == MOTIF_KERNEL_GROUP && p == 4 ? kKindTiledSplit : kind;
+}
 size_t step_smem_bytes(int kind, int p, int wstride, int block);
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem);
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem);

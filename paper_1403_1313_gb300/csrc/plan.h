@@ -24,6 +24,7 @@ struct motif_plan_s {
   bool tiled = false;        // GROUP k=4 fresh passes use the prefix-tiled form
   bool tiled_in_batch = false;  // ... and inside a batch (where few, long tiles run side by side)
   int seq_block = 0;         // tiled with bitmap output: sequences per (tile, block) item; 0 = none
+  int lkind = 0;             // step kernel variant of a single search (launch_kind of kind, p)
   int block = 256, grid = 0;
   size_t smem = 0;
   uint64_t lo = 0, hi = 0;   // candidate range

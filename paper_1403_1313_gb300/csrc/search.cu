@@ -749,6 +749,10 @@ __device__ __forceinline__ void group_and_bitmap(const JobDesc& jd, uint64_t g,
     if (~alive.w[i]) atomicAnd(w + i, (unsigned long long)alive.w[i]);
 }
 
+// One item of the tiled pass.  SPLIT = false: the tile at group offset tbase, walked through
+// every sequence, its survivors appended (or ORed into the bitmap).  SPLIT = true: the tile and
+// the sequences [s_begin, s_end), its survivors ANDed into the bitmap.
+template <bool SPLIT>
 __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
                             unsigned long long tbase, int s_begin, int s_end, uint32_t* head,
                             uint32_t* map, unsigned* s_cnt /* [2] */) {
@@ -756,7 +760,9 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wcap = jd.wstride;
   const unsigned long long item = tbase + tid;
-  const bool in_chunk = item < p.chunk_units;
+  // (a whole-tile pass has work == chunk_units; the loop bound of a whole tile is read from the
+  // descriptor each time, which keeps one register free in the hot loop)
+  const bool in_chunk = item < (SPLIT ? p.chunk_units : p.work);
   const uint64_t g = p.chunk_base + item;
   GroupMask<KS> alive;
 #pragma unroll
@@ -765,9 +771,9 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
   uint32_t E, O;
   code_planes(g, E, O);  // prefix planes (l-4 bases); the lane's P2 code is tid
   const uint32_t P1E = E >> 4, P1O = O >> 4;  // identical in every lane of the tile
-  if (tid == 0) s_cnt[s_begin & 1] = 0;
+  if (tid == 0) s_cnt[SPLIT ? (s_begin & 1) : 0] = 0;
   int live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
-  for (int s = s_begin; s < s_end && live; ++s) {
+  for (int s = SPLIT ? s_begin : 0; s < (SPLIT ? s_end : jd.n) && live; ++s) {
     unsigned* cnt = s_cnt + (s & 1);
     // 1. filter the windows by the shared prefix (the list count was zeroed before the
     //    barrier that precedes this phase)
@@ -835,7 +841,7 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     // One barrier: the list may be rebuilt, and the tile stops once no lane has a live candidate.
     live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
   }
-  if (jd.seq_block > 0) {
+  if (SPLIT) {
     if (in_chunk) group_and_bitmap(jd, g, alive);
   } else {
     group_output<KS>(jd, st, g, alive);
@@ -846,9 +852,11 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
 // The step kernel.
 
 // KIND = MOTIF_KERNEL_CAND with P = candidates per lane, or MOTIF_KERNEL_GROUP with P = ks.
+// SPLIT (GROUP, P = 4 only): the tiled pass also runs jobs split into (tile, sequence block)
+// items; without it the whole-tile loop carries none of that code.
 // Shared memory: staged windows of the pass (CAND: planes; GROUP: prefix planes, suffix values
 // and one hit list per thread).
-template <int KIND, int P>
+template <int KIND, int P, bool SPLIT>
 __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restrict__ jobs,
                                                          JobState* states, int njobs,
                                                          StepCtl* ctl,
@@ -941,14 +949,16 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
         __syncthreads();
         const unsigned long long b = s_tbase;
         if (b >= p.work) break;
-        if (jd.seq_block > 0) {  // item b / 256 = (sequence block, tile), blocks outermost
-          const unsigned long long tiles = (p.chunk_units + 255) / 256, u = b >> 8;
-          const int s_begin = (int)(u / tiles) * jd.seq_block;
-          const int s_end = s_begin + jd.seq_block < jd.n ? s_begin + jd.seq_block : jd.n;
-          group_tiled(jd, st, p, (u % tiles) << 8, s_begin, s_end, head, map, s_tcnt);
-        } else {
-          group_tiled(jd, st, p, b, 0, jd.n, head, map, s_tcnt);
+        if constexpr (SPLIT) {
+          if (jd.seq_block > 0) {  // item b / 256 = (sequence block, tile), blocks outermost
+            const unsigned long long tiles = (p.chunk_units + 255) / 256, u = b >> 8;
+            const int s0 = (int)(u / tiles) * jd.seq_block;
+            const int s1 = s0 + jd.seq_block < jd.n ? s0 + jd.seq_block : jd.n;
+            group_tiled<true>(jd, st, p, (u % tiles) << 8, s0, s1, head, map, s_tcnt);
+            continue;
+          }
         }
+        group_tiled<false>(jd, st, p, b, 0, 0, head, map, s_tcnt);
       }
       continue;
     }
@@ -1169,12 +1179,13 @@ __global__ void ball_kernel(uint64_t* table, int ks) {
 }
 
 
-template <int KIND, int P>
+template <int KIND, int P, bool SPLIT = false>
 const void* step_fn() {
-  return reinterpret_cast<const void*>(&step_kernel<KIND, P>);
+  return reinterpret_cast<const void*>(&step_kernel<KIND, P, SPLIT>);
 }
 
 const void* step_function(int kind, int p) {
+  if (kind == kKindTiledSplit) return p == 4 ? step_fn<MOTIF_KERNEL_GROUP, 4, true>() : nullptr;
   if (kind == MOTIF_KERNEL_CAND) {
     switch (p) {
       case 1: return step_fn<MOTIF_KERNEL_CAND, 1>();
@@ -1220,9 +1231,9 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
 // share the kernels, and one caller's smaller request must not break another's launch.
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem) {
   static std::mutex mu;
-  static size_t set[MOTIF_KERNEL_BITSLICE + 1][kMaxKs + 1] = {};
+  static size_t set[kKindTiledSplit + 1][kMaxKs + 1] = {};
   const void* f = step_function(kind, p);
-  if (!f || kind < 1 || kind > MOTIF_KERNEL_BITSLICE || p < 1 || p > kMaxKs)
+  if (!f || kind < 1 || kind > kKindTiledSplit || p < 1 || p > kMaxKs)
     return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> g(mu);
   if (smem <= set[kind][p]) return cudaSuccess;

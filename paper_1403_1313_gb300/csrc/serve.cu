@@ -251,8 +251,11 @@ int prepare_launch(Server* S, int kind, int pv, size_t smem) {
   if (S->kind == kind && S->pv == pv && S->smem >= smem && (S->exec || !S->o.use_graph))
     return MOTIF_OK;
   smem = std::max(smem, S->smem);
-  if (step_kernel_attrs(kind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
-  const int per_sm = step_max_ctas_per_sm(kind, pv, S->block, smem);
+  // GROUP k = 4 tables run the kernel variant with the split tiled pass: jobs of either form
+  // share the table as they arrive.
+  const int lk = launch_kind(kind, pv, true);
+  if (step_kernel_attrs(lk, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
+  const int per_sm = step_max_ctas_per_sm(lk, pv, S->block, smem);
   if (per_sm <= 0) return MOTIF_ERR_ARG;
   S->kind = kind;
   S->pv = pv;
@@ -267,7 +270,7 @@ int prepare_launch(Server* S, int kind, int pv, size_t smem) {
     cudaGraphNode_t node;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess)
-      e = add_step_node(g, kind, pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl, S->grid,
+      e = add_step_node(g, lk, pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl, S->grid,
                         S->block, S->smem, 0, 0, &node);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&S->exec, g, 0);
     if (g) cudaGraphDestroy(g);
@@ -436,7 +439,8 @@ void scheduler(Server* S) {
         e = cudaGraphLaunch(S->exec, S->stream);
         note_launches(1);
       } else {
-        e = launch_step(S->kind, S->pv, S->d_jobs, S->d_states, max_active(S), S->d_ctl,
+        e = launch_step(launch_kind(S->kind, S->pv, true), S->pv, S->d_jobs, S->d_states,
+                        max_active(S), S->d_ctl,
                         S->grid, S->block, S->smem, S->stream);
       }
     }

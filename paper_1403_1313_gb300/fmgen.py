@@ -120,6 +120,7 @@ SINGLE_CONFIGS = {
     "l9d2": (9, 2, 20, 600, 1),
     "l15d4": (15, 4, 20, 600, 2),
     "l17d5": (17, 5, 20, 600, 3),
+    "l11d4": (11, 4, 28, 859, 7),
 }
 
 

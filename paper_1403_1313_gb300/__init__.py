@@ -208,12 +208,13 @@ def motif_plan_destroy(plan: Plan) -> None:
 
 
 def _rows(seqs, t=None):
-    """(bytes, n, t, stride) for a list of str/bytes rows or an (n, t) uint8 array."""
+    """(buffer, n, t) for a list of str/bytes rows or an (n, t) uint8 array; an array is passed
+    by pointer (the caller keeps the returned array alive through the call)."""
     if isinstance(seqs, np.ndarray):
         a = np.ascontiguousarray(seqs, dtype=np.uint8)
         if a.ndim != 2:
             raise ValueError("expected an (n, t) array of characters")
-        return a.tobytes(), a.shape[0], a.shape[1]
+        return a, a.shape[0], a.shape[1]
     rows = [s.encode() if isinstance(s, str) else bytes(s) for s in seqs]
     if not rows or len({len(r) for r in rows}) != 1:
         raise ValueError("expected n >= 1 rows of one common length")
@@ -224,7 +225,8 @@ def motif_load_seqs(plan: Plan, seqs) -> None:
     buf, n, t = _rows(seqs)
     if (n, t) != (plan.n, plan.t):
         raise ValueError("sequences are %dx%d, plan expects %dx%d" % (n, t, plan.n, plan.t))
-    _check(_load().motif_load_seqs(plan, buf, t), "motif_load_seqs")
+    ptr = buf.ctypes.data_as(ctypes.c_char_p) if isinstance(buf, np.ndarray) else buf
+    _check(_load().motif_load_seqs(plan, ptr, t), "motif_load_seqs")
 
 
 def motif_load_seqs_device(plan: Plan, d_seqs, stride: int | None = None) -> None:
@@ -282,16 +284,23 @@ def read_fasta(path: str) -> list:
 _PINNED = None  # torch, once it is known to have a CUDA device; False where it has none
 
 
+_PINNED_MIN_CODES = 1 << 17  # 1 MiB: below this a plain array costs less than a pinned block
+
+
 def _host_codes(capacity: int) -> np.ndarray:
     """An uninitialised host buffer for `capacity` codes (the library writes every returned one).
 
-    Taken from torch's caching pinned-host allocator: the device copy runs at full link rate,
-    and a block freed by an earlier result comes back with its pages already mapped.  A freshly
-    allocated pageable array instead pays the operating system's first touch of every page inside
-    the copy (about 8 ms for 195 MB on a GB300 host, against 1 ms into mapped memory).  The
-    returned array keeps its block alive; dropping the array gives the block back."""
+    Large buffers come from torch's caching pinned-host allocator: the device copy runs at full
+    link rate, and a block freed by an earlier result comes back with its pages already mapped.
+    A freshly allocated pageable array instead pays the operating system's first touch of every
+    page inside the copy (about 8 ms for 195 MB on a GB300 host, against 1 ms into mapped
+    memory).  The returned array keeps its block alive; dropping the array gives the block back.
+    Small buffers are plain arrays (small results arrive through the library's own pinned
+    staging)."""
     global _PINNED
     n = max(int(capacity), 1)
+    if n < _PINNED_MIN_CODES:
+        return np.empty(n, dtype=np.uint64)
     if _PINNED is None:
         try:
             import torch

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <atomic>
 #include <mutex>
@@ -478,6 +479,32 @@ int ensure_sort(motif_plan_s* p, int64_t cap) {
   return p->d_sort ? MOTIF_OK : MOTIF_ERR_OOM;
 }
 
+// The sort graph over (out, cap): the one-CTA sort, and, when `scratch` (sized for cap) is
+// given, the multi-CTA sort under a conditional IF node that runs only when the count needs it.
+// A count above cap (an overflowed search) is left as it is.
+int ensure_sort_graph(motif_plan_s* p, uint64_t* out, int64_t cap, void* scratch) {
+  if (p->g_sort && p->gs_out == out && p->gs_cap == cap && p->gs_scratch == scratch)
+    return MOTIF_OK;
+  if (p->g_sort) cudaGraphExecDestroy(p->g_sort);
+  p->g_sort = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphNode_t last;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess)
+    e = add_sort_nodes(g, nullptr, out, &p->d_state->out_count, cap, 2 * p->l, scratch, p->sms,
+                       &last);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->g_sort, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p->g_sort = nullptr;
+    return status_from_cuda(e);
+  }
+  p->gs_out = out;
+  p->gs_cap = cap;
+  p->gs_scratch = scratch;
+  return MOTIF_OK;
+}
+
 int check_alphabet(motif_plan_s* p) {
   if (!p->check_alpha) return MOTIF_OK;
   int err = 0;
@@ -708,6 +735,9 @@ void motif_plan_destroy(motif_plan p) {
     if (ev) cudaEventDestroy(ev);
   invalidate_graphs(p);
   if (p->h_desc) cudaFreeHost(p->h_desc);
+  if (p->h_chars) cudaFreeHost(p->h_chars);
+  if (p->h_chars_done) cudaEventDestroy(p->h_chars_done);
+  if (p->h_res) cudaFreeHost(p->h_res);
   delete p;
 }
 
@@ -725,10 +755,53 @@ static int load_common(motif_plan p, bool sync_check) {
   return sync_check ? check_alphabet(p) : MOTIF_OK;
 }
 
+// Host loads up to this size are validated on the host while they are copied into pinned
+// staging: a few microseconds, against a wait for the device's check.
+constexpr size_t kHostCheckBytes = (size_t)1 << 16;
+
+// Copies the n rows into the plan's pinned staging buffer; false if a character is outside
+// ACGTacgt.
+static bool stage_checked(motif_plan_s* p, const char* seqs, int64_t stride) {
+  static const std::array<uint8_t, 256> valid = [] {
+    std::array<uint8_t, 256> a{};
+    for (unsigned char c : {'A', 'C', 'G', 'T', 'a', 'c', 'g', 't'}) a[c] = 1;
+    return a;
+  }();
+  unsigned bad = 0;
+  for (int r = 0; r < p->n; ++r) {
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(seqs) + (size_t)r * stride;
+    char* dst = p->h_chars + (size_t)r * p->t;
+    for (int c = 0; c < p->t; ++c) {
+      bad |= valid[src[c]] ^ 1u;
+      dst[c] = (char)src[c];
+    }
+  }
+  return bad == 0;
+}
+
 int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride) {
   if (!p || !seqs || stride < p->t) return MOTIF_ERR_ARG;
   DeviceGuard g(p->device);
   p->loaded = false;
+  const size_t bytes = (size_t)p->n * p->t;
+  if (bytes <= kHostCheckBytes) {
+    cudaError_t e = cudaSuccess;
+    if (!p->h_chars) {
+      e = cudaHostAlloc((void**)&p->h_chars, bytes, 0);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->h_chars_done, cudaEventDisableTiming);
+      if (e != cudaSuccess) return status_from_cuda(e);
+    } else {
+      e = cudaEventSynchronize(p->h_chars_done);  // the previous upload has read the staging
+      if (e != cudaSuccess) return status_from_cuda(e);
+    }
+    if (!stage_checked(p, seqs, stride)) return MOTIF_ERR_ALPHABET;
+    e = cudaMemcpyAsync(p->d_chars, p->h_chars, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->h_chars_done, p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    const int rc = load_common(p, false);
+    p->check_alpha = false;  // validated above
+    return rc;
+  }
   cudaError_t e = cudaMemcpy2DAsync(p->d_chars, p->t, seqs, (size_t)stride, p->t, p->n,
                                     cudaMemcpyHostToDevice, p->stream);
   if (e != cudaSuccess) return status_from_cuda(e);
@@ -800,6 +873,9 @@ int motif_load_seqs_var(motif_plan p, const char* seqs, int64_t stride, const in
   return MOTIF_OK;
 }
 
+// Codes a blocking search reads back speculatively with its count (one wait for small results).
+constexpr int64_t kResultPeek = 512;
+
 int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* out_count) {
   if (!p || !out_count || capacity < 0 || (capacity > 0 && !out_codes)) return MOTIF_ERR_ARG;
   if (!p->loaded) return MOTIF_ERR_STATE;
@@ -824,35 +900,64 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   cudaEvent_t* ev = next_event_quad(p);
   if (!ev) return MOTIF_ERR_CUDA;
   if (p->bitmap) return search_bitmap(p, out_codes, capacity, out_count, ev, t0);
+  // List output: the steps and the sort graph run back to back, then one wait reads the final
+  // count and, speculatively, the first codes.  A count above the buffer means the search
+  // overflowed it (the sort leaves such a count alone): the buffer grows and the search reruns.
+  if (!p->h_res) {
+    cudaError_t e = cudaHostAlloc((void**)&p->h_res, (1 + kResultPeek) * sizeof(uint64_t), 0);
+    if (e != cudaSuccess) {
+      p->h_res = nullptr;
+      return status_from_cuda(e);
+    }
+  }
+  unsigned long long final_count = 0;
+  int64_t peek = 0;
+  bool sorted = false;  // the graph's multi-CTA branch covers every count up to the buffer's
   for (;;) {
-    cudaEventRecord(ev[0], p->stream);
     rc = plan_ensure_buffers(p);
     if (rc) return rc;
+    // (the multi-CTA sort's scratch is allocated by the first result that needs it; until then
+    // the graph holds the one-CTA sort only)
+    sorted = p->out_cap <= 4096 ||
+             (p->d_sort && p->sort_bytes >= sort_scratch_bytes(p->out_cap, p->sms));
+    rc = ensure_sort_graph(p, p->d_out, p->out_cap, sorted ? p->d_sort : nullptr);
+    if (rc) return rc;
+    cudaEventRecord(ev[0], p->stream);
     rc = enqueue_search(p, p->d_out, (uint64_t)p->out_cap, true);
     if (rc) return rc;
     cudaEventRecord(ev[1], p->stream);
-    cudaError_t e = cudaMemcpyAsync(&found, &p->d_state->out_count, sizeof(found),
-                                    cudaMemcpyDeviceToHost, p->stream);
+    cudaEventRecord(ev[2], p->stream);
+    cudaError_t e = cudaGraphLaunch(p->g_sort, p->stream);
+    note_launches(1);
+    cudaEventRecord(ev[3], p->stream);
+    peek = std::min<int64_t>(std::min<int64_t>(p->out_cap, capacity), kResultPeek);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->h_res, &p->d_state->out_count, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess && peek > 0)
+      e = cudaMemcpyAsync(p->h_res + 1, p->d_out, (size_t)peek * 8, cudaMemcpyDeviceToHost,
+                          p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
-    if (found <= (unsigned long long)p->out_cap) break;
-    rc = ensure_out(p, (int64_t)std::max<unsigned long long>(found, 2 * (unsigned long long)p->out_cap));
+    final_count = p->h_res[0];
+    if (final_count <= (unsigned long long)p->out_cap) break;
+    rc = ensure_out(p, (int64_t)std::max<unsigned long long>(final_count,
+                                                             2 * (unsigned long long)p->out_cap));
     if (rc) return rc;
   }
-  if (found > 4096) {
+  if (final_count > 4096 && !sorted) {  // more codes than the one-CTA sort takes: sort them now
     rc = ensure_sort(p, p->out_cap);
     if (rc) return rc;
+    cudaError_t e = launch_sort_unique(p->d_out, &p->d_state->out_count, p->out_cap, 2 * p->l,
+                                       p->d_sort, p->sms, (long long)final_count, p->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->h_res, &p->d_state->out_count, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    final_count = p->h_res[0];
+    peek = 0;  // the codes read back with the count were not sorted yet
   }
-  cudaEventRecord(ev[2], p->stream);
-  cudaError_t e = launch_sort_unique(p->d_out, &p->d_state->out_count, p->out_cap, 2 * p->l,
-                                     p->d_sort, p->sms, (long long)found, p->stream);
-  cudaEventRecord(ev[3], p->stream);
-  unsigned long long final_count = 0;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&final_count, &p->d_state->out_count, sizeof(final_count),
-                        cudaMemcpyDeviceToHost, p->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-  if (e != cudaSuccess) return status_from_cuda(e);
   *out_count = (int64_t)final_count;
   rc = fold_event_quads(p);
   if (rc) return rc;
@@ -861,8 +966,11 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
     p->stats.total_ms = now_ms() - t0;
     return MOTIF_ERR_CAPACITY;
   }
-  if (final_count) {
-    e = cudaMemcpyAsync(out_codes, p->d_out, final_count * 8, cudaMemcpyDeviceToHost, p->stream);
+  if ((int64_t)final_count <= peek) {
+    if (final_count) memcpy(out_codes, p->h_res + 1, (size_t)final_count * 8);
+  } else {
+    cudaError_t e = cudaMemcpyAsync(out_codes, p->d_out, final_count * 8, cudaMemcpyDeviceToHost,
+                                    p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
   }
@@ -907,22 +1015,8 @@ int motif_search_device(motif_plan p, uint64_t* d_out_codes, int64_t capacity,
     if (rc) return rc;
     cudaEventRecord(ev[1], p->stream);
     cudaEventRecord(ev[2], p->stream);
-    if (!p->g_sort || p->gs_out != d_out_codes || p->gs_cap != capacity || p->gs_scratch != p->d_sort) {
-      if (p->g_sort) cudaGraphExecDestroy(p->g_sort);
-      p->g_sort = nullptr;
-      cudaGraph_t g = nullptr;
-      cudaGraphNode_t last;
-      cudaError_t e = cudaGraphCreate(&g, 0);
-      if (e == cudaSuccess)
-        e = add_sort_nodes(g, nullptr, d_out_codes, &p->d_state->out_count, capacity, 2 * p->l,
-                           p->d_sort, p->sms, &last);
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&p->g_sort, g, 0);
-      if (g) cudaGraphDestroy(g);
-      if (e != cudaSuccess) { p->g_sort = nullptr; return status_from_cuda(e); }
-      p->gs_out = d_out_codes;
-      p->gs_cap = capacity;
-      p->gs_scratch = p->d_sort;
-    }
+    rc = ensure_sort_graph(p, d_out_codes, capacity, p->d_sort);  // sized for capacity above
+    if (rc) return rc;
     cudaError_t e = cudaGraphLaunch(p->g_sort, p->stream);
     note_launches(1);
     cudaEventRecord(ev[3], p->stream);

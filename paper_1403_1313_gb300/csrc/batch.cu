@@ -258,7 +258,10 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
             p->d_sort = plan_alloc(p, need);
             cudaStreamSynchronize(p->stream);  // the scratch is used on the batch stream
             p->sort_bytes = p->d_sort ? need : 0;
-            p->gs_scratch = nullptr;  // any cached sort graph names the old scratch
+            if (p->g_sort) {  // a cached sort graph may name the old scratch
+              cudaGraphExecDestroy(p->g_sort);
+              p->g_sort = nullptr;
+            }
             if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
           }
         }

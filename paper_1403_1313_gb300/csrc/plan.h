@@ -63,6 +63,12 @@ struct motif_plan_s {
   cudaGraphExec_t g_steps = nullptr;
   cudaGraphExec_t g_sort = nullptr;
   motif::JobDesc* h_desc = nullptr;  // pinned copy of the uploaded descriptor
+  // Pinned host staging: the characters of a small host load (validated while they are copied
+  // in, so the load need not wait for the device), and the final count plus the first codes of
+  // a blocking search (read back with one wait).
+  char* h_chars = nullptr;
+  cudaEvent_t h_chars_done = nullptr;  // recorded after the staged characters' upload
+  uint64_t* h_res = nullptr;           // [1 + kResultPeek]
   uint64_t* desc_out = nullptr;      // output buffer named by the uploaded descriptor
   int64_t desc_cap = -1;
   uint64_t* gs_out = nullptr;        // buffers the sort graph was built for

@@ -330,7 +330,7 @@ void invalidate_graphs(motif_plan_s* p) {
 
 void free_seed(motif_plan_s* p) {
   if (p->d_pat) plan_free(p, p->d_pat, p->pat_alloc * 8);
-  if (p->d_seed) plan_free(p, p->d_seed, p->seed_alloc_words * 4);
+  if (p->d_seed) plan_free(p, p->d_seed, (p->seed_alloc_words + 1) * 4);
   if (p->d_seed_scratch)
     plan_free(p, p->d_seed_scratch, bitmap_scratch_words(p->seed_alloc_words) * 4);
   if (p->d_seed_count) plan_free(p, p->d_seed_count, sizeof(unsigned long long));
@@ -342,7 +342,7 @@ void free_seed(motif_plan_s* p) {
 }
 
 int prepare_seed(motif_plan_s* p, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(p->d_seed, 0, p->seed_words * 4, s);
+  cudaError_t e = cudaMemsetAsync(p->d_seed, 0, (p->seed_words + 1) * 4, s);
   if (e == cudaSuccess)
     e = launch_seed_scatter(p->d_codes, p->W, p->d_pat, p->npat, p->lo, p->hi, p->d_seed,
                             p->seed_base, s);
@@ -382,7 +382,8 @@ int plan_ensure_buffers(motif_plan_s* p) {
     std::vector<uint64_t> pat;
     difference_patterns(p->l, p->d, pat);
     p->d_pat = (uint64_t*)plan_alloc(p, pat.size() * 8);
-    p->d_seed = (uint32_t*)plan_alloc(p, p->seed_words * 4);
+    // one word past the bitmap: a fresh pass reads each lane's 32 bits as two words
+    p->d_seed = (uint32_t*)plan_alloc(p, (p->seed_words + 1) * 4);
     p->d_seed_scratch = (unsigned*)plan_alloc(p, bitmap_scratch_words(p->seed_words) * 4);
     p->d_seed_count = (unsigned long long*)plan_alloc(p, sizeof(unsigned long long));
     p->desc_out = nullptr;  // the descriptor names the seed bitmap

@@ -341,6 +341,38 @@ __device__ __forceinline__ unsigned scan_bitslice(const uint32_t* __restrict__ s
   return matched & alive;
 }
 
+// Seeded FRESH tile (CAND, BITSLICE): the seed bitmap holds exactly the candidates within d of
+// a window of the first sequence, so the pass scans no sequence; it compacts the seeded items of
+// [base, base + 1024), 32 per lane (one seed word, read as two when the range start is not a
+// multiple of 32), into the queue, or accepts them when there is no other sequence.
+__device__ __noinline__ void seeded_fresh_tile(const JobDesc& jd, JobState* st, const Pass& p,
+                                  unsigned long long base) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long item0 = base + 32ull * (unsigned)lane;
+  uint32_t bits = 0;
+  if (item0 < p.work) {
+    // bit (code - seed_base) of the bitmap, for the codes chunk_base + item0 + 0..31; the
+    // bitmap holds one word past its end, so word + 1 is always readable
+    const uint64_t b = p.chunk_base + item0 - jd.seed_base;
+    const uint32_t w0 = __ldg(jd.seed + (b >> 5)), w1 = __ldg(jd.seed + (b >> 5) + 1);
+    bits = __funnelshift_r(w0, w1, (unsigned)(b & 31));
+    const unsigned long long left = p.work - item0;
+    if (left < 32) bits &= (1u << (unsigned)left) - 1u;
+  }
+  const unsigned cnt = __popc(bits);
+  if (p.s1 >= jd.n && jd.bitmap) {
+    for (uint32_t x = bits; x; x &= x - 1) bitmap_set(jd, p.chunk_base + item0 + (__ffs(x) - 1));
+  } else if (p.s1 >= jd.n) {
+    unsigned long long slot = warp_reserve(&st->out_count, cnt);
+    for (uint32_t x = bits; x; x &= x - 1, ++slot)
+      if (slot < jd.out_cap) jd.out[slot] = p.chunk_base + item0 + (__ffs(x) - 1);
+  } else {
+    unsigned long long slot = warp_reserve(&st->qcount[p.qout], cnt);
+    for (uint32_t x = bits; x; x &= x - 1)
+      jd.qidx[p.qout][slot++] = (uint32_t)(item0 + (__ffs(x) - 1));
+  }
+}
+
 // FRESH / QUEUE tile: lane slot c of the warp owns item base + c*32 + lane.
 template <int KIND, int CPT>
 __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
@@ -356,12 +388,7 @@ __device__ void cand_tile(const JobDesc& jd, JobState* st, const Pass& p,
     if (item < p.work) {
       off[c] = p.mode == kFresh ? (uint32_t)item : jd.qidx[p.qin][item];
       code_planes(p.chunk_base + off[c], E[c], O[c]);
-      bool seeded = true;
-      if (p.mode == kFresh && jd.seed) {
-        const uint64_t b = p.chunk_base + off[c] - jd.seed_base;
-        seeded = (__ldg(jd.seed + (b >> 5)) >> (b & 31)) & 1u;
-      }
-      if (seeded) alive |= 1u << c;
+      alive |= 1u << c;
     }
   }
   const int wpad = jd.wstride;
@@ -963,7 +990,8 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       continue;
     }
     // Pull tiles until the pass is exhausted (or the step's tile budget is spent).
-    const unsigned long long tile = tile_of(KIND, P, p.mode);
+    const bool seeded_fresh = KIND != MOTIF_KERNEL_GROUP && p.mode == kFresh && jd.seed;
+    const unsigned long long tile = seeded_fresh ? 1024 : tile_of(KIND, P, p.mode);
     for (;;) {
       unsigned long long base = 0;
       int stop = 0;
@@ -980,6 +1008,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
       base = __shfl_sync(kFull, base, 0);
       if (KIND == MOTIF_KERNEL_CAND || KIND == MOTIF_KERNEL_BITSLICE) {
         if (p.mode == kRest) cand_rest(jd, st, p, base);
+        else if (seeded_fresh) seeded_fresh_tile(jd, st, p, base);
         else if (p.mode == kFresh) cand_tile<KIND, P>(jd, st, p, base, stage4);
         else cand_tile<KIND, 1>(jd, st, p, base, stage4);
       } else {

@@ -1,9 +1,9 @@
 """Seeded random combinations of every option against the oracle, element by element.
 
 Each case draws a kernel form, an output collection, candidate seeding (where the form allows
-it), equal-length or ragged rows with masked symbols, a candidate sub-range and a search path
-(blocking, device, or batched with its neighbours), and compares the codes with the oracle's
-exactly.  The draws are fixed by the case number, so a failure names a reproducible case.
+it), the tiled pass's sequence blocks, equal-length or ragged rows with masked symbols, a
+candidate sub-range and a search path (blocking, device, or batched with its neighbours), and
+compares the codes with the oracle's exactly.  The draws are fixed by the case number, so a failure names a reproducible case.
 """
 import random
 
@@ -49,6 +49,8 @@ def _draw(case):
             opts["seed"] = m.SEED_NEIGHBOURHOOD
     if kernel == m.KERNEL_GROUP:
         opts["suffix_bases"] = rng.randint(1, 4)
+    if kernel in (m.KERNEL_AUTO, m.KERNEL_TILED) and rng.random() < 0.5:
+        opts["seq_block"] = rng.choice([-1, 1, 2, 3])  # a dense bitmap job's tiled-pass split
     space = 4 ** l
     lo, hi = 0, space
     if rng.random() < 0.4:

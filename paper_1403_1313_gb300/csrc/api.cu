@@ -742,18 +742,21 @@ void motif_plan_destroy(motif_plan p) {
   delete p;
 }
 
-static int load_common(motif_plan p, bool sync_check) {
+// Packs the plan's characters.  checked: validated on the host already (no device check);
+// otherwise the device check's flag is read now (sync_check) or by the next call that waits.
+// The flag is cleared either way: the device search path reports it.
+static int load_common(motif_plan p, bool sync_check, bool checked = false) {
   if (p->ragged) p->desc_out = nullptr;  // the descriptor names the ragged-row buffers
   p->ragged = false;
   p->empty_row = false;
   cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
-  if (e != cudaSuccess) return status_from_cuda(e);
-  e = launch_pack(p->d_chars, p->t, p->n, p->t, p->l, p->wstride, p->d_planes, p->d_codes,
-                  p->d_err, p->stream);
+  if (e == cudaSuccess)
+    e = launch_pack(p->d_chars, p->t, p->n, p->t, p->l, p->wstride, p->d_planes, p->d_codes,
+                    checked ? nullptr : p->d_err, p->stream);
   if (e != cudaSuccess) return status_from_cuda(e);
   p->loaded = true;
-  p->check_alpha = true;
-  return sync_check ? check_alphabet(p) : MOTIF_OK;
+  p->check_alpha = !checked;
+  return sync_check && !checked ? check_alphabet(p) : MOTIF_OK;
 }
 
 // Host loads up to this size are validated on the host while they are copied into pinned
@@ -799,9 +802,7 @@ int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride) {
     e = cudaMemcpyAsync(p->d_chars, p->h_chars, bytes, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaEventRecord(p->h_chars_done, p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
-    const int rc = load_common(p, false);
-    p->check_alpha = false;  // validated above
-    return rc;
+    return load_common(p, false, true);  // validated above
   }
   cudaError_t e = cudaMemcpy2DAsync(p->d_chars, p->t, seqs, (size_t)stride, p->t, p->n,
                                     cudaMemcpyHostToDevice, p->stream);
@@ -917,10 +918,12 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   for (;;) {
     rc = plan_ensure_buffers(p);
     if (rc) return rc;
-    // (the multi-CTA sort's scratch is allocated by the first result that needs it; until then
-    // the graph holds the one-CTA sort only)
+    // The graph holds the multi-CTA sort (under a conditional node, about 10 us even when it
+    // is skipped) only once the plan's previous result needed it; until then the one-CTA sort
+    // alone, and a larger result is sorted below with one more wait.
     sorted = p->out_cap <= 4096 ||
-             (p->d_sort && p->sort_bytes >= sort_scratch_bytes(p->out_cap, p->sms));
+             (p->stats.survivors > 4096 && p->d_sort &&
+              p->sort_bytes >= sort_scratch_bytes(p->out_cap, p->sms));
     rc = ensure_sort_graph(p, p->d_out, p->out_cap, sorted ? p->d_sort : nullptr);
     if (rc) return rc;
     cudaEventRecord(ev[0], p->stream);

@@ -96,6 +96,8 @@ cudaError_t launch_pack_var(const char* d_chars, int64_t stride, int n, int l, i
                             const int32_t* d_lens, int mask_unknown, uint2* planes,
                             uint64_t* codes, uint8_t* valid, int* d_err, int* d_empty,
                             cudaStream_t s);
+// Packs n rows of t characters into window planes and codes; with d_err, a character outside
+// ACGTacgt sets *d_err (checked while packing, or alone when t < l); d_err null: no check.
 cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l, int wstride,
                         uint2* planes, uint64_t* codes, int* d_err, cudaStream_t s);
 // Fills the Hamming-ball table for ks (ball_table_words(ks) words).

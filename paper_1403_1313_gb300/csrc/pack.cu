@@ -33,11 +33,14 @@ __global__ void validate_kernel(const char* __restrict__ chars, int64_t stride, 
   }
 }
 
+// Packs every window and, when err is given, validates the characters on the way: with t >= l
+// the windows cover every character of every row.
 __global__ void pack_kernel(const char* __restrict__ chars, int64_t stride, int n, int t, int l,
                             int wstride, uint2* __restrict__ planes,
-                            uint64_t* __restrict__ codes) {
+                            uint64_t* __restrict__ codes, int* err) {
   const int W = t - l + 1;
   const int64_t total = (int64_t)n * wstride;
+  int bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int s = (int)(i / wstride);
@@ -48,7 +51,8 @@ __global__ void pack_kernel(const char* __restrict__ chars, int64_t stride, int 
     uint32_t E = 0, O = 0;
     for (int b = 0; b < l; ++b) {
       int v = base_code(p[b]);
-      v = v < 0 ? 0 : v;  // invalid characters are reported by validate_kernel
+      bad |= v < 0;
+      v = v < 0 ? 0 : v;
       code = (code << 2) | (uint64_t)v;
       E = (E << 1) | (uint32_t)(v & 1);
       O = (O << 1) | (uint32_t)(v >> 1);
@@ -56,6 +60,7 @@ __global__ void pack_kernel(const char* __restrict__ chars, int64_t stride, int 
     planes[i] = make_uint2(E, O);
     codes[i] = code;
   }
+  if (err && bad) atomicOr(err, 1);
 }
 
 // Ragged rows: row s holds lens[s] characters.  A window is valid when it lies inside its row
@@ -160,14 +165,17 @@ cudaError_t launch_pack(const char* d_chars, int64_t stride, int n, int t, int l
   int grid = (int)((chars + block - 1) / block);
   if (grid > 4096) grid = 4096;
   if (grid < 1) grid = 1;
-  validate_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, d_err);
-  note_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || t < l) return e;
+  if (t < l) {  // no windows: only the characters to check
+    if (d_err) {
+      validate_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, d_err);
+      note_launches(1);
+    }
+    return cudaGetLastError();
+  }
   const int64_t wins = (int64_t)n * wstride;
   grid = (int)((wins + block - 1) / block);
   if (grid > 4096) grid = 4096;
-  pack_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, l, wstride, planes, codes);
+  pack_kernel<<<grid, block, 0, s>>>(d_chars, stride, n, t, l, wstride, planes, codes, d_err);
   note_launches(1);
   return cudaGetLastError();
 }

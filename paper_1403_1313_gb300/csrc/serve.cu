@@ -115,17 +115,20 @@ uint64_t* host_take(Server* S, size_t n, size_t* cap) {
   return b;
 }
 
-void host_give(Server* S, uint64_t* b, size_t cap) {
+// Returns a block to the pool (under S->mu).  Blocks that do not fit the pool's bound go to
+// `evicted`, for the caller to free once it has released the lock: cudaFreeHost may wait for the
+// device, which must not hold up the scheduler.
+void host_give(Server* S, uint64_t* b, size_t cap, std::vector<uint64_t*>* evicted) {
   if (!b) return;
+  if (cap * 8 > kHostPoolBytes) {
+    evicted->push_back(b);
+    return;
+  }
   while (S->host_free_bytes + cap * 8 > kHostPoolBytes && !S->host_free.empty()) {
     auto big = std::prev(S->host_free.end());  // evict the largest pooled blocks first
     S->host_free_bytes -= big->first * 8;
-    cudaFreeHost(big->second);
+    evicted->push_back(big->second);
     S->host_free.erase(big);
-  }
-  if (cap * 8 > kHostPoolBytes) {
-    cudaFreeHost(b);
-    return;
   }
   S->host_free.emplace(cap, b);
   S->host_free_bytes += cap * 8;
@@ -711,8 +714,11 @@ extern "C" int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity,
   if (j->status == MOTIF_OK && j->result_size > capacity) return MOTIF_ERR_CAPACITY;
   if (j->result_size > 0) memcpy(out_codes, j->result, (size_t)j->result_size * 8);
   const int st = j->status;
-  host_give(S, j->result, j->result_cap);
+  std::vector<uint64_t*> evicted;
+  host_give(S, j->result, j->result_cap, &evicted);
   S->jobs.erase(it);
   delete j;  // the scheduler released its device buffers when it retired the job
+  lk.unlock();
+  for (uint64_t* b : evicted) cudaFreeHost(b);
   return st;
 }

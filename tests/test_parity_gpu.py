@@ -7,6 +7,7 @@ tiles; the full-size workloads are checked on sampled candidate sub-ranges the o
 directly, plus properties that hold at any size (the planted consensus is accepted, every
 accepted code is accepted by the oracle one by one, the kernels agree with each other).
 """
+import hashlib
 import json
 import os
 import random
@@ -256,6 +257,44 @@ def test_full_size_sampled(cfg):
         assert cmp == ref_cmp
         inside = full[(full >= lo) & (full < hi)]
         assert np.array_equal(inside, ref)
+
+
+FULL_GOLDEN = {"l15d4": "l15d4_n20_t600_seed2.json"}
+
+
+@pytest.mark.parametrize("form", ["auto", "device", "bitslice_seeded"])
+@pytest.mark.parametrize("cfg", sorted(FULL_GOLDEN))
+def test_full_space_matches_stored_oracle(cfg, form):
+    """The whole code space of the (15,4) workload against the oracle's complete result
+    (tests/golden/, written by make_golden.py from oracle/ alone): every code, none missing,
+    and the canonical compare tally.  ((17,5), 16 times the candidates, is checked on sampled
+    ranges and per accepted code in test_full_size_sampled.)"""
+    path = os.path.join(GOLDEN, FULL_GOLDEN[cfg])
+    if not os.path.exists(path):
+        pytest.skip("no stored oracle result for %s (tests/golden/make_golden.py %s)" % (cfg, cfg))
+    with open(path) as f:
+        g = json.load(f)
+    job = fmgen.single(cfg)
+    assert hashlib.sha256(job.seqs.tobytes()).hexdigest() == g["seqs_sha256"]
+    if form == "device":  # the benchmark's launch configuration
+        torch = pytest.importorskip("torch")
+        plan = m.motif_plan_create(job.n, job.t, job.l, job.d, m.torch_opts())
+        m.motif_load_seqs_device(plan, torch.from_numpy(job.seqs.copy()).cuda())
+        out = torch.zeros(1 << 16, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        m.motif_search_device(plan, out, out.numel(), cnt)
+        torch.cuda.synchronize()
+        c = int(cnt.item())
+        got = out[:c].cpu().numpy().astype(np.uint64)
+    else:
+        kw = dict(kernel=m.KERNEL_BITSLICE, seed=m.SEED_NEIGHBOURHOOD) if form != "auto" else {}
+        plan = m.motif_plan_create(job.n, job.t, job.l, job.d, _opts(**kw))
+        m.motif_load_seqs(plan, job.seqs)
+        got = m.motif_search(plan)
+    assert got.tolist() == g["codes"]
+    if form == "auto":
+        assert m.motif_count_compares(plan) == g["compares"]
+    m.motif_plan_destroy(plan)
 
 
 def test_l15d4_kernels_agree():

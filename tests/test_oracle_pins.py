@@ -8,6 +8,7 @@ work.  A plausible mistake in the oracle (a dropped sequence, `<` for `<=`, an o
 window count, a wrong base order in the code, a broken skip) fails at least one of them.
 """
 import itertools
+import math
 import json
 import os
 import random
@@ -269,3 +270,28 @@ def test_golden_l9d2_matches_regeneration():
     codes, compares = oracle.search(job.rows(), 9, 2, threads=4)
     assert codes.tolist() == g["codes"] and compares == g["compares"]
     assert base4(job.consensus) in g["codes"]
+
+
+def test_golden_l15d4_is_consistent():
+    """The stored complete (15,4) result (about 25 minutes of oracle time on 8 cores, so not
+    regenerated here): same inputs, the planted consensus among the codes, every stored code
+    accepted by the oracle alone, its neighbours at distance one in the last base rejected, and a
+    compare tally within 0.1 % of the closed form for uniform bases (the skip's expected work)."""
+    with open(os.path.join(GOLDEN, "l15d4_n20_t600_seed2.json")) as f:
+        g = json.load(f)
+    job = fmgen.single("l15d4")
+    import hashlib
+    assert hashlib.sha256(job.seqs.tobytes()).hexdigest() == g["seqs_sha256"]
+    assert g["consensus"] == job.consensus and base4(job.consensus) in g["codes"]
+    stored = set(g["codes"])
+    for c in g["codes"]:
+        assert oracle.search(job.rows(), 15, 4, lo=c, hi=c + 1)[0].tolist() == [c]
+        for x in range(1, 4):  # the other three bases at the last position
+            other = (c & ~3) | ((c + x) & 3)
+            got = oracle.search(job.rows(), 15, 4, lo=other, hi=other + 1)[0].tolist()
+            assert (other in stored) == (got == [other])
+    l, d, n, W = 15, 4, 20, 600 - 15 + 1
+    p = sum(math.comb(l, k) * 3 ** k for k in range(d + 1)) / 4 ** l
+    q = 1 - (1 - p) ** W
+    expect = 4 ** l * (1 - q ** n) / (1 - q) * q / p
+    assert abs(g["compares"] / expect - 1) < 0.001

@@ -275,8 +275,9 @@ def test_golden_l9d2_matches_regeneration():
 def test_golden_l15d4_is_consistent():
     """The stored complete (15,4) result (about 25 minutes of oracle time on 8 cores, so not
     regenerated here): same inputs, the planted consensus among the codes, every stored code
-    accepted by the oracle alone, its neighbours at distance one in the last base rejected, and a
-    compare tally within 0.1 % of the closed form for uniform bases (the skip's expected work)."""
+    accepted by the oracle alone, its three neighbours in the last base stored exactly when the
+    oracle accepts them, and a compare tally within 0.1 % of the closed form for uniform bases
+    (the skip's expected work)."""
     with open(os.path.join(GOLDEN, "l15d4_n20_t600_seed2.json")) as f:
         g = json.load(f)
     job = fmgen.single("l15d4")

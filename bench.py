@@ -149,6 +149,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_cpu() -> dict:
+    """The host's processor: model name (from /proc/cpuinfo where it has one) and ISA."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:  # Arm kernels list no model name there; lscpu names the core
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name:"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model, "isa": platform.machine()}
+
+
 def cpu_baseline(job, seconds: float, steps: int = 1):
     """Times the oracle (all host cores, the paper's range split) on a bounded sub-range."""
     from oracle import oracle
@@ -192,8 +217,8 @@ def run_reference(args):
         "data": "synthetic", "impl": "reference",
         "config": {"workload": "l%dd%d_n%d_t%d_seed%d" % (l, d, n, t, seed), "l": l, "d": d,
                    "n": n, "t": t, "seed": seed, "sample_candidates_per_step": size},
-        "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": cores,
-                         "kind": "oracle", "sample": sample},
+        "cpu_baseline": dict({"value": value, "unit": "candidates/s", "cores": cores,
+                              "kind": "oracle", "sample": sample}, **host_cpu()),
         "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -411,10 +436,10 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             size, times, cores, lo = cpu_baseline(job, args.cpu_seconds)
-            line["cpu_baseline"] = {
+            line["cpu_baseline"] = dict({
                 "value": size / times[0], "unit": "candidates/s", "cores": cores, "kind": "oracle",
                 "sample": "candidates [%d, %d) of %s (%.1f s wall, all %d cores)" % (
-                    lo, lo + size, workload, times[0], cores)}
+                    lo, lo + size, workload, times[0], cores)}, **host_cpu())
         print(json.dumps(line), flush=True)
     m.motif_plan_destroy(plan)
     if world > 1:

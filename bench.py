@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--rates", default="1,2,5,10,20,50,100,200")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-step-tiles", type=int, default=0,
+                    help="serve mode: tile budget of one server step over all warps (0 = default)")
     return ap.parse_args()
 
 
@@ -544,7 +546,7 @@ def run_serve(args):
     for rate in [float(r) for r in args.rates.split(",")]:
         count = int(min(args.serve_jobs, max(20, rate * args.serve_seconds)))
         jobs = fmgen.serving_jobs(rate, count, seed=5)
-        m.motif_server_start(max_active=64)
+        m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
         # warm-up job (graph capture, ball tables, allocator pools)
         wj = fmgen.fm_job(10, 300, 11, 3, 1)
         pl = m.motif_plan_create(wj.n, wj.t, wj.l, wj.d)

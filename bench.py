@@ -45,6 +45,11 @@ LOP3_PER_SM_CLK = 64.0  # measured by the K4 probe (motif_probe_rate LOP3) on GB
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the tiled pass on the
 # (15,4) n=20 t=600 seed-2 workload (one --set full capture of the current kernel): 295.2 KB + 0 B.
 TILED_L15D4_DRAM_BYTES = 295168
+# The same capture's smsp__issue_active (the fraction of issue slots the kernel used) and
+# sm__inst_executed_pipe_alu (its busiest pipe): the factored kernel's own bound is instruction
+# issue, not the per-compare POPC rate.
+TILED_L15D4_ISSUE_ACTIVE = 0.573
+TILED_L15D4_ALU_PIPE = 0.575
 
 
 def parse():
@@ -353,6 +358,11 @@ def run_ours(args):
             "note": ("frac > 1: the %s kernel factors the Hamming distance over shared candidate "
                      "prefixes, so one POPC or bit test resolves many algorithmic compares; see "
                      "roofline_cand for the per-compare kernel" % kname) if kname != "CAND" else ""}
+    if kname == "TILED" and workload == "l15d4_n20_t600_seed2":
+        # its own bound, from the committed ncu capture of this kernel on this workload
+        roof["issue"] = {"issue_active_frac": TILED_L15D4_ISSUE_ACTIVE,
+                         "alu_pipe_frac": TILED_L15D4_ALU_PIPE,
+                         "source": "ncu --set full, one launch of this kernel on this workload"}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (POPC_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
     def per_candidate_leg(kernel, label, cpt):

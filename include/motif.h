@@ -97,7 +97,11 @@ typedef struct {
   int32_t cands_per_thread; /* CAND kernel: candidates a lane carries per fresh tile; 0 = tuned */
   int32_t compact_levels;   /* CAND kernel: sequences with a survivor queue; 0 = tuned */
   int32_t suffix_bases;     /* GROUP kernel: k, suffix bases enumerated in one lane; 0 = tuned */
-  int32_t timeout_ms;       /* bound on every device-side and host-side wait; 0 = 60000 */
+  int32_t timeout_ms;       /* bound on a polled step loop (batches without a graph, and the
+                               profiling mode that launches steps without one): past it the
+                               call returns MOTIF_ERR_TIMEOUT with nothing left in flight;
+                               0 = 60000.  A graph-launched search ends after its step bound
+                               (every chunk needs at most n passes) instead. */
   int32_t output;           /* motif_output */
   motif_alloc_fn alloc;     /* NULL = cudaMallocAsync / cudaFreeAsync on the plan's stream */
   motif_free_fn free;
@@ -268,7 +272,8 @@ typedef struct {
   int64_t device_budget;   /* bytes of device memory the admitted jobs may hold; 0 = 4 GiB */
   int32_t step_tiles;      /* candidate tiles per device step between admissions; 0 = tuned */
   int32_t use_graph;       /* != 0: replay the step launch from a CUDA graph */
-  int32_t timeout_ms;      /* bound on each device step; 0 = 60000 */
+  int32_t timeout_ms;      /* not used: each server step is bounded by step_tiles, and callers
+                              bound their waits with motif_poll's timeout_ms */
 } motif_server_opts;
 
 /* Starts the process-wide serving loop (a scheduler thread with its own stream).  opts may be

@@ -43,7 +43,9 @@ typedef enum {
   MOTIF_ERR_CAPACITY = -3,   /* more results than the output capacity; *out_count = required */
   MOTIF_ERR_OOM = -4,        /* a device or host allocation failed */
   MOTIF_ERR_CUDA = -5,       /* a CUDA runtime call failed (or no CUDA device is present) */
-  MOTIF_ERR_TIMEOUT = -6,    /* a bounded wait ran out (host poll or a device-side wait) */
+  MOTIF_ERR_TIMEOUT = -6,    /* a step loop reached its bound with work left: a polled loop
+                                past motif_opts.timeout_ms, or a graph-launched loop at its
+                                step bound */
   MOTIF_ERR_BUSY = -7,       /* the serving queue refused the job (queue full) */
   MOTIF_ERR_STATE = -8,      /* wrong call order, e.g. a search before sequences were loaded */
   MOTIF_ERR_NOTFOUND = -9    /* unknown job id */
@@ -61,8 +63,6 @@ typedef enum {
                                back to CAND otherwise) */
 } motif_kernel;
 
-/* How a search collects the accepted codes before returning them in ascending order (not in the
- * paper, whose output is the surviving l-mers, Sec. III.A; a GPU design choice). */
 /* Which candidates a search enumerates. */
 typedef enum {
   MOTIF_SEED_ALL = 0,           /* every index of the range (Sec. IV.A) */
@@ -75,6 +75,8 @@ typedef enum {
                                    most 2^24 of them */
 } motif_seed;
 
+/* How a search collects the accepted codes before returning them in ascending order (not in the
+ * paper, whose output is the surviving l-mers, Sec. III.A; a GPU design choice). */
 typedef enum {
   MOTIF_OUTPUT_AUTO = 0,   /* BITMAP where the expected survivors are dense, else LIST */
   MOTIF_OUTPUT_LIST = 1,   /* append codes to a list, then sort and deduplicate it */

@@ -271,8 +271,9 @@ int motif_tune_cache_load(const char* path);
 typedef struct {
   int32_t max_active;      /* jobs resident on the device at once; 0 = 64 */
   int32_t max_queued;      /* jobs waiting for admission before submit returns BUSY; 0 = 4096 */
-  int64_t device_budget;   /* bytes of device memory the admitted jobs may hold; 0 = 4 GiB */
-  int32_t step_tiles;      /* candidate tiles per device step between admissions; 0 = tuned */
+  int64_t device_budget;   /* bytes of device memory the admitted jobs may hold; 0 = 8 GiB */
+  int32_t step_tiles;      /* candidate tiles one device step may take over all its warps
+                              (admissions happen between steps); 0 = 48 per warp */
   int32_t use_graph;       /* != 0: replay the step launch from a CUDA graph */
   int32_t timeout_ms;      /* not used: each server step is bounded by step_tiles, and callers
                               bound their waits with motif_poll's timeout_ms */

@@ -133,3 +133,27 @@ def test_bad_block_is_rejected():
     with pytest.raises(m.MotifError) as e:
         _plan(job, seq_block=-2)
     assert e.value.status == m.ERR_ARG
+
+
+def test_split_across_chunks():
+    # (16,7) on 4 rows of 40 bases over [0, 2^31): two chunks of 2^22 groups, about 1.8 M
+    # accepted codes (bitmap output); the split and whole-tile passes must agree exactly, and the
+    # oracle must agree on ranges at both ends, across the chunk boundary at 2^30, and around
+    # the planted consensus (in the second chunk for this seed)
+    job = fmgen.fm_job(4, 40, 16, 7, 92)
+    cons = m.motif_encode(job.consensus)
+    assert (1 << 30) < cons < (1 << 31)
+    results = {}
+    for sb in (-1, 1, 2):
+        p = _plan(job, kernel=m.KERNEL_TILED, output=m.OUTPUT_BITMAP, seq_block=sb,
+                  range_lo=0, range_hi=1 << 31)
+        results[sb] = m.motif_search(p)
+        m.motif_plan_destroy(p)
+    assert results[-1].size > 1_000_000
+    assert np.array_equal(results[1], results[-1])
+    assert np.array_equal(results[2], results[-1])
+    full = results[-1]
+    for lo, hi in [(0, 1 << 14), ((1 << 30) - (1 << 13), (1 << 30) + (1 << 13)),
+                   (cons - (1 << 13), cons + (1 << 13)), ((1 << 31) - (1 << 14), 1 << 31)]:
+        ref, _ = oracle.search(job.rows(), 16, 7, lo=lo, hi=hi, threads=8)
+        assert np.array_equal(full[(full >= lo) & (full < hi)], ref), (lo, hi)

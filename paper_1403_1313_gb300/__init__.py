@@ -31,7 +31,7 @@ __all__ = [
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
     "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED", "KERNEL_BITSLICE",
     "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP", "SEED_ALL", "SEED_NEIGHBOURHOOD",
-    "motif_seed_count",
+    "motif_seed_count", "motif_sort_codes_noalloc",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -133,6 +133,7 @@ def _load():
             "motif_count_compares": (ctypes.c_int, [P, u64p]),
             "motif_count_work": (ctypes.c_int, [P, u64p, u64p]),
             "motif_seed_count": (ctypes.c_int, [P, u64p]),
+            "motif_sort_codes_noalloc": (ctypes.c_int, [P, i64, i32, P, P]),
             "motif_kernel_launches": (ctypes.c_uint64, []),
             "motif_stats": (ctypes.c_int, [P, ctypes.POINTER(motif_stats_t)]),
             "motif_batch_search": (ctypes.c_int, [i32, ctypes.POINTER(P), ctypes.POINTER(u64p), i64p, i64p, ctypes.POINTER(i32), i32]),
@@ -343,6 +344,20 @@ def motif_search_device(plan: Plan, d_out, capacity: int, d_count) -> None:
     pc = d_count.data_ptr() if hasattr(d_count, "data_ptr") else int(d_count)
     _check(_load().motif_search_device(plan, ctypes.c_void_p(po), capacity, ctypes.c_void_p(pc)),
            "motif_search_device")
+
+
+def motif_sort_codes_noalloc(d_codes, count: int, key_bits: int, d_unique_count,
+                             stream=None) -> None:
+    """Sorts `count` device codes ascending and drops repeats in place, without allocating
+    device memory; the number of distinct codes goes to d_unique_count (one int64).  Tensors
+    (int64/uint64 CUDA) or raw device pointers; stream: a torch stream, a raw handle or None."""
+    pc = d_codes.data_ptr() if hasattr(d_codes, "data_ptr") else int(d_codes)
+    pu = d_unique_count.data_ptr() if hasattr(d_unique_count, "data_ptr") else int(d_unique_count)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(_load().motif_sort_codes_noalloc(ctypes.c_void_p(pc), int(count), int(key_bits),
+                                            ctypes.c_void_p(pu),
+                                            ctypes.c_void_p(s) if s else None),
+           "motif_sort_codes_noalloc")
 
 
 def motif_seed_count(plan: Plan) -> int:

@@ -75,3 +75,19 @@ def test_noalloc_sort_rejects_too_many_codes(lib):
     assert st == m.ERR_ARG
     st = lib.motif_sort_codes_noalloc(fake, -1, 30, fake, None)
     assert st == m.ERR_ARG
+
+
+def test_noalloc_sort_through_the_binding(lib):
+    torch = pytest.importorskip("torch")
+    ref = _search_result(8, 3, seed=5)
+    mixed = np.concatenate([ref, ref[::-1]])
+    d_codes = torch.from_numpy(mixed.astype(np.int64)).cuda()
+    d_count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    m.motif_sort_codes_noalloc(d_codes, mixed.size, 16, d_count, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    cnt = int(d_count.item())
+    assert cnt == ref.size
+    assert np.array_equal(d_codes[:cnt].cpu().numpy().astype(np.uint64), ref)
+    with pytest.raises(m.MotifError) as e:  # rejected on the host, nothing launched
+        m.motif_sort_codes_noalloc(256, 5, 0, 256)
+    assert e.value.status == m.ERR_ARG

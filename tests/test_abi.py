@@ -98,3 +98,10 @@ def test_plan_create_rejects_bad_arguments():
 
 def test_version_names_the_target():
     assert "sm_103a" in m.motif_version()
+
+
+def test_every_declared_symbol_has_a_binding_of_its_name():
+    """The Python binding marshals arguments for every entry point, under the same name."""
+    missing = [n for n in _header_functions() if not callable(getattr(m, n, None))]
+    assert not missing, missing
+    assert set(_header_functions()) <= set(m.__all__)

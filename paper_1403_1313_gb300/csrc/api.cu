@@ -13,6 +13,42 @@
 
 #include "plan.h"
 
+// Codes a blocking search reads back speculatively with its count (one wait for small results).
+constexpr int64_t kResultPeek = 512;
+// A plan's pinned host block: the read-back words, then (16-byte aligned) the search descriptor.
+constexpr size_t kDescOffset = ((1 + kResultPeek) * sizeof(uint64_t) + 15) & ~(size_t)15;
+constexpr size_t kHostBlockBytes = kDescOffset + sizeof(motif::JobDesc);
+
+// Pinned host blocks of plans, shared by all plans of the process: the read-back words of a
+// blocking search ([1 + kResultPeek]) and then the descriptor a search uploads.  A plan takes
+// one at its first search and gives it back when destroyed, so plans that live for one search
+// do not pin and unpin memory each time.
+static std::mutex g_res_mu;
+static std::vector<uint64_t*> g_res_free;
+
+static uint64_t* take_result_block() {
+  {
+    std::lock_guard<std::mutex> g(g_res_mu);
+    if (!g_res_free.empty()) {
+      uint64_t* b = g_res_free.back();
+      g_res_free.pop_back();
+      return b;
+    }
+  }
+  uint64_t* b = nullptr;
+  if (cudaHostAlloc((void**)&b, kHostBlockBytes, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return b;
+}
+
+static void give_result_block(uint64_t* b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> g(g_res_mu);
+  g_res_free.push_back(b);
+}
+
 using motif::JobDesc;
 using motif::JobState;
 using motif::StepCtl;
@@ -239,13 +275,26 @@ int plan_configure(motif_plan_s* p) {
   p->want_qcap = chunk;
   p->want_qwords = words;
   invalidate_graphs(p);
+  // The prefix-tiled first pass (GROUP, k = 4): 256 lanes per CTA whose groups share all but
+  // their last 4 prefix bases, so tiles must start on multiples of 256 groups.
+  const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
+  const bool tiled_ok = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 &&
+                        p->l >= 8 && p->W <= 65535 && unit_lo % 256 == 0 &&
+                        (chunk % 256 == 0 || units <= chunk);
+  // Few tiles (< 64) that walk through most sequences (q > 0.52): alone, they would leave most
+  // of the GPU idle for the whole search.
+  const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
   // Output: a bitmap over the range (rounded out to whole 256-code groups) where it holds at
-  // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size.
+  // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size; and,
+  // for few long tiles, where it is small (at most 2^24 bits): the skip saves little in such
+  // tiles, and with a bitmap they split into (tile, sequence block) items that fill the GPU.
   const uint64_t bm_base = p->lo & ~255ull;
   const uint64_t bm_bits = ((p->hi + 255) & ~255ull) - bm_base;
   if (o.output < MOTIF_OUTPUT_AUTO || o.output > MOTIF_OUTPUT_BITMAP) return MOTIF_ERR_ARG;
   bool bitmap = o.output == MOTIF_OUTPUT_BITMAP ||
-                (o.output == MOTIF_OUTPUT_AUTO && expected_survivors(p) * 2048.0 >= (double)bm_bits);
+                (o.output == MOTIF_OUTPUT_AUTO &&
+                 (expected_survivors(p) * 2048.0 >= (double)bm_bits ||
+                  (tiled_ok && few_long_tiles && o.seq_block != -1 && bm_bits <= (1ull << 24))));
   if (bm_bits > (1ull << 31)) {
     if (o.output == MOTIF_OUTPUT_BITMAP) return MOTIF_ERR_ARG;
     bitmap = false;
@@ -253,12 +302,6 @@ int plan_configure(motif_plan_s* p) {
   p->bitmap = bitmap && p->hi > p->lo;
   p->bm_base = bm_base;
   p->bm_words = p->bitmap ? bm_bits / 32 : 0;
-  // The prefix-tiled first pass (GROUP, k = 4): 256 lanes per CTA whose groups share all but
-  // their last 4 prefix bases, so tiles must start on multiples of 256 groups.
-  const bool want_tiled = o.kernel == MOTIF_KERNEL_AUTO || o.kernel == MOTIF_KERNEL_TILED;
-  const bool tiled_ok = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 &&
-                        p->l >= 8 && p->W <= 65535 && unit_lo % 256 == 0 &&
-                        (chunk % 256 == 0 || units <= chunk);
   // With bitmap output the expected survivors (at least 1/2048 of the range: 32 per tile of
   // 65536 codes) keep every tile alive to the last sequence, so the skip saves nothing there and
   // a tile splits into (tile, sequence block) items at no extra work; the blocks are sized so
@@ -275,11 +318,9 @@ int plan_configure(motif_plan_s* p) {
       if (blocks > 1) p->seq_block = (int)((p->n + blocks - 1) / blocks);
     }
   }
-  // AUTO leaves the tiled pass out where a tile would walk through most sequences (q > 0.52)
-  // and there are too few tiles (< 64) to fill the GPU, unless the tiles split into sequence
-  // blocks: the per-group passes run those faster alone.  A batch runs its jobs side by side, so
-  // there every eligible AUTO job stays tiled.
-  const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
+  // AUTO leaves the tiled pass out for few long tiles that do not split into sequence blocks:
+  // the per-group passes run those faster alone.  A batch runs its jobs side by side, so there
+  // every eligible AUTO job stays tiled.
   p->tiled = tiled_ok && !(o.kernel == MOTIF_KERNEL_AUTO && few_long_tiles && p->seq_block == 0);
   p->tiled_in_batch = tiled_ok;
   // A split search runs on the step kernel variant that has the split; its occupancy decides the
@@ -540,9 +581,9 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   // Upload the descriptor when (out, cap) changed; it lives in pinned memory so the copy is
   // stream-ordered without blocking the host.
   if (p->desc_out != out || p->desc_cap != (int64_t)cap) {
-    if (!p->h_desc && cudaHostAlloc((void**)&p->h_desc, sizeof(JobDesc), 0) != cudaSuccess) {
-      p->h_desc = nullptr;
-      return MOTIF_ERR_OOM;
+    if (!p->h_desc) {  // the descriptor's place in the plan's pinned host block
+      if (!p->h_res && !(p->h_res = take_result_block())) return MOTIF_ERR_OOM;
+      p->h_desc = reinterpret_cast<JobDesc*>(reinterpret_cast<char*>(p->h_res) + kDescOffset);
     }
     cudaError_t e = cudaStreamSynchronize(p->stream);  // the previous upload has completed
     if (e != cudaSuccess) return status_from_cuda(e);
@@ -712,6 +753,7 @@ static void free_ragged(motif_plan p) {
   p->d_empty = nullptr;
 }
 
+
 void motif_plan_destroy(motif_plan p) {
   if (!p) return;
   DeviceGuard g(p->device);
@@ -735,10 +777,9 @@ void motif_plan_destroy(motif_plan p) {
   for (cudaEvent_t ev : p->evq)
     if (ev) cudaEventDestroy(ev);
   invalidate_graphs(p);
-  if (p->h_desc) cudaFreeHost(p->h_desc);
-  if (p->h_chars) cudaFreeHost(p->h_chars);
+  free(p->h_chars);
   if (p->h_chars_done) cudaEventDestroy(p->h_chars_done);
-  if (p->h_res) cudaFreeHost(p->h_res);
+  give_result_block(p->h_res);
   delete p;
 }
 
@@ -759,11 +800,11 @@ static int load_common(motif_plan p, bool sync_check, bool checked = false) {
   return sync_check && !checked ? check_alphabet(p) : MOTIF_OK;
 }
 
-// Host loads up to this size are validated on the host while they are copied into pinned
-// staging: a few microseconds, against a wait for the device's check.
+// Host loads up to this size are validated on the host while they are copied into the plan's
+// staging buffer: a few microseconds, against a wait for the device's check.
 constexpr size_t kHostCheckBytes = (size_t)1 << 16;
 
-// Copies the n rows into the plan's pinned staging buffer; false if a character is outside
+// Copies the n rows into the plan's staging buffer; false if a character is outside
 // ACGTacgt.
 static bool stage_checked(motif_plan_s* p, const char* seqs, int64_t stride) {
   static const std::array<uint8_t, 256> valid = [] {
@@ -790,14 +831,19 @@ int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride) {
   const size_t bytes = (size_t)p->n * p->t;
   if (bytes <= kHostCheckBytes) {
     cudaError_t e = cudaSuccess;
-    if (!p->h_chars) {
-      e = cudaHostAlloc((void**)&p->h_chars, bytes, 0);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->h_chars_done, cudaEventDisableTiming);
-      if (e != cudaSuccess) return status_from_cuda(e);
+    if (!p->h_chars_done) {
+      e = cudaEventCreateWithFlags(&p->h_chars_done, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        p->h_chars_done = nullptr;
+        return status_from_cuda(e);
+      }
     } else {
       e = cudaEventSynchronize(p->h_chars_done);  // the previous upload has read the staging
       if (e != cudaSuccess) return status_from_cuda(e);
     }
+    // plain host memory: pinning it would cost more than it saves on an upload of a few
+    // kilobytes, for plans that live for one search
+    if (!p->h_chars && !(p->h_chars = (char*)malloc(bytes))) return MOTIF_ERR_OOM;
     if (!stage_checked(p, seqs, stride)) return MOTIF_ERR_ALPHABET;
     e = cudaMemcpyAsync(p->d_chars, p->h_chars, bytes, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaEventRecord(p->h_chars_done, p->stream);
@@ -875,8 +921,7 @@ int motif_load_seqs_var(motif_plan p, const char* seqs, int64_t stride, const in
   return MOTIF_OK;
 }
 
-// Codes a blocking search reads back speculatively with its count (one wait for small results).
-constexpr int64_t kResultPeek = 512;
+
 
 int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* out_count) {
   if (!p || !out_count || capacity < 0 || (capacity > 0 && !out_codes)) return MOTIF_ERR_ARG;
@@ -898,20 +943,13 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
     p->stats.total_ms = now_ms() - t0;
     return MOTIF_OK;
   }
-  unsigned long long found = 0;
   cudaEvent_t* ev = next_event_quad(p);
   if (!ev) return MOTIF_ERR_CUDA;
   if (p->bitmap) return search_bitmap(p, out_codes, capacity, out_count, ev, t0);
   // List output: the steps and the sort graph run back to back, then one wait reads the final
   // count and, speculatively, the first codes.  A count above the buffer means the search
   // overflowed it (the sort leaves such a count alone): the buffer grows and the search reruns.
-  if (!p->h_res) {
-    cudaError_t e = cudaHostAlloc((void**)&p->h_res, (1 + kResultPeek) * sizeof(uint64_t), 0);
-    if (e != cudaSuccess) {
-      p->h_res = nullptr;
-      return status_from_cuda(e);
-    }
-  }
+  if (!p->h_res && !(p->h_res = take_result_block())) return MOTIF_ERR_OOM;
   unsigned long long final_count = 0;
   int64_t peek = 0;
   bool sorted = false;  // the graph's multi-CTA branch covers every count up to the buffer's

@@ -63,8 +63,8 @@ struct motif_plan_s {
   cudaGraphExec_t g_steps = nullptr;
   cudaGraphExec_t g_sort = nullptr;
   motif::JobDesc* h_desc = nullptr;  // pinned copy of the uploaded descriptor
-  // Pinned host staging: the characters of a small host load (validated while they are copied
-  // in, so the load need not wait for the device), and the final count plus the first codes of
+  // Host staging: the characters of a small host load (validated while they are copied in, so
+  // the load need not wait for the device), and, pinned, the final count plus the first codes of
   // a blocking search (read back with one wait).
   char* h_chars = nullptr;
   cudaEvent_t h_chars_done = nullptr;  // recorded after the staged characters' upload

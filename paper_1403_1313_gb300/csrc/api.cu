@@ -281,20 +281,24 @@ int plan_configure(motif_plan_s* p) {
   const bool tiled_ok = want_tiled && kind == MOTIF_KERNEL_GROUP && pv == 4 && block == 256 &&
                         p->l >= 8 && p->W <= 65535 && unit_lo % 256 == 0 &&
                         (chunk % 256 == 0 || units <= chunk);
-  // Few tiles (< 64) that walk through most sequences (q > 0.52): alone, they would leave most
-  // of the GPU idle for the whole search.
-  const bool few_long_tiles = units / 256 < 64 && match_probability(p) > 0.52;
+  // Tiles that walk through most sequences (q > 0.52), fewer than the grid's CTAs: alone, they
+  // leave the GPU partly idle for the whole search (few_long_tiles: fewer than 64, most of it).
+  const bool long_tiles = match_probability(p) > 0.52;
+  const bool few_long_tiles = long_tiles && units / 256 < 64;
+  const bool underfilled_long_tiles = long_tiles && units / 256 < (uint64_t)per_sm * p->sms;
   // Output: a bitmap over the range (rounded out to whole 256-code groups) where it holds at
   // most 2^31 bits and the expected survivors make a list at least 1/2048 of its size; and,
-  // for few long tiles, where it is small (at most 2^24 bits): the skip saves little in such
-  // tiles, and with a bitmap they split into (tile, sequence block) items that fill the GPU.
+  // for long tiles that do not fill the grid, where it is small (at most 2^24 bits): the skip
+  // saves little in such tiles, and with a bitmap they split into (tile, sequence block) items
+  // that fill the GPU.
   const uint64_t bm_base = p->lo & ~255ull;
   const uint64_t bm_bits = ((p->hi + 255) & ~255ull) - bm_base;
   if (o.output < MOTIF_OUTPUT_AUTO || o.output > MOTIF_OUTPUT_BITMAP) return MOTIF_ERR_ARG;
   bool bitmap = o.output == MOTIF_OUTPUT_BITMAP ||
                 (o.output == MOTIF_OUTPUT_AUTO &&
                  (expected_survivors(p) * 2048.0 >= (double)bm_bits ||
-                  (tiled_ok && few_long_tiles && o.seq_block != -1 && bm_bits <= (1ull << 24))));
+                  (tiled_ok && underfilled_long_tiles && o.seq_block != -1 &&
+                   bm_bits <= (1ull << 24))));
   if (bm_bits > (1ull << 31)) {
     if (o.output == MOTIF_OUTPUT_BITMAP) return MOTIF_ERR_ARG;
     bitmap = false;

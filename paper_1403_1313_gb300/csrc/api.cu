@@ -642,14 +642,22 @@ int search_bitmap(motif_plan_s* p, uint64_t* out_codes, int64_t capacity, int64_
   if (rc) return rc;
   cudaEventRecord(ev[1], p->stream);
   cudaEventRecord(ev[2], p->stream);
+  // One wait reads the count and, speculatively, the first codes (as the list path does).
+  if (!p->h_res && !(p->h_res = take_result_block())) return MOTIF_ERR_OOM;
   unsigned long long found = 0;
+  int64_t peek = 0;
   for (;;) {
     rc = compact_bitmap(p, p->d_out, p->out_cap);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(&found, &p->d_state->out_count, sizeof(found),
+    peek = std::min<int64_t>(std::min<int64_t>(p->out_cap, capacity), kResultPeek);
+    cudaError_t e = cudaMemcpyAsync(p->h_res, &p->d_state->out_count, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess && peek > 0)
+      e = cudaMemcpyAsync(p->h_res + 1, p->d_out, (size_t)peek * 8, cudaMemcpyDeviceToHost,
+                          p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
+    found = p->h_res[0];
     if (found <= (unsigned long long)p->out_cap) break;
     rc = ensure_out(p, (int64_t)found);
     if (rc) return rc;
@@ -663,7 +671,9 @@ int search_bitmap(motif_plan_s* p, uint64_t* out_codes, int64_t capacity, int64_
     p->stats.total_ms = now_ms() - t0;
     return MOTIF_ERR_CAPACITY;
   }
-  if (found) {
+  if ((int64_t)found <= peek) {
+    if (found) memcpy(out_codes, p->h_res + 1, (size_t)found * 8);
+  } else {
     cudaError_t e = cudaMemcpyAsync(out_codes, p->d_out, found * 8, cudaMemcpyDeviceToHost,
                                     p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

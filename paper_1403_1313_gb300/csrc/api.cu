@@ -347,6 +347,15 @@ int plan_configure(motif_plan_s* p) {
     if (p->npat > (1ull << 24) || bits > (1ull << 36)) return MOTIF_ERR_ARG;
     p->seed_words = std::max<uint64_t>(bits / 32, 1);
   }
+  // A plan that runs the tiled pass alone and in batches never uses the survivor queues (the
+  // tiled pass takes every sequence of a tile): its whole range is one chunk, so the pass does
+  // not stop at chunk boundaries, and its queues hold a single entry.
+  uint64_t plan_chunk = chunk;
+  if (p->tiled && p->tiled_in_batch && units > 0) {
+    plan_chunk = units;
+    if (p->qcap != 1) free_queues(p);
+    p->want_qcap = 1;
+  }
   p->kind = kind;
   p->p = pv;
   p->span0 = span0;
@@ -355,8 +364,8 @@ int plan_configure(motif_plan_s* p) {
   p->smem = smem;
   p->unit_lo = unit_lo;
   p->unit_hi = unit_hi;
-  p->chunk_units = chunk;
-  p->nchunks = units == 0 ? 0 : (units + chunk - 1) / chunk;
+  p->chunk_units = plan_chunk;
+  p->nchunks = units == 0 ? 0 : (units + plan_chunk - 1) / plan_chunk;
   p->rest_threshold = (uint64_t)256 * p->sms;
   if (kind == MOTIF_KERNEL_GROUP && !ball_table(p->device, pv, p->stream)) return MOTIF_ERR_CUDA;
   return MOTIF_OK;

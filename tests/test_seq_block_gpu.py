@@ -135,11 +135,11 @@ def test_bad_block_is_rejected():
     assert e.value.status == m.ERR_ARG
 
 
-def test_split_across_chunks():
-    # (16,7) on 4 rows of 40 bases over [0, 2^31): two chunks of 2^22 groups, about 1.8 M
-    # accepted codes (bitmap output); the split and whole-tile passes must agree exactly, and the
-    # oracle must agree on ranges at both ends, across the chunk boundary at 2^30, and around
-    # the planted consensus (in the second chunk for this seed)
+def test_split_over_a_large_range_and_served_chunks():
+    # (16,7) on 4 rows of 40 bases over [0, 2^31), about 1.8 M accepted codes (bitmap output):
+    # the split and whole-tile passes must agree exactly (a tiled plan takes the range as one
+    # chunk), the server (which cuts it into chunks of 2^20 groups) must agree too, and the
+    # oracle must agree on ranges at both ends, across 2^30, and around the planted consensus
     job = fmgen.fm_job(4, 40, 16, 7, 92)
     cons = m.motif_encode(job.consensus)
     assert (1 << 30) < cons < (1 << 31)
@@ -153,6 +153,15 @@ def test_split_across_chunks():
     assert np.array_equal(results[1], results[-1])
     assert np.array_equal(results[2], results[-1])
     full = results[-1]
+    try:
+        p = _plan(job, kernel=m.KERNEL_TILED, output=m.OUTPUT_BITMAP, seq_block=1,
+                  range_lo=0, range_hi=1 << 31)
+        jid = m.motif_submit(p)
+        m.motif_plan_destroy(p)
+        served, _ = m.motif_poll(jid, timeout_ms=120000, capacity=full.size)
+        assert np.array_equal(served, full)
+    finally:
+        m.motif_server_stop()
     for lo, hi in [(0, 1 << 14), ((1 << 30) - (1 << 13), (1 << 30) + (1 << 13)),
                    (cons - (1 << 13), cons + (1 << 13)), ((1 << 31) - (1 << 14), 1 << 31)]:
         ref, _ = oracle.search(job.rows(), 16, 7, lo=lo, hi=hi, threads=8)

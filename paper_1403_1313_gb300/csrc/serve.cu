@@ -630,6 +630,11 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   j->words = mask_words(j->pv);
   j->tiled = j->pv == 4 && j->l >= 8 && j->W <= 65535 && j->unit_lo % 256 == 0 &&
              (j->chunk_units % 256 == 0 || units <= j->chunk_units);
+  if (j->tiled && units > 0) {  // the tiled pass uses no queues: one chunk, one-entry queues
+    j->chunk_units = units;
+    j->nchunks = j->W <= 0 || p->empty_row ? 0 : 1;
+    j->qcap = 1;
+  }
   if (p->bitmap) {  // the plan's output choice: dense results go to a bitmap over the range
     j->bm_base = p->bm_base;
     j->bm_words = p->bm_words;

@@ -135,11 +135,11 @@ def test_bad_block_is_rejected():
     assert e.value.status == m.ERR_ARG
 
 
-def test_split_over_a_large_range_and_served_chunks():
+def test_split_over_a_large_range_and_served():
     # (16,7) on 4 rows of 40 bases over [0, 2^31), about 1.8 M accepted codes (bitmap output):
-    # the split and whole-tile passes must agree exactly (a tiled plan takes the range as one
-    # chunk), the server (which cuts it into chunks of 2^20 groups) must agree too, and the
-    # oracle must agree on ranges at both ends, across 2^30, and around the planted consensus
+    # the split and whole-tile passes must agree exactly (a tiled pass takes the range as one
+    # chunk), the served job must agree too, and the oracle must agree on ranges at both ends,
+    # across 2^30, and around the planted consensus
     job = fmgen.fm_job(4, 40, 16, 7, 92)
     cons = m.motif_encode(job.consensus)
     assert (1 << 30) < cons < (1 << 31)

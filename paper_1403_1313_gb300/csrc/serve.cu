@@ -25,6 +25,8 @@ using namespace motif;
 
 namespace motif_serve {
 
+// Chunk of a served job's per-group passes (its survivor queues hold one chunk); a tiled job
+// takes its whole range as one chunk, since the tiled pass uses no queues.
 constexpr uint64_t kServeChunkGroups = 1ull << 20;
 
 struct Job {

@@ -72,8 +72,8 @@ def parse():
     ap.add_argument("--cand-subrange", type=int, default=1 << 27,
                     help="candidates of the roofline_cand sub-range run (0 = skip)")
     ap.add_argument("--mode", choices=["single", "batch", "serve", "cpu-scaling"], default="single",
-                    help="single: the driver's (l,d) line; batch: 64 uneven jobs batched vs one "
-                         "job per launch; serve: Poisson arrivals, p50/p99 latency per rate")
+                    help="single: one (l,d) search workload, the JSON line; batch: 64 uneven "
+                         "jobs batched vs one job per launch; serve: Poisson arrivals, p50/p99 latency per rate")
     ap.add_argument("--rates", default="1,2,5,10,20,50,100,200")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-jobs", type=int, default=200)

@@ -776,6 +776,63 @@ __device__ __forceinline__ void group_and_bitmap(const JobDesc& jd, uint64_t g,
     if (~alive.w[i]) atomicAnd(w + i, (unsigned long long)alive.w[i]);
 }
 
+// Phase 1 of the tiled pass for l <= 16, four windows per lane: the first l - 8 bases of a
+// window are byte 1 of its planes, so the lane packs the prefix planes of windows j0..j0+3 into
+// one byte each and counts the mismatches with the tile's prefix for all four at once (a
+// byte-wise popcount).  Windows within d - 1 are listed, windows at exactly d mark the map, as
+// in the one-window form.  Every slot below the row stride holds a window of the row (padding
+// repeats one), so the last lane group reads no further than the stride and a repeated window
+// only repeats an entry.  P1E4 / P1O4: the tile's prefix planes in every byte.
+__device__ __forceinline__ void filter_packed4(const uint2* __restrict__ row,
+                                               const uint64_t* __restrict__ crow, int W, int d,
+                                               uint32_t P1E4, uint32_t P1O4, uint32_t* head,
+                                               uint32_t* map, unsigned* cnt, int tid) {
+  const int lane = tid & 31;
+  const uint4* row4 = reinterpret_cast<const uint4*>(row);
+  const uint32_t over_d = (0x7Fu - (uint32_t)d) * 0x01010101u;  // bit 7 of a byte: count > d
+  const uint32_t at_d = (0x80u - (uint32_t)d) * 0x01010101u;     // bit 7 of a byte: count >= d
+  const unsigned lt = (1u << lane) - 1u;
+  for (int b = 0; b < W; b += 1024) {
+    const int j0 = b + 4 * tid;
+    uint32_t pass = 0, cnt4 = 0;
+    if (j0 < W) {
+      const uint4 a = __ldg(row4 + (j0 >> 1));      // windows j0, j0+1: E, O, E, O
+      const uint4 c = __ldg(row4 + (j0 >> 1) + 1);  // windows j0+2, j0+3
+      const uint32_t e4 = __byte_perm(__byte_perm(a.x, a.z, 0x0051u),
+                                      __byte_perm(c.x, c.z, 0x0051u), 0x5410u);
+      const uint32_t o4 = __byte_perm(__byte_perm(a.y, a.w, 0x0051u),
+                                      __byte_perm(c.y, c.w, 0x0051u), 0x5410u);
+      uint32_t x = (e4 ^ P1E4) | (o4 ^ P1O4);  // byte k: the mismatch mask of window j0+k
+      x = x - ((x >> 1) & 0x55555555u);
+      x = (x & 0x33333333u) + ((x >> 2) & 0x33333333u);
+      cnt4 = (x + (x >> 4)) & 0x0F0F0F0Fu;     // byte k: its mismatch count (at most 8)
+      pass = ~(cnt4 + over_d) & 0x80808080u;  // count <= d
+    }
+    const uint32_t keep = pass & ~(cnt4 + at_d);  // count < d: r1 > 0, listed
+    const int nk = __popc(keep);
+    // exclusive prefix of the lanes' listed counts (0..4) from the three bits of each count
+    const unsigned b0 = __ballot_sync(kFull, nk & 1), b1 = __ballot_sync(kFull, nk & 2),
+                   b2 = __ballot_sync(kFull, nk & 4);
+    const int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+    unsigned wb = 0;
+    if (lane == 0 && total) wb = atomicAdd(cnt, (unsigned)total);
+    unsigned slot = __shfl_sync(kFull, wb, 0) + __popc(b0 & lt) + 2 * __popc(b1 & lt) +
+                    4 * __popc(b2 & lt);
+    while (pass) {
+      const int bit = __ffs(pass) - 1;
+      pass &= pass - 1;
+      const int k = bit >> 3;
+      const uint32_t v = (uint32_t)__ldg(crow + j0 + k) & 0xFFFFu;  // P2 code << 8 | suffix
+      const int r1 = d - (int)((cnt4 >> (8 * k)) & 0xFu);
+      if (r1 == 0) {
+        atomicOr(map + (v >> 5), 1u << (v & 31u));  // one candidate
+      } else {
+        head[slot++] = (uint32_t)(r1 < 15 ? r1 : 15) | (v << 4);
+      }
+    }
+  }
+}
+
 // One item of the tiled pass.  SPLIT = false: the tile at group offset tbase, walked through
 // every sequence, its survivors appended (or ORed into the bitmap).  SPLIT = true: the tile and
 // the sequences [s_begin, s_end), its survivors ANDed into the bitmap.
@@ -806,6 +863,10 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     //    barrier that precedes this phase)
     const uint2* row = jd.planes + (size_t)s * wcap;
     const uint64_t* crow = jd.codes + (size_t)s * wcap;
+    if (jd.l <= 16)
+      filter_packed4(row, crow, jd.W, jd.d, P1E * 0x01010101u, P1O * 0x01010101u, head, map,
+                     cnt, tid);
+    else
     for (int b = 0; b < jd.W; b += 256) {
       const int j = b + tid;
       bool keep = false;

@@ -726,7 +726,8 @@ __device__ void group_rest(const JobDesc& jd, JobState* st, const Pass& p, unsig
 //      h1 <= d can match any of the tile's 65536 candidates.  A window with h1 = d matches
 //      exactly one of them (its own last 8 bases), so its lane sets that bit in a 65536-bit map
 //      of the tile in shared memory.  The other windows are compacted into a list of head words
-//      (r1 = d - h1, the window's P2 and suffix codes);
+//      (r1 = d - h1, the window's P2 and suffix codes).  For l <= 16 a lane filters four
+//      windows at once (filter_packed4), otherwise one;
 //   2. after one barrier each lane ORs its 256 bits of the map into its matched mask and clears
 //      them; then, 32 listed entries at a time, each warp loads its 32-bit word of each entry's
 //      4-base ball-table row (the P2 values within min(r1, 4) of the window's) and transposes

@@ -137,6 +137,34 @@ def test_tiled_every_window_listed(l, d, n, t):
     assert cmp == ref_cmp
 
 
+@pytest.mark.parametrize("l,d,t", [(16, 5, 17), (16, 5, 1043), (16, 2, 1046), (16, 8, 40),
+                                   (17, 5, 1045), (17, 6, 19), (13, 4, 1042)])
+def test_tiled_prefix_filter_edges(l, d, t):
+    """The tiled pass's prefix filter: l = 16 (the longest prefix it compares four windows per
+    lane, a whole byte per window) and l = 17 (one window per lane); rows of 2 and 3 windows and
+    of just over 1024 (a second trip of the four-window loop), with every remainder mod 4; d at
+    the prefix length (every window passes).  Ranges: the two tiles from the planted
+    consensus's tile, and two tiles from a random tile."""
+    job = fmgen.fm_job(3, t, l, d, 400 + 8 * l + d)
+    tile = 4 ** 8
+    cons = m.motif_encode(job.consensus)
+    rng = random.Random(t)
+    for lo in (cons // tile * tile, tile * rng.randrange(4 ** l // tile)):
+        hi = min(4 ** l, lo + 2 * tile)
+        ref, ref_cmp = oracle.search(job.rows(), l, d, lo=lo, hi=hi, threads=8)
+        plan = m.motif_plan_create(3, t, l, d, _opts(kernel=m.KERNEL_TILED, range_lo=lo,
+                                                     range_hi=hi))
+        m.motif_load_seqs(plan, job.seqs)
+        got = m.motif_search(plan)
+        assert m.motif_stats(plan)["kernel"] == m.KERNEL_TILED
+        cmp = m.motif_count_compares(plan)
+        m.motif_plan_destroy(plan)
+        assert np.array_equal(got, ref), (lo, hi)
+        assert cmp == ref_cmp
+        if lo == cons // tile * tile:
+            assert cons in set(ref.tolist())  # the planted consensus lies in the range
+
+
 # ---- edge cases ---------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name,kw", VARIANTS, ids=[v[0] for v in VARIANTS])

@@ -864,29 +864,30 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     //    barrier that precedes this phase)
     const uint2* row = jd.planes + (size_t)s * wcap;
     const uint64_t* crow = jd.codes + (size_t)s * wcap;
-    if (jd.l <= 16)
+    if (jd.l <= 16) {
       filter_packed4(row, crow, jd.W, jd.d, P1E * 0x01010101u, P1O * 0x01010101u, head, map,
                      cnt, tid);
-    else
-    for (int b = 0; b < jd.W; b += 256) {
-      const int j = b + tid;
-      bool keep = false;
-      uint32_t e = 0;
-      if (j < jd.W) {
-        const uint2 w = __ldg(row + j);
-        const int r1 = jd.d - __popc(((w.x >> 8) ^ P1E) | ((w.y >> 8) ^ P1O));
-        if (r1 >= 0) {
-          const uint32_t v = (uint32_t)__ldg(crow + j) & 0xFFFFu;  // P2 code << 8 | suffix
-          if (r1 == 0) atomicOr(map + (v >> 5), 1u << (v & 31u));   // one candidate
-          keep = r1 > 0;
-          e = (uint32_t)(r1 < 15 ? r1 : 15) | (v << 4);
+    } else {  // one window per lane
+      for (int b = 0; b < jd.W; b += 256) {
+        const int j = b + tid;
+        bool keep = false;
+        uint32_t e = 0;
+        if (j < jd.W) {
+          const uint2 w = __ldg(row + j);
+          const int r1 = jd.d - __popc(((w.x >> 8) ^ P1E) | ((w.y >> 8) ^ P1O));
+          if (r1 >= 0) {
+            const uint32_t v = (uint32_t)__ldg(crow + j) & 0xFFFFu;  // P2 code << 8 | suffix
+            if (r1 == 0) atomicOr(map + (v >> 5), 1u << (v & 31u));   // one candidate
+            keep = r1 > 0;
+            e = (uint32_t)(r1 < 15 ? r1 : 15) | (v << 4);
+          }
         }
+        const unsigned bal = __ballot_sync(kFull, keep);
+        unsigned wb = 0;
+        if (lane == 0 && bal) wb = atomicAdd(cnt, (unsigned)__popc(bal));
+        wb = __shfl_sync(kFull, wb, 0);
+        if (keep) head[wb + __popc(bal & ((1u << lane) - 1u))] = e;
       }
-      const unsigned bal = __ballot_sync(kFull, keep);
-      unsigned wb = 0;
-      if (lane == 0 && bal) wb = atomicAdd(cnt, (unsigned)__popc(bal));
-      wb = __shfl_sync(kFull, wb, 0);
-      if (keep) head[wb + __popc(bal & ((1u << lane) - 1u))] = e;
     }
     if (tid == 0) s_cnt[(s + 1) & 1] = 0;  // the next sequence's list count
     __syncthreads();

@@ -283,8 +283,11 @@ typedef struct {
  * NULL.  MOTIF_ERR_STATE if it is already running. */
 int motif_server_start(const motif_server_opts* opts);
 
-/* Stops the serving loop after the jobs in flight finish; pending unfinished jobs fail with
- * MOTIF_ERR_STATE at their next poll. */
+/* Stops the serving loop.  The scheduler first runs every submitted job, queued or active, to
+ * completion; then the server is released together with the jobs it still holds (results not
+ * yet polled are discarded), and their IDs are unknown afterwards (motif_poll returns
+ * MOTIF_ERR_NOTFOUND).  It does not wait for motif_submit or motif_poll calls of other threads:
+ * call it once no other thread is inside either.  MOTIF_ERR_STATE if no server is running. */
 int motif_server_stop(void);
 
 /* Submits the loaded plan as a job (starting the loop with defaults if needed).  The plan's

@@ -448,6 +448,8 @@ def motif_server_start(max_active=0, max_queued=0, device_budget=0, step_tiles=0
 
 
 def motif_server_stop() -> None:
+    """Runs every submitted job to completion, then releases the server and the results not yet
+    polled.  Call it once no other thread is inside motif_submit or motif_poll."""
     _check(_load().motif_server_stop(), "motif_server_stop")
 
 

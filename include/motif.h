@@ -156,10 +156,12 @@ void motif_plan_destroy(motif_plan p);
 
 /* Copies n rows of t characters (row r at seqs + r*stride, stride >= t) to the device and
  * packs every window into its 2l-bit code (a 64-bit word) and two l-bit planes (the low and
- * the high bit of every base, one 32-bit word each).  Blocking; the
- * characters are validated and a character outside ACGTacgt returns MOTIF_ERR_ALPHABET
- * (the plan then holds no sequences).  Errors: MOTIF_ERR_ARG, MOTIF_ERR_ALPHABET,
- * MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
+ * the high bit of every base, one 32-bit word each).  Returns once the characters are
+ * validated and the caller's buffer may be reused: a load of at most 64 KB is checked and
+ * staged on the host (its upload and packing may still be in flight on the plan's stream); a
+ * larger one is checked on the device before the return.  A character outside ACGTacgt returns
+ * MOTIF_ERR_ALPHABET (the plan then holds no sequences).
+ * Errors: MOTIF_ERR_ARG, MOTIF_ERR_ALPHABET, MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
 int motif_load_seqs(motif_plan p, const char* seqs, int64_t stride);
 
 /* Same as motif_load_seqs for characters already in device memory (d_seqs, row stride

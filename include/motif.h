@@ -294,7 +294,10 @@ int motif_server_stop(void);
 
 /* Submits the loaded plan as a job (starting the loop with defaults if needed).  The plan's
  * packed windows are copied, so the plan may be reused or destroyed after this returns.
- * *job_id receives the job id.  Errors: MOTIF_ERR_STATE (no sequences), MOTIF_ERR_BUSY. */
+ * *job_id receives the job id.  Errors: MOTIF_ERR_ARG (NULL arguments, or a plan on another
+ * device than the running server), MOTIF_ERR_STATE (no sequences), MOTIF_ERR_ALPHABET (an
+ * invalid character from motif_load_seqs_device; the plan then holds no sequences),
+ * MOTIF_ERR_BUSY (max_queued jobs already wait), MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
 int motif_submit(motif_plan p, int64_t* job_id);
 
 /* Waits up to timeout_ms (0 = do not wait) for the job.  Returns MOTIF_PENDING while it runs;

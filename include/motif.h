@@ -302,7 +302,10 @@ int motif_submit(motif_plan p, int64_t* job_id);
 
 /* Waits up to timeout_ms (0 = do not wait) for the job.  Returns MOTIF_PENDING while it runs;
  * on completion writes the codes by motif_search's rules and releases the job (on
- * MOTIF_ERR_CAPACITY the job stays so that it can be polled again).  stats may be NULL. */
+ * MOTIF_ERR_CAPACITY the job stays so that it can be polled again).  stats may be NULL.
+ * Errors: MOTIF_ERR_ARG, MOTIF_ERR_NOTFOUND (an unknown or already released id, or no server
+ * running), MOTIF_ERR_CAPACITY, and a failed job's own status (MOTIF_ERR_OOM when it can never
+ * fit the device budget, MOTIF_ERR_CUDA), after which the job is released. */
 int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity, int64_t* out_count,
                int32_t timeout_ms, motif_stats_t* stats);
 

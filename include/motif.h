@@ -264,7 +264,9 @@ int motif_batch_search(int32_t njobs, const motif_plan* plans, uint64_t* const* 
  * and copies it into *best when best != NULL.  budget_ms bounds the tuning time. */
 int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best);
 
-/* Saves / loads the process-wide tuning cache as JSON. */
+/* Saves / loads the process-wide tuning cache as JSON.  MOTIF_ERR_ARG when path is NULL or
+ * the file cannot be opened; loading skips entries it cannot parse and entries outside the
+ * option rules (kernel, block, candidates per lane, suffix bases, negative counts). */
 int motif_tune_cache_save(const char* path);
 int motif_tune_cache_load(const char* path);
 
@@ -313,7 +315,9 @@ int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity, int64_t* o
 
 /* Splits the candidate space [0, total) into `world` contiguous ranges with sizes in
  * proportion to weights[0..world) (NULL = equal) and returns rank's [*lo, *hi).  Concatenating
- * the per-rank ascending results in rank order gives the global ascending result. */
+ * the per-rank ascending results in rank order gives the global ascending result.
+ * Errors: MOTIF_ERR_ARG (world < 1, rank outside [0, world), NULL lo or hi, a negative or NaN
+ * weight, weights summing to zero). */
 int motif_shard_range(uint64_t total, int32_t rank, int32_t world, const double* weights,
                       uint64_t* lo, uint64_t* hi);
 
@@ -321,10 +325,12 @@ int motif_shard_range(uint64_t total, int32_t rank, int32_t world, const double*
 
 const char* motif_strerror(int status);
 
-/* Encodes the first l characters of s (ACGTacgt) into a 2l-bit code (layout above). */
+/* Encodes the first l characters of s (ACGTacgt) into a 2l-bit code (layout above).
+ * Errors: MOTIF_ERR_ARG (NULL pointers, l outside [1, 31]), MOTIF_ERR_ALPHABET. */
 int motif_encode(const char* s, int32_t l, uint64_t* code);
 
-/* Decodes a 2l-bit code into l characters (no terminator written). */
+/* Decodes a 2l-bit code into l characters (no terminator written).
+ * Errors: MOTIF_ERR_ARG (NULL out, l outside [1, 31], a code of 4^l or more). */
 int motif_decode(uint64_t code, int32_t l, char* out);
 
 /* K4 issue-rate probes: operations per SM per clock of one instruction class, measured with
@@ -343,6 +349,9 @@ typedef enum {
   MOTIF_PROBE_COUNT = 10
 } motif_probe_kind;
 
+/* Runs probe `kind` for `iters` loop trips: *ops_per_sm_clk receives its rate and, when
+ * sm_cycles != NULL, *sm_cycles the SM cycles it took.  Errors: MOTIF_ERR_ARG, MOTIF_ERR_OOM,
+ * MOTIF_ERR_CUDA. */
 int motif_probe_rate(int32_t kind, int32_t iters, double* ops_per_sm_clk, double* sm_cycles);
 
 /* ---- ordering codes without allocating ------------------------------------------------------ */

@@ -352,6 +352,17 @@ std::string key_of(const motif_plan_s* p) {
   return buf;
 }
 
+// A loaded entry is kept only within the option rules every plan checks (kernel, block,
+// candidates per lane, suffix bases, non-negative counts), so a damaged cache file cannot make
+// the plans it matches fail.
+bool choice_ok(const Choice& c) {
+  return c.kernel >= MOTIF_KERNEL_AUTO && c.kernel <= MOTIF_KERNEL_BITSLICE && c.block >= 0 &&
+         c.block <= 256 && c.block % 32 == 0 && c.ctas_per_sm >= 0 &&
+         (c.cands_per_thread == 0 || c.cands_per_thread == 1 || c.cands_per_thread == 2 ||
+          c.cands_per_thread == 4) &&
+         c.compact_levels >= 0 && c.suffix_bases >= 0 && c.suffix_bases <= motif::kMaxKs;
+}
+
 void apply(motif_opts* o, const Choice& c) {
   o->kernel = c.kernel;
   o->block = c.block;
@@ -476,7 +487,8 @@ extern "C" int motif_tune_cache_load(const char* path) {
                "\"cands_per_thread\": %d, \"compact_levels\": %d, \"suffix_bases\": %d, "
                "\"cand_per_s\": %lf",
                key, &c.kernel, &c.block, &c.ctas_per_sm, &c.cands_per_thread, &c.compact_levels,
-               &c.suffix_bases, &c.cand_per_s) == 8)
+               &c.suffix_bases, &c.cand_per_s) == 8 &&
+        choice_ok(c))
       g_cache[key] = c;
   }
   fclose(f);

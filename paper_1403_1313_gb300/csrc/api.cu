@@ -1191,14 +1191,18 @@ int motif_shard_range(uint64_t total, int32_t rank, int32_t world, const double*
     sum += w;
   }
   if (!(sum > 0)) return MOTIF_ERR_ARG;
-  // Boundaries at floor(total * cumulative_weight / sum), computed in long double; the last
-  // boundary is exactly total.
+  // Boundary r at floor(total * (w_0 + ... + w_{r-1}) / sum); the last one is exactly total.
+  // Equal weights: exact in 128-bit integers.  Given weights: IEEE double arithmetic, which
+  // rounds alike on every host, and is monotone in r, so the ranges stay contiguous.
   auto cut = [&](int r) -> uint64_t {
     if (r >= world) return total;
-    long double acc = 0;
-    for (int i = 0; i < r; ++i) acc += weights ? weights[i] : 1.0;
-    long double v = (long double)total * acc / (long double)sum;
-    uint64_t c = (uint64_t)v;
+    if (!weights) return (uint64_t)((unsigned __int128)total * (uint32_t)r / (uint32_t)world);
+    double acc = 0;
+    for (int i = 0; i < r; ++i) acc += weights[i];
+    if (acc >= sum) return total;  // only zero weights follow: they get empty ranges
+    const double v = (double)total * (acc / sum);
+    if (!(v < 18446744073709551616.0)) return total;
+    const uint64_t c = (uint64_t)v;
     return c > total ? total : c;
   };
   *lo = cut(rank);

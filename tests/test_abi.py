@@ -68,6 +68,11 @@ def test_encode_decode_roundtrip():
     assert e.value.status == m.ERR_ALPHABET
     with pytest.raises(m.MotifError):
         m.motif_decode(1 << 10, 4)  # more than 2l bits
+    for bad in (lambda: m.motif_encode("A" * 32), lambda: m.motif_encode(""),
+                lambda: m.motif_decode(0, 32), lambda: m.motif_decode(0, 0)):
+        with pytest.raises(m.MotifError) as e:  # l outside [1, 31]
+            bad()
+        assert e.value.status == m.ERR_ARG
 
 
 @pytest.mark.parametrize("world", [1, 2, 3, 7])

@@ -84,6 +84,20 @@ typedef enum {
                               order; needs (range length)/8 bytes of device memory */
 } motif_output;
 
+/* How a search launches its step kernel (not in the paper; a GPU design choice). */
+typedef enum {
+  MOTIF_LAUNCH_GRAPH = 0,  /* one CUDA graph launch per search: an init kernel, then a
+                              conditional while node whose body is the step kernel, so no host
+                              round trip separates the passes */
+  MOTIF_LAUNCH_DIRECT = 1  /* the step kernel launched from the host once per step (a blocking
+                              search polls the job state between groups of steps; a device
+                              search launches the step bound).  Same kernels, same result; it
+                              lets profilers, which do not list kernels inside conditional graph
+                              nodes, see every step launch.  The environment variable
+                              MOTIF_NO_GRAPH, set at the first search of a process, selects it
+                              for every plan */
+} motif_launch;
+
 typedef struct motif_plan_s* motif_plan;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a device
@@ -115,6 +129,8 @@ typedef struct {
                                (a tile and a block of sequences, ANDed into the bitmap); 0 =
                                chosen so the items fill the GPU, -1 = one item walks a tile
                                through every sequence */
+  int32_t launch;           /* motif_launch (searches of this plan alone; a batch or a server
+                               launches its own graphs) */
 } motif_opts;
 
 typedef struct {
@@ -346,7 +362,10 @@ typedef enum {
   MOTIF_PROBE_CMP_SPLIT = 7,   /* split-plane window compares */
   MOTIF_PROBE_CMP_FOLD = 8,    /* folded window compares */
   MOTIF_PROBE_LDS64_DIV = 9,   /* 64-bit shared loads at distinct conflict-free addresses */
-  MOTIF_PROBE_COUNT = 10
+  MOTIF_PROBE_ATOMS_OR = 10,   /* 32-bit shared-memory atomic ORs (result unused), every lane of
+                                  a warp on its own bank */
+  MOTIF_PROBE_SHFL = 11,       /* warp butterfly shuffles (shfl.sync.bfly.b32) */
+  MOTIF_PROBE_COUNT = 12
 } motif_probe_kind;
 
 /* Runs probe `kind` for `iters` loop trips: *ops_per_sm_clk receives its rate and, when

@@ -31,6 +31,7 @@ __all__ = [
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
     "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED", "KERNEL_BITSLICE",
     "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP", "SEED_ALL", "SEED_NEIGHBOURHOOD",
+    "LAUNCH_GRAPH", "LAUNCH_DIRECT",
     "motif_seed_count", "motif_sort_codes_noalloc",
 ]
 
@@ -45,9 +46,10 @@ ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_NOTFOUND = -5, -6, -7, -8, -9
 KERNEL_AUTO, KERNEL_CAND, KERNEL_GROUP, KERNEL_TILED, KERNEL_BITSLICE = 0, 1, 2, 3, 4
 OUTPUT_AUTO, OUTPUT_LIST, OUTPUT_BITMAP = 0, 1, 2
 SEED_ALL, SEED_NEIGHBOURHOOD = 0, 1
+LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1
 
 PROBE_KINDS = ["POPC", "LOP3", "IMNMX", "SHF", "IADD", "IMAD", "POPC_LOP3", "CMP_SPLIT",
-               "CMP_FOLD", "LDS64_DIV"]
+               "CMP_FOLD", "LDS64_DIV", "ATOMS_OR", "SHFL"]
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -62,6 +64,7 @@ class motif_opts(ctypes.Structure):
         ("free", _FREE_FN),
         ("alloc_ctx", ctypes.c_void_p), ("range_lo", ctypes.c_uint64),
         ("range_hi", ctypes.c_uint64), ("seed", ctypes.c_int32), ("seq_block", ctypes.c_int32),
+        ("launch", ctypes.c_int32),
     ]
 
 

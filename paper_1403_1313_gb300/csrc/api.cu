@@ -611,7 +611,7 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   // list kernels inside conditional graph nodes); the blocking path polls, the device path
   // launches the step bound blindly.
   static const bool no_graph = getenv("MOTIF_NO_GRAPH") != nullptr;
-  if (no_graph) {
+  if (no_graph || p->opts.launch == MOTIF_LAUNCH_DIRECT) {
     cudaError_t e = launch_init_steps(p->d_state, 1, p->d_ctl, 0, 0, 0, p->stream);
     if (e != cudaSuccess) return status_from_cuda(e);
     return run_steps(p->lkind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid, p->block, p->smem,
@@ -737,6 +737,10 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
   p->lo = p->opts.range_lo;
   p->hi = p->opts.range_hi ? p->opts.range_hi : space;
   if (p->hi > space || p->lo > p->hi) { delete p; return MOTIF_ERR_ARG; }
+  if (p->opts.launch != MOTIF_LAUNCH_GRAPH && p->opts.launch != MOTIF_LAUNCH_DIRECT) {
+    delete p;
+    return MOTIF_ERR_ARG;
+  }
   p->stream = (cudaStream_t)p->opts.stream;
   cudaError_t e = cudaGetDevice(&p->device);
   cudaDeviceProp prop;

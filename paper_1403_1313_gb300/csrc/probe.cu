@@ -104,6 +104,18 @@ probe_kernel(uint32_t seed, int iters, long long* cycles, uint32_t* sink) {
         mn[c] = min(mn[c], (uint32_t)__popc((x2 | (x2 >> 1)) & 0x55555555u));
         mn[c] = min(mn[c], (uint32_t)__popc((x3 | (x3 >> 1)) & 0x55555555u));
       }
+    } else if (KIND == MOTIF_PROBE_ATOMS_OR) {
+      // Shared-memory atomic ORs, result unused: word c * 1024 + tid (mod the array) puts every
+      // lane of a warp on its own bank and no two threads on one word within a chain.
+      uint32_t* wv = reinterpret_cast<uint32_t*>(win);
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        atomicOr(wv + (((c & 3) * 1024 + tid) & (kProbeSmemWords - 1)), r[c] + (uint32_t)it);
+    } else if (KIND == MOTIF_PROBE_SHFL) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) r[c] = __shfl_xor_sync(0xffffffffu, r[c], 1 << (c & 3));
     } else if (KIND == MOTIF_PROBE_LDS64_DIV) {
       // Per-thread 64-bit shared loads at distinct, bank-conflict-free addresses.
       const uint2* w2 = reinterpret_cast<const uint2*>(win);
@@ -142,6 +154,7 @@ double ops_per_iter(int kind) {
     case MOTIF_PROBE_CMP_SPLIT: return 8.0 * 2.0;   // window compares
     case MOTIF_PROBE_CMP_FOLD: return 8.0 * 4.0;    // window compares
     case MOTIF_PROBE_LDS64_DIV: return 8.0;         // 64-bit shared loads
+    case MOTIF_PROBE_ATOMS_OR: return 8.0;          // shared atomic ORs
     default: return 32.0;                           // 4 x 8 instructions of the probed kind
   }
 }
@@ -179,6 +192,8 @@ extern "C" int motif_probe_rate(int kind, int iters, double* ops_per_sm_clk, dou
     PROBE_CASE(MOTIF_PROBE_CMP_SPLIT)
     PROBE_CASE(MOTIF_PROBE_CMP_FOLD)
     PROBE_CASE(MOTIF_PROBE_LDS64_DIV)
+    PROBE_CASE(MOTIF_PROBE_ATOMS_OR)
+    PROBE_CASE(MOTIF_PROBE_SHFL)
 #undef PROBE_CASE
     default: e = cudaErrorInvalidValue;
   }

@@ -52,9 +52,37 @@ def test_status_codes_match_header(lib):
 
 
 def test_struct_sizes_match_c_layout():
-    # motif_opts: pointer, 7 int32, 2 fn pointers, ctx pointer, 2 uint64.
-    assert ctypes.sizeof(m.motif_opts) == 8 + 8 * 4 + 3 * 8 + 2 * 8 + 2 * 4
+    # motif_opts: pointer, 8 int32, 2 fn pointers, ctx pointer, 2 uint64, 3 int32 (+ padding).
+    assert ctypes.sizeof(m.motif_opts) == 8 + 8 * 4 + 3 * 8 + 2 * 8 + 3 * 4 + 4
     assert ctypes.sizeof(m.motif_stats_t) == 3 * 8 + 4 * 8 + 8 + 4 * 4 + 3 * 8
+
+
+def test_struct_offsets_match_the_header(tmp_path):
+    """Every field of the binding's structs sits at the offset the C compiler gives it."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "motif.h"', "int main(void) {"]
+    for cname, py in (("motif_opts", m.motif_opts), ("motif_stats_t", m.motif_stats_t),
+                      ("motif_server_opts", m.motif_server_opts)):
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), "-o", str(exe), str(src)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        a, b, c = ln.split()
+        got[(a, b)] = int(c)
+    for cname, py in (("motif_opts", m.motif_opts), ("motif_stats_t", m.motif_stats_t),
+                      ("motif_server_opts", m.motif_server_opts)):
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
 
 
 def test_encode_decode_roundtrip():

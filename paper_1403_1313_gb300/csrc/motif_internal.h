@@ -114,6 +114,8 @@ constexpr int kKindTiledSplit = MOTIF_KERNEL_BITSLICE + 1;
 inline int launch_kind(int kind, int p, bool split) {
   return split && kind == MOTIF_KERNEL_GROUP && p == 4 ? kKindTiledSplit : kind;
 }
+// Dynamic shared memory of a step kernel variant: kind is a unit kind (MOTIF_KERNEL_*) or
+// kKindTiledSplit.
 size_t step_smem_bytes(int kind, int p, int wstride, int block);
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem);
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem);

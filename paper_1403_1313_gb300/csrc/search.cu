@@ -939,6 +939,69 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
 }
 
 // ---------------------------------------------------------------------------------------------
+// End of a step, shared by every step-kernel variant: the last CTA to finish advances every job
+// to its next pass (and, inside a graph's while loop, sets the loop condition).  All threads of
+// the CTA call it.
+__device__ void finish_step(const JobDesc* __restrict__ jobs, JobState* states, int njobs,
+                            StepCtl* ctl, cudaGraphConditionalHandle cond, int use_cond,
+                            int* s_last, unsigned* s_act) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->ctas_done, 1u);
+    *s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  unsigned active = 0;
+  for (int j = tid; j < njobs; j += blockDim.x) {
+    JobState* st = &states[j];
+    if (ld_volatile(&st->done)) continue;
+    const JobDesc jd = jobs[j];
+    const Pass p = make_pass(jd, st);
+    const unsigned long long cur = ld_volatile(&st->cursor);
+    if (cur > 0 || p.work == 0) st->steps += 1;
+    if (cur >= p.work) {  // the pass is complete
+      st->cursor = 0;
+      const bool chunk_done = p.s1 >= jd.n || ld_volatile(&st->qcount[p.qout]) == 0;
+      if (chunk_done) {
+        const unsigned long long next = ld_volatile(&st->chunk) + 1;
+        st->chunk = next;
+        st->pass_seq = 0;
+        st->qcount[0] = 0;
+        if (next >= jd.nchunks) st->done = 1;
+      } else {
+        st->pass_seq = p.s1;
+        st->qsel = p.qout;
+        st->qcount[1 - p.qout] = 0;
+      }
+    }
+    if (!ld_volatile(&st->done)) ++active;
+  }
+  for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(kFull, active, o);
+  if (lane == 0) s_act[tid >> 5] = active;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_act[w];
+    const unsigned steps = ctl->steps + 1;
+    ctl->active_jobs = tot;
+    ctl->steps = steps;
+    __threadfence();
+    ctl->ctas_done = 0;
+    if (use_cond) {
+      // Inside a graph's while loop: run another step while work remains, never beyond the
+      // step bound (which ends the loop even if a job failed to complete).
+      const bool more = tot > 0 && (ctl->max_steps == 0 || steps < ctl->max_steps);
+      cudaGraphSetConditional(cond, more ? 1u : 0u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // The step kernel.
 
 // KIND = MOTIF_KERNEL_CAND with P = candidates per lane, or MOTIF_KERNEL_GROUP with P = ks.
@@ -1081,59 +1144,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const JobDesc* __restri
     }
   }
 
-  // The last CTA to finish advances every job to its next pass.
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->ctas_done, 1u);
-    s_last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  unsigned active = 0;
-  for (int j = tid; j < njobs; j += blockDim.x) {
-    JobState* st = &states[j];
-    if (ld_volatile(&st->done)) continue;
-    const JobDesc jd = jobs[j];
-    const Pass p = make_pass(jd, st);
-    const unsigned long long cur = ld_volatile(&st->cursor);
-    if (cur > 0 || p.work == 0) st->steps += 1;
-    if (cur >= p.work) {  // the pass is complete
-      st->cursor = 0;
-      const bool chunk_done = p.s1 >= jd.n || ld_volatile(&st->qcount[p.qout]) == 0;
-      if (chunk_done) {
-        const unsigned long long next = ld_volatile(&st->chunk) + 1;
-        st->chunk = next;
-        st->pass_seq = 0;
-        st->qcount[0] = 0;
-        if (next >= jd.nchunks) st->done = 1;
-      } else {
-        st->pass_seq = p.s1;
-        st->qsel = p.qout;
-        st->qcount[1 - p.qout] = 0;
-      }
-    }
-    if (!ld_volatile(&st->done)) ++active;
-  }
-  for (int o = 16; o > 0; o >>= 1) active += __shfl_down_sync(kFull, active, o);
-  if (lane == 0) s_act[tid >> 5] = active;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned tot = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_act[w];
-    const unsigned steps = ctl->steps + 1;
-    ctl->active_jobs = tot;
-    ctl->steps = steps;
-    __threadfence();
-    ctl->ctas_done = 0;
-    if (use_cond) {
-      // Inside a graph's while loop: run another step while work remains, never beyond the
-      // step bound (which ends the loop even if a job failed to complete).
-      const bool more = tot > 0 && (ctl->max_steps == 0 || steps < ctl->max_steps);
-      cudaGraphSetConditional(cond, more ? 1u : 0u);
-    }
-  }
+  finish_step(jobs, states, njobs, ctl, cond, use_cond, &s_last, s_act);
 }
 
 // Resets the states of a job table and its step control block.
@@ -1304,6 +1315,7 @@ const void* step_function(int kind, int p) {
 }  // namespace
 
 size_t step_smem_bytes(int kind, int p, int wstride, int block) {
+  if (kind == kKindTiledSplit) kind = MOTIF_KERNEL_GROUP;
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
   if (kind == MOTIF_KERNEL_BITSLICE)  // 4 words per base position (l <= 32) per 32 windows,
                                       // blocks in fours

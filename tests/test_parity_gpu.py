@@ -251,14 +251,22 @@ def test_device_path_matches_blocking_path():
 
 # ---- full-size workloads: sampled parity ---------------------------------------------------------
 
-def _sample_ranges(l, consensus_code, seed, count=6, width=1 << 13):
+TILE = 1 << 16  # candidates of one tile of the prefix-tiled pass (256 groups of 256 suffixes)
+
+
+def _sample_ranges(l, consensus_code, seed, count=6, tiles=3):
+    """Sub-ranges that start on a tile boundary and span several whole tiles (so that the
+    default plan of each runs the tiled pass, as the whole-space search does), the first one
+    holding the consensus's tile."""
     rng = random.Random(seed)
-    space = 4 ** l
-    ranges = [(max(0, consensus_code - width // 2), min(space, consensus_code + width // 2))]
-    for _ in range(count - 1):
-        lo = rng.randrange(0, space - width)
-        ranges.append((lo, lo + width))
-    return ranges
+    ntiles = 4 ** l // TILE
+    first = max(0, min(ntiles - tiles, consensus_code // TILE - tiles // 2))
+    starts = [first]
+    while len(starts) < count:
+        t = rng.randrange(0, ntiles - tiles + 1)
+        if all(abs(t - u) >= tiles for u in starts):
+            starts.append(t)
+    return [(t * TILE, (t + tiles) * TILE) for t in starts]
 
 
 @pytest.mark.parametrize("cfg", ["l15d4", "l17d5"])
@@ -278,25 +286,32 @@ def test_full_size_sampled(cfg):
         assert ref.tolist() == [c]
     # Sampled sub-ranges: the oracle over each range, the GPU over the same range, and the
     # whole-space GPU result restricted to it.
-    for lo, hi in _sample_ranges(l, cons, seed=l * 100 + d):
-        ref, ref_cmp = oracle.search(job.rows(), l, d, lo=lo, hi=hi, threads=8)
-        sub, cmp = gpu_search(job.seqs, l, d, lo=lo, hi=hi)
+    ranges = _sample_ranges(l, cons, seed=l * 100 + d)
+    assert ranges[0][0] <= cons < ranges[0][1]
+    for lo, hi in ranges:
+        assert lo % TILE == 0 and hi - lo >= 2 * TILE
+        ref, ref_cmp = oracle.search(job.rows(), l, d, lo=lo, hi=hi, threads=os.cpu_count() or 8)
+        plan = m.motif_plan_create(job.n, job.t, l, d, _opts(range_lo=lo, range_hi=hi))
+        m.motif_load_seqs(plan, job.seqs)
+        sub = m.motif_search(plan)
+        assert m.motif_stats(plan)["kernel"] == m.KERNEL_TILED, (lo, hi)
+        cmp = m.motif_count_compares(plan)
+        m.motif_plan_destroy(plan)
         assert np.array_equal(sub, ref), (lo, hi)
         assert cmp == ref_cmp
         inside = full[(full >= lo) & (full < hi)]
         assert np.array_equal(inside, ref)
 
 
-FULL_GOLDEN = {"l15d4": "l15d4_n20_t600_seed2.json"}
+FULL_GOLDEN = {"l15d4": "l15d4_n20_t600_seed2.json", "l17d5": "l17d5_n20_t600_seed3.json"}
 
 
 @pytest.mark.parametrize("form", ["auto", "device", "bitslice_seeded"])
 @pytest.mark.parametrize("cfg", sorted(FULL_GOLDEN))
 def test_full_space_matches_stored_oracle(cfg, form):
-    """The whole code space of the (15,4) workload against the oracle's complete result
-    (tests/golden/, written by make_golden.py from oracle/ alone): every code, none missing,
-    and the canonical compare tally.  ((17,5), 16 times the candidates, is checked on sampled
-    ranges and per accepted code in test_full_size_sampled.)"""
+    """The whole code space of the (15,4) and (17,5) workloads against the oracle's complete
+    results (tests/golden/, written by make_golden.py from oracle/ alone): every code, none
+    missing, and the canonical compare tally."""
     path = os.path.join(GOLDEN, FULL_GOLDEN[cfg])
     if not os.path.exists(path):
         pytest.skip("no stored oracle result for %s (tests/golden/make_golden.py %s)" % (cfg, cfg))

@@ -300,7 +300,14 @@ typedef struct {
 } motif_server_opts;
 
 /* Starts the process-wide serving loop (a scheduler thread with its own stream).  opts may be
- * NULL.  MOTIF_ERR_STATE if it is already running. */
+ * NULL.  MOTIF_ERR_STATE if it is already running.
+ *
+ * Admission (between device steps): queued jobs are taken in arrival order while table slots
+ * (max_active) and the device budget allow.  The resident table runs one step-kernel variant,
+ * chosen by the first job admitted into an empty table (the suffix length k = min(l, 4)); a job
+ * that needs another variant waits until the table drains, and later jobs of the table's
+ * variant are admitted past it until it has waited 50 ms, after which nothing more is admitted
+ * until it is.  A job whose footprint exceeds the remaining budget stops admission. */
 int motif_server_start(const motif_server_opts* opts);
 
 /* Stops the serving loop.  The scheduler first runs every submitted job, queued or active, to

@@ -28,6 +28,9 @@ namespace motif_serve {
 // Chunk of a served job's per-group passes (its survivor queues hold one chunk); a tiled job
 // takes its whole range as one chunk, since the tiled pass uses no queues.
 constexpr uint64_t kServeChunkGroups = 1ull << 20;
+// How long a queued job of another kernel variant than the active table's may be passed over by
+// later jobs before admission stops so that the table drains for it.
+constexpr double kHeadWaitMs = 50.0;
 
 struct Job {
   int64_t id = 0;
@@ -381,20 +384,29 @@ void scheduler(Server* S) {
   bool dirty = true;
   std::vector<int> old_slot;
   for (;;) {
-    // Admission: first come, first served, while slots and the memory budget allow.
+    // Admission, in arrival order, while slots and the memory budget allow.  The table runs one
+    // kernel variant, so a job of another variant waits until the table drains; later jobs of
+    // the table's variant are admitted past it until it has waited kHeadWaitMs, after which
+    // nothing more is admitted and the table drains for it.  A job that does not fit the memory
+    // budget stops admission (memory is granted in arrival order).
     const int64_t budget = S->o.device_budget > 0 ? S->o.device_budget : (8ll << 30);
     old_slot.assign(S->active.size(), 0);
     for (size_t i = 0; i < S->active.size(); ++i) old_slot[i] = (int)i;
-    while (!S->queue.empty() && (int)S->active.size() < max_active(S)) {
-      Job* j = S->queue.front();
-      if (!S->active.empty() && (j->kind != S->kind || j->pv != S->pv)) break;
+    for (auto it = S->queue.begin();
+         it != S->queue.end() && (int)S->active.size() < max_active(S);) {
+      Job* j = *it;
+      if (!S->active.empty() && (j->kind != S->kind || j->pv != S->pv)) {
+        if (now_ms() - j->t_submit > kHeadWaitMs) break;  // the oldest passed-over job
+        ++it;
+        continue;
+      }
       j->footprint = footprint_of(j);
       if (!S->active.empty() && S->budget_used + j->footprint > budget) break;
       if (!allocate_job(S, j)) {
         release_run_buffers(S, j);  // keeps the window copies: the job stays queued
         if (S->active.empty()) {  // cannot ever fit: fail the job
           release_buffers(S, j);
-          S->queue.pop_front();
+          it = S->queue.erase(it);
           j->status = MOTIF_ERR_OOM;
           j->done = true;
           j->t_done = now_ms();
@@ -403,12 +415,13 @@ void scheduler(Server* S) {
         }
         break;
       }
-      S->queue.pop_front();
+      it = S->queue.erase(it);
       if (j->ready) cudaStreamWaitEvent(S->stream, j->ready, 0);  // its windows are copied
       if (prepare_launch(S, j->kind, j->pv, j->smem) != MOTIF_OK) {
         release_buffers(S, j);
         j->status = MOTIF_ERR_CUDA;
         j->done = true;
+        j->t_done = now_ms();
         S->cv_done.notify_all();
         continue;
       }

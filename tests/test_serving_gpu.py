@@ -127,3 +127,37 @@ def test_dense_jobs_take_the_bitmap(server, use_graph):
         assert got is not None
         ref, _ = oracle.search(rows, l, d, threads=8)
         assert np.array_equal(got[0], ref)
+
+
+def test_other_variant_does_not_hold_back_later_jobs(server):
+    """A queued job that needs another step-kernel variant than the running table (l = 3: suffix
+    length 3) does not hold back the jobs that arrive after it: they are admitted while the long
+    job that fills the table still runs, the passed-over job runs once the table drains, and
+    every result equals the oracle's."""
+    import time
+    # One tile per CTA per step, so the long (17,5) job spans hundreds of steps.
+    m.motif_server_start(max_active=8, step_tiles=256)
+    long_job = fmgen.single("l17d5")
+    t0 = time.perf_counter()
+    a = _submit(long_job)
+    other = fmgen.fm_job(4, 30, 3, 0, 41)
+    b = _submit(other)
+    later = [fmgen.fm_job(5, 60, l, 2, 50 + l) for l in (8, 9, 10)]
+    ids, t_sub = [], []
+    for job in later:
+        t_sub.append(1e3 * (time.perf_counter() - t0))
+        ids.append(_submit(job))
+    res_later = [m.motif_poll(jid, timeout_ms=120000) for jid in ids]
+    codes_a, st_a = m.motif_poll(a, timeout_ms=120000)
+    codes_b, st_b = m.motif_poll(b, timeout_ms=120000)
+    for job, (codes, st), ts in zip(later, res_later, t_sub):
+        # admitted (ts + queue_ms after the first submit) before the long job ended
+        assert ts + st["queue_ms"] < st_a["total_ms"], (ts, st["queue_ms"], st_a["total_ms"])
+        ref, _ = oracle.search(job.rows(), job.l, job.d, threads=8)
+        assert np.array_equal(codes, ref)
+    ref_b, _ = oracle.search(other.rows(), other.l, other.d)
+    assert np.array_equal(codes_b, ref_b)
+    assert m.motif_encode(long_job.consensus) in set(codes_a.tolist())
+    for c in codes_a.tolist():
+        ref, _ = oracle.search(long_job.rows(), long_job.l, long_job.d, lo=c, hi=c + 1)
+        assert ref.tolist() == [c]

@@ -16,8 +16,15 @@ e2e     = the same metric through the blocking C-ABI call with host buffers (H2D
 roofline= the step kernel against its POPC issue bound (one POPC per canonical unit step).
 cpu_baseline / --impl reference = the CPU oracle (C, POSIX threads over all host cores, the
           paper's index-range split) on a bounded sub-range of the same workload.
-Multi-GPU (torchrun): every rank searches its own independently seeded instance of the
-workload (weak scaling, no collective on the data path); max time over ranks.
+Multi-GPU (torchrun, --parallelism range, the default): the ranks split the candidate index
+space of the one workload into contiguous ranges (Sec. IV.A's per-worker first/last index, by
+motif_shard_range); every step each rank searches its range and the accepted codes are
+all-gathered over NCCL (counts, then codes padded to the largest count) inside the timed region;
+strong scaling, max time over ranks, and the gathered result is checked against the whole-space
+search.  --parallelism replicas: every rank searches its own independently seeded instance (weak
+scaling, no collective on the data path).
+cpu_baseline_1t = the oracle on one thread over a stated sub-range, extrapolated to the whole
+          space (the paper's sequential baseline).
 """
 from __future__ import annotations
 
@@ -77,6 +84,15 @@ def parse():
     ap.add_argument("--rates", default="1,2,5,10,20,50,100,200")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--parallelism", choices=["range", "replicas"], default="range",
+                    help="N > 1: split one workload's candidate range over the ranks and gather "
+                         "the codes (strong scaling), or one independent instance per rank (weak)")
+    ap.add_argument("--cpu-1t-seconds", type=float, default=8.0,
+                    help="single-thread oracle sample for cpu_baseline_1t (0 = skip)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch mode: leave the plans on their AUTO choices")
+    ap.add_argument("--tune-ms", type=int, default=400,
+                    help="batch mode: motif_autotune's time budget per job")
     ap.add_argument("--serve-step-tiles", type=int, default=0,
                     help="serve mode: tile budget of one server step over all warps (0 = default)")
     return ap.parse_args()
@@ -202,6 +218,28 @@ def cpu_baseline(job, seconds: float, steps: int = 1):
     return size, times, cores, lo
 
 
+def cpu_baseline_1t(job, seconds: float) -> dict:
+    """The oracle on ONE thread (the paper's sequential baseline, Sec. V) over a sub-range sized
+    for about `seconds` of work, extrapolated to the whole candidate space."""
+    from oracle import oracle
+    l = job.l
+    lo = (4 ** l) // 3
+    probe = 1 << 10
+    t0 = time.perf_counter()
+    oracle.search(job.rows(), l, job.d, lo=lo, hi=lo + probe, threads=1)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    size = int(min(4 ** l - lo, max(probe, rate * seconds)))
+    t0 = time.perf_counter()
+    oracle.search(job.rows(), l, job.d, lo=lo, hi=lo + size, threads=1)
+    dt = time.perf_counter() - t0
+    rate = size / dt
+    return dict({"value": rate, "unit": "candidates/s", "cores": 1, "kind": "oracle",
+                 "sample": "candidates [%d, %d), %.1f s on one thread" % (lo, lo + size, dt),
+                 "full_search_s": 4 ** l / rate,
+                 "full_search_s_basis": "extrapolated: 4^%d candidates / the sample's rate" % l},
+                **host_cpu())
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -241,12 +279,16 @@ def run_ours(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    import torch.distributed as dist
     if world > 1:
-        import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     l, d, n, t, seed = CONFIGS[args.config]
-    job = fmgen.fm_job(n, t, l, d, seed + rank * 1000)
+    shard = world > 1 and args.parallelism == "range"
+    job = fmgen.fm_job(n, t, l, d, seed + (0 if shard or world == 1 else rank * 1000))
     workload = "l%dd%d_n%d_t%d_seed%d" % (l, d, n, t, seed)
+    cands = 4 ** l
+    # This rank's contiguous share of the candidate space (the whole space at N = 1).
+    r_lo, r_hi = m.motif_shard_range(cands, rank, world) if shard else (0, cands)
 
     stream = torch.cuda.Stream()
     kw = {}
@@ -264,7 +306,8 @@ def run_ours(args):
         kw["seed"] = m.SEED_NEIGHBOURHOOD
     if args.cands_per_thread:
         kw["cands_per_thread"] = args.cands_per_thread
-    opts = m.torch_opts(stream=stream, **kw)
+    rkw = dict(kw, range_lo=r_lo, range_hi=r_hi) if shard else dict(kw)
+    opts = m.torch_opts(stream=stream, **rkw)
     plan = m.motif_plan_create(n, t, l, d, opts)
     cap = 1 << 16
     with torch.cuda.stream(stream):
@@ -273,30 +316,58 @@ def run_ours(args):
         d_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    if shard:
+        from paper_1403_1313_gb300.shard import gather_codes_device
+
     def step():
         m.motif_load_seqs_device(plan, d_chars)
         m.motif_search_device(plan, d_out, cap, d_cnt)
+        if shard:  # the variable-size gather of every rank's codes (counts, then codes)
+            return gather_codes_device(d_out, d_cnt)
+        return None
 
     for _ in range(max(args.warmup, 3)):
         step()
     stream.synchronize()
     count = int(d_cnt.item())
-    if count > cap:  # a dense result: room for every code, then warm up again
-        cap = count
+    if shard:  # every rank needs room for its own codes
+        cnt_all = torch.tensor([count], dtype=torch.int64, device="cuda")
+        dist.all_reduce(cnt_all, op=dist.ReduceOp.MAX)
+        count_max = int(cnt_all.item())
+    else:
+        count_max = count
+    if count_max > cap:  # a dense result: room for every code, then warm up again
+        cap = count_max
         with torch.cuda.stream(stream):
             d_out = torch.zeros(cap, dtype=torch.int64, device="cuda")
         for _ in range(max(args.warmup, 3)):
             step()
         stream.synchronize()
         count = int(d_cnt.item())
-    codes = d_out[:max(count, 0)].cpu().numpy().astype(np.uint64)
-    assert count >= 1 and m.motif_encode(job.consensus) in set(codes.tolist()), "result check failed"
+    if shard:
+        # The gathered result of one step against the whole-space search of this GPU.
+        with torch.cuda.stream(stream):
+            gathered = step()
+        stream.synchronize()
+        codes = gathered.cpu().numpy().astype(np.uint64)
+        whole = m.motif_plan_create(n, t, l, d, m.torch_opts(stream=stream, **kw))
+        m.motif_load_seqs(whole, np.ascontiguousarray(job.seqs))
+        ref = m.motif_search(whole)
+        m.motif_plan_destroy(whole)
+        assert np.array_equal(codes, ref), "gathered result != whole-space search"
+    else:
+        codes = d_out[:max(count, 0)].cpu().numpy().astype(np.uint64)
+    assert codes.size >= 1 and m.motif_encode(job.consensus) in set(codes.tolist()), \
+        "result check failed"
     compares, unit_steps = m.motif_count_work(plan)
+    if shard:  # the whole job's canonical tally: every rank's range
+        cmp_all = torch.tensor([compares, unit_steps], dtype=torch.int64, device="cuda")
+        dist.all_reduce(cmp_all)
+        compares, unit_steps = (int(x) for x in cmp_all.tolist())
     m.motif_stats(plan)  # resets the summed device times
     st0 = m.motif_stats(plan)
 
     if world > 1:
-        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
@@ -317,15 +388,14 @@ def run_ours(args):
     st = m.motif_stats(plan)  # also accounts the step launches run inside the graphs
     launches = m.motif_kernel_launches() - launches0
     if world > 1:
-        import torch.distributed as dist
         tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
         dist.barrier()
 
-    cands = 4 ** l
-    value = world * cands * args.steps / (t_ms / 1e3)
-    cps = world * compares * args.steps / (t_ms / 1e3)
+    jobs_per_step = 1 if shard else world  # one shared workload, or one instance per rank
+    value = jobs_per_step * cands * args.steps / (t_ms / 1e3)
+    cps = (1 if shard else world) * compares * args.steps / (t_ms / 1e3)
 
     # Roofline of the dominant kernel (the step kernel; its launches are bracketed by the plan's
     # events: search_ms_sum over the timed searches), by the per-compare recipe: one algorithmic
@@ -390,6 +460,8 @@ def run_ours(args):
                 "sample": "candidates [0, %d) of %s" % (min(cands, args.cand_subrange), workload)}
 
     roof_cand = roof_bitslice = None
+    if rank != 0:  # the per-candidate legs are rank 0's alone
+        args.cand_subrange = 0
     if kname != "CAND" and args.cand_subrange > 0:
         roof_cand = per_candidate_leg(m.KERNEL_CAND, "CAND", 2)
     if args.cand_subrange > 0 and d <= 7:
@@ -406,36 +478,52 @@ def run_ours(args):
             "peak_lop3_basis": "64 LOP3/clk/SM (K4 probe) x %d SMs x %.0f MHz x 32 / %d LOP3 "
                                "per 32 compares" % (sms, max_mhz, lop3)})
 
-    # End to end through the blocking C ABI with host buffers.
-    e2e = None
-    if rank == 0 or world > 1:
-        plan2 = m.motif_plan_create(n, t, l, d, m.torch_opts(stream=stream, **kw))
-        host_chars = np.ascontiguousarray(job.seqs)
+    # End to end through the blocking C ABI with host buffers (each rank its own range, and the
+    # ranks' host codes gathered, in range-shard mode).
+    plan2 = m.motif_plan_create(n, t, l, d, m.torch_opts(stream=stream, **rkw))
+    host_chars = np.ascontiguousarray(job.seqs)
+    m.motif_load_seqs(plan2, host_chars)
+    m.motif_search(plan2)
+    ne = max(3, args.e2e_steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        from paper_1403_1313_gb300.shard import gather_codes
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne):
         m.motif_load_seqs(plan2, host_chars)
-        m.motif_search(plan2)
-        ne = max(3, args.e2e_steps)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(ne):
-            m.motif_load_seqs(plan2, host_chars)
-            got = m.motif_search(plan2)
-        dt = time.perf_counter() - t0
-        e2e = {"value": world * cands * ne / dt, "unit": "candidates/s",
-               "h2d_bytes_per_step": int(n * t), "d2h_bytes_per_step": int(8 * got.size + 8)}
-        m.motif_plan_destroy(plan2)
+        got = m.motif_search(plan2)
+        d2h = 8 * got.size + 8
+        if shard:
+            got = gather_codes(got)
+    dt = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    e2e = {"value": jobs_per_step * cands * ne / dt, "unit": "candidates/s",
+           "h2d_bytes_per_step": int(n * t), "d2h_bytes_per_step": int(d2h)}
+    if shard:
+        e2e["note"] = "per rank: its range's codes to the host, then a host-buffer gather"
+    m.motif_plan_destroy(plan2)
 
     line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic",
+            "higher_is_better": True,
+            "scaling": "strong" if args.parallelism == "range" else "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload, "l": l, "d": d, "n": n, "t": t, "seed": seed,
                        "candidates": cands, "kernel": roof["kernel"],
                        "candidate_seeding": args.seed,
                        "l2": "flushed (256 MiB write) before every timed step",
-                       "parallelism": "weak: one independent instance per GPU" if world > 1 else "1 GPU"},
+                       "parallelism": ("range shard: %d GPUs, contiguous candidate ranges "
+                                       "(motif_shard_range), NCCL gather of the codes inside the "
+                                       "timed region" % world) if shard else
+                                      ("weak: one independent instance per GPU" if world > 1
+                                       else "1 GPU")},
             "window_compares_per_s": cps,
             "algorithmic_compares_per_search": compares,
             "survivors": count,
@@ -452,10 +540,11 @@ def run_ours(args):
                 "value": size / times[0], "unit": "candidates/s", "cores": cores, "kind": "oracle",
                 "sample": "candidates [%d, %d) of %s (%.1f s wall, all %d cores)" % (
                     lo, lo + size, workload, times[0], cores)}, **host_cpu())
+            if args.cpu_1t_seconds > 0:
+                line["cpu_baseline_1t"] = cpu_baseline_1t(job, args.cpu_1t_seconds)
         print(json.dumps(line), flush=True)
     m.motif_plan_destroy(plan)
     if world > 1:
-        import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 
@@ -470,13 +559,25 @@ def run_batch(args):
     torch.cuda.set_device(0)
     jobs = fmgen.batched_jobs(seed=4, count=64)
     out = {}
-    for label, sel in (("all_64", lambda j: True), ("small_l_le_12", lambda j: j.l <= 12)):
+    runs = [("all_64", lambda j: True, True), ("small_l_le_12", lambda j: j.l <= 12, True)]
+    if not args.no_autotune:  # the AUTO choices too, for comparison
+        runs.append(("all_64_auto", lambda j: True, False))
+    tuned_choice = {}
+    for label, sel, tune in runs:
         js = [j for j in jobs if sel(j)]
         plans = []
+        t_tune = time.perf_counter()
         for j in js:
             pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
             m.motif_load_seqs(pl, j.seqs)
+            if tune and not args.no_autotune:
+                # the autotuner times the kernel forms on a sub-range of this job's candidates and
+                # keeps the fastest in the plan (and its cache, keyed by the job's shape)
+                best = m.motif_autotune(pl, budget_ms=args.tune_ms)
+                tuned_choice[(j.l, j.d, j.n, j.t)] = (best.kernel, best.cands_per_thread,
+                                                      best.suffix_bases, best.compact_levels)
             plans.append(pl)
+        t_tune = time.perf_counter() - t_tune
         compares = sum(m.motif_count_compares(pl) for pl in plans)
         cands = sum(4 ** j.l for j in js)
         plain_res = [m.motif_search(pl) for pl in plans]          # warm-up + reference result
@@ -523,6 +624,8 @@ def run_batch(args):
                        (statistics.median(x) for x in zip(*phases))))
         out[label] = {
             "jobs": len(js), "candidates": cands, "algorithmic_compares": compares,
+            "plans": ("autotuned (motif_autotune per job, %.1f s)" % t_tune
+                      if tune and not args.no_autotune else "AUTO"),
             "survivors": survivors,
             "plain_ms": 1e3 * t_plain, "batched_ms": 1e3 * t_batch,
             "batched_nograph_ms": 1e3 * t_batch_nograph,
@@ -538,9 +641,13 @@ def run_batch(args):
         }
         for pl in plans:
             m.motif_plan_destroy(pl)
+    kinds = {}
+    for v in tuned_choice.values():
+        kinds[str(v)] = kinds.get(str(v), 0) + 1
     print(json.dumps({"mode": "batch", "workload": "64 jobs, seed 4: l~U{9..15}, d~U{1..4}, "
                       "n~U{5..40}, t~U{200..1000}, FM-planted", "reps": max(1, args.steps),
-                      "results": out}), flush=True)
+                      "tuned_choices (kernel, cands_per_thread, suffix_bases, compact_levels)":
+                          kinds, "results": out}), flush=True)
     return 0
 
 

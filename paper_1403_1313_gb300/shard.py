@@ -56,6 +56,29 @@ def gather_codes(codes: np.ndarray, group=None) -> np.ndarray:
     return np.concatenate([p[:c].cpu().numpy().astype(np.uint64) for p, c in zip(parts, counts)])
 
 
+def gather_codes_device(d_codes, d_count, group=None):
+    """All-gathers every rank's ascending device codes (d_codes[0 .. d_count[0]), int64 CUDA
+    tensors, d_count holding one count) and returns the rank-order concatenation as a CUDA
+    tensor: counts first (read on the host to size the exchange), then the codes padded to the
+    largest count.  NCCL backend; the codes stay on the device."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    counts = torch.zeros(world, dtype=torch.int64, device=d_count.device)
+    dist.all_gather_into_tensor(counts, d_count.reshape(1), group=group)
+    host_counts = counts.tolist()
+    width = max(1, max(host_counts))
+    mine = d_codes[:width]
+    if mine.numel() < width:
+        mine = torch.cat([mine, torch.zeros(width - mine.numel(), dtype=mine.dtype,
+                                            device=mine.device)])
+    parts = torch.empty(world * width, dtype=d_codes.dtype, device=d_codes.device)
+    dist.all_gather_into_tensor(parts, mine.contiguous(), group=group)
+    parts = parts.view(world, width)
+    return torch.cat([parts[r, :c] for r, c in enumerate(host_counts)])
+
+
 def sharded_search(seqs, l: int, d: int, rank: int, world: int, weights=None, search_fn=None,
                    group=None) -> np.ndarray:
     """Searches this rank's share of [0, 4^l) and gathers the global ascending result.

@@ -374,6 +374,43 @@ def test_batch_matches_oracle(use_graph):
         assert np.array_equal(got, ref)
 
 
+def _closed_form_compares(job):
+    """Expected canonical compares of a uniform-base job (the oracle's cost estimate)."""
+    import math
+    p = sum(math.comb(job.l, k) * 3 ** k for k in range(min(job.d, job.l) + 1)) / 4 ** job.l
+    q = 1 - (1 - p) ** (job.t - job.l + 1)
+    per = (q / p) * (1 - q ** job.n) / (1 - q) if q < 1 else (job.t - job.l + 1) * job.n
+    return 4 ** job.l * per
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_64_job_mix(use_graph):
+    """The 64-job batch mix (seed 4: l 9..15, d 1..4, n 5..40, t 200..1000) in one batched
+    search: the jobs the oracle finishes within about 2e10 compares (the 20 cheapest: l <= 12)
+    equal the oracle's results, and every job equals its own one-job search."""
+    jobs = fmgen.batched_jobs(seed=4, count=64)
+    plans = []
+    for j in jobs:
+        plan = m.motif_plan_create(j.n, j.t, j.l, j.d)
+        m.motif_load_seqs(plan, j.seqs)
+        plans.append(plan)
+    outs = m.motif_batch_search(plans, use_graph=use_graph)
+    order = sorted(range(len(jobs)), key=lambda i: _closed_form_compares(jobs[i]))
+    budget, checked = 2e10, 0
+    for i in order:
+        budget -= _closed_form_compares(jobs[i])
+        if budget < 0:
+            break
+        ref, _ = oracle.search(jobs[i].rows(), jobs[i].l, jobs[i].d, threads=os.cpu_count() or 8)
+        assert np.array_equal(outs[i], ref), (jobs[i].l, jobs[i].d, jobs[i].n, jobs[i].t)
+        checked += 1
+    assert checked >= 15
+    for job, plan, got in zip(jobs, plans, outs):
+        assert np.array_equal(got, m.motif_search(plan)), (job.l, job.d, job.n, job.t)
+        assert m.motif_encode(job.consensus) in set(got.tolist())
+        m.motif_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("l,d", [(9, 8), (12, 9)])
 def test_bitslice_beyond_its_counter_falls_back_to_cand(l, d):
     """The bit-sliced counter holds distances up to 7; larger d runs the POPC compare."""

@@ -115,3 +115,40 @@ def test_dynamic_chunks_gather_equals_single(tmp_path, chunk):
     assert len(claims) == nchunks
     assert claims[0, 0] == 0 and claims[-1, 1] == 4 ** l
     assert np.all(claims[1:, 0] == claims[:-1, 1])
+
+
+def _dev_gather_worker(rank, world, port, l, d, seed, out_dir):
+    """The bench's range-shard step with the oracle standing in for the rank's device search:
+    motif_shard_range's split, this rank's codes in a buffer longer than its count, and the
+    variable-size tensor gather (counts, then codes padded to the largest count)."""
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+    import paper_1403_1313_gb300 as m
+    from paper_1403_1313_gb300 import fmgen
+    from paper_1403_1313_gb300.shard import gather_codes_device
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=30))
+    job = fmgen.fm_job(6, 90, l, d, seed)
+    lo, hi = m.motif_shard_range(4 ** l, rank, world)
+    codes = _oracle_range(job.rows(), l, d, lo, hi)
+    buf = torch.full((codes.size + 5 + 3 * rank,), -1, dtype=torch.int64)  # room past the count
+    buf[:codes.size] = torch.from_numpy(codes.astype(np.int64))
+    cnt = torch.tensor([codes.size], dtype=torch.int64)
+    got = gather_codes_device(buf, cnt)
+    np.save(os.path.join(out_dir, "devgather%d.npy" % rank), got.numpy().astype(np.uint64))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("l,d,seed", [(8, 2, 91), (7, 3, 12), (6, 0, 5)])
+def test_range_shard_tensor_gather_equals_single(tmp_path, l, d, seed):
+    from oracle import oracle
+    from paper_1403_1313_gb300 import fmgen
+    mp.start_processes(_dev_gather_worker, args=(2, _free_port(), l, d, seed, str(tmp_path)),
+                       nprocs=2, join=True, start_method="spawn")
+    job = fmgen.fm_job(6, 90, l, d, seed)
+    ref, _ = oracle.search(job.rows(), l, d)
+    for r in range(2):
+        assert np.array_equal(np.load(tmp_path / ("devgather%d.npy" % r)), ref)

@@ -49,14 +49,17 @@ CONFIGS = {  # name: (l, d, n, t, seed)
 }
 POPC_PER_SM_CLK = 16.0  # measured by the K4 probe (motif_probe_rate POPC) on GB300
 LOP3_PER_SM_CLK = 64.0  # measured by the K4 probe (motif_probe_rate LOP3) on GB300
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the tiled pass on the
-# (15,4) n=20 t=600 seed-2 workload (one --set full capture of the current kernel): 297.2 KB + 0 B.
-TILED_L15D4_DRAM_BYTES = 297216
-# The same capture's smsp__issue_active (the fraction of issue slots the kernel used) and
-# sm__inst_executed_pipe_alu (its busiest pipe): the factored kernel's own bound is instruction
-# issue, not the per-compare POPC rate.
-TILED_L15D4_ISSUE_ACTIVE = 0.542
-TILED_L15D4_ALU_PIPE = 0.573
+# Issue slots: each of an SM's 4 sub-partitions issues one warp instruction per clock (the IADD3
+# and IMNMX probes reach 128 lanes/clk/SM = 4 warp instructions).
+ISSUE_PER_SM_CLK = 4.0
+# ncu figures of one launch of the whole-tile tiled pass (tiled_kernel) per workload, from one
+# `ncu --set full --clock-control none -k regex:tiled_kernel -c 1` capture of the current kernel
+# (MOTIF_NO_GRAPH=1 so that ncu lists it): smsp__inst_executed.sum (warp instructions), DRAM
+# bytes read + written, smsp__issue_active and the ALU pipe's share.  Null entries: not captured.
+TILED_NCU = {
+    "l15d4_n20_t600_seed2": {"inst": 369165171, "dram_bytes": 261888, "issue_active": 0.589,
+                             "alu_pipe": 0.633},
+}
 
 
 def parse():
@@ -360,6 +363,13 @@ def run_ours(args):
     assert codes.size >= 1 and m.motif_encode(job.consensus) in set(codes.tolist()), \
         "result check failed"
     compares, unit_steps = m.motif_count_work(plan)
+    st_k = m.motif_stats(plan)
+    tiled_units = None
+    if st_k["kernel"] == m.KERNEL_TILED:
+        try:
+            tiled_units = m.motif_count_tiled_work(plan)  # the tiled pass's own work units
+        except m.MotifError:  # split into sequence blocks: no whole-tile counts
+            tiled_units = None
     if shard:  # the whole job's canonical tally: every rank's range
         cmp_all = torch.tensor([compares, unit_steps], dtype=torch.int64, device="cuda")
         dist.all_reduce(cmp_all)
@@ -415,8 +425,7 @@ def run_ours(args):
     # DRAM traffic per launch of the timed kernel, from an ncu capture of the tiled pass on the
     # default workload (dram__bytes_read.sum + dram__bytes_write.sum of its first step launch);
     # other kernels and workloads were not captured: null.
-    traffic = (TILED_L15D4_DRAM_BYTES if (kname == "TILED" and workload == "l15d4_n20_t600_seed2"
-                                          and args.seed == "all") else None)
+    traffic = None
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
             "unit": "G window-compares/s (1 POPC each)", "frac": achieved / peak,
             "traffic": traffic,
@@ -428,13 +437,36 @@ def run_ours(args):
             "note": ("frac > 1: the %s kernel factors the Hamming distance over shared candidate "
                      "prefixes, so one POPC or bit test resolves many algorithmic compares; see "
                      "roofline_cand for the per-compare kernel" % kname) if kname != "CAND" else ""}
-    if kname == "TILED" and workload == "l15d4_n20_t600_seed2":
-        # its own bound, from the committed ncu capture of this kernel on this workload
-        roof["issue"] = {"issue_active_frac": TILED_L15D4_ISSUE_ACTIVE,
-                         "alu_pipe_frac": TILED_L15D4_ALU_PIPE,
-                         "source": "ncu --set full, one launch of this kernel on this workload"}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / (POPC_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
+    if kname == "TILED" and tiled_units and not shard:
+        # The tiled pass's own roofline: it is bound by instruction issue (integer ALU work,
+        # shuffles, shared loads; DRAM traffic is the packed windows once).  achieved = its
+        # unit count (tile-sequence visits, counted live by motif_count_tiled_work) x warp
+        # instructions per visit (ncu's smsp__inst_executed of one launch / the same visits)
+        # / the kernel's event-timed device time; peak = 4 issue slots per SM per clock.
+        ncu = TILED_NCU.get(workload, {}) if args.seed == "all" else {}
+        peak_i = ISSUE_PER_SM_CLK * sms * max_mhz * 1e6
+        per_compare = dict(roof)
+        per_compare["note"] = ("the per-compare recipe (one POPC per algorithmic compare): the "
+                               "tiled pass resolves a window for a whole tile per filter POPC, "
+                               "so this ratio is not a roofline fraction")
+        ipv = ncu["inst"] / tiled_units["visits"] if ncu.get("inst") else None
+        ach_i = tiled_units["visits"] * ipv / (step_ms / 1e3) if ipv else None
+        roof = {"bound": "issue", "kernel": "tiled_kernel (whole-tile prefix-tiled pass)",
+                "unit": "G warp-instructions/s",
+                "achieved": ach_i / 1e9 if ach_i else None, "peak": peak_i / 1e9,
+                "frac": ach_i / peak_i if ach_i else None,
+                "traffic": ncu.get("dram_bytes"),
+                "peak_basis": "4 warp instructions issued per clock per SM (IADD3 probe: 128 "
+                              "lanes/clk/SM) x %d SMs x %.0f MHz (max SM clock)" % (sms, max_mhz),
+                "units_per_search": tiled_units, "warp_instructions_per_visit": ipv,
+                "warp_instructions_per_search": ncu.get("inst"),
+                "ncu": {k: ncu.get(k) for k in ("issue_active", "alu_pipe")},
+                "step_kernel_ms": step_ms, "sort_ms": sort_ms,
+                "per_compare_popc": per_compare}
+        if ach_i and clocks and clocks.get("sm_mhz"):
+            roof["frac_at_observed_clock"] = ach_i / (ISSUE_PER_SM_CLK * sms * clocks["sm_mhz"] * 1e6)
     def per_candidate_leg(kernel, label, cpt):
         """A per-candidate kernel on a sub-range of the same workload (full per-compare work)."""
         o = m.torch_opts(stream=stream, kernel=kernel, cands_per_thread=cpt,
@@ -611,9 +643,16 @@ def run_batch(args):
             m.motif_search(pl)
             dt = time.perf_counter() - t1
             stp = m.motif_stats(pl)
+            # work items of its search: 65,536-candidate tiles (tiled pass), else 256-candidate
+            # groups per 32 lanes; a job with at least a grid's worth keeps every SM busy alone
+            items = (4 ** j.l + 65535) // 65536 if stp["kernel"] == m.KERNEL_TILED else 1 << 40
             per_job.append({"l": j.l, "d": j.d, "n": j.n, "t": j.t, "survivors": int(r.size),
                             "plain_ms": 1e3 * dt, "search_ms": stp["search_ms"],
-                            "sort_ms": stp["sort_ms"]})
+                            "sort_ms": stp["sort_ms"], "fills_gpu": items >= stp["grid"]})
+        # Amdahl bound: a job that fills the GPU alone gains nothing from sharing it, so the
+        # batch takes at least those jobs' own search time; the ratio cannot exceed
+        # plain_ms / that time, however cheap the rest becomes.
+        full_ms = sum(x["search_ms"] for x in per_job if x["fills_gpu"])
         per_job.sort(key=lambda x: -x["plain_ms"])
         phases = []  # the batch's device phase split: median over a few calls
         for _ in range(5):
@@ -632,6 +671,9 @@ def run_batch(args):
             "plain_jobs_per_s": len(js) / t_plain, "batched_jobs_per_s": len(js) / t_batch,
             "plain_compares_per_s": compares / t_plain, "batched_compares_per_s": compares / t_batch,
             "batched_over_plain": t_plain / t_batch,
+            "jobs_filling_gpu": sum(1 for x in per_job if x["fills_gpu"]),
+            "filling_jobs_search_ms": full_ms,
+            "ratio_bound_amdahl": (1e3 * t_plain / full_ms) if full_ms > 0 else None,
             "batch_device_steps_ms": stb["search_ms"], "batch_device_sort_ms": stb["sort_ms"],
             "batch_copy_to_host_ms": stb["queue_ms"],
             "plain_device_ms": sum(x["search_ms"] + x["sort_ms"] for x in per_job),

@@ -247,6 +247,24 @@ int motif_count_compares(motif_plan p, uint64_t* out);
  * pointer may be NULL. */
 int motif_count_work(motif_plan p, uint64_t* compares, uint64_t* unit_steps);
 
+/* Work units of the whole-tile prefix-tiled pass (the tiled form of the Sec. III.A compare; not
+ * in the paper, whose compare is per l-mer): for a plan whose search runs that pass
+ * (motif_stats' kernel is MOTIF_KERNEL_TILED and its output is not split into sequence blocks),
+ * one search by a counting build of the same kernel fills units[0..7):
+ *   [0] tile-sequence visits (a tile is 65,536 candidates sharing their first l - 8 bases; it
+ *       visits sequences in order until none of its candidates is left: the skip),
+ *   [1] windows filtered (W per visit),
+ *   [2] map marks (distinct candidates marked by windows at tile-prefix distance exactly d),
+ *   [3] listed windows (tile-prefix distance below d; for l <= 16 the filter takes windows in
+ *       fours, and a row's padding slots up to a multiple of 4, copies of its last window, are
+ *       listed with it),
+ *   [4] scan rounds (per visit, warps with a live lane x ceil(listed / 32)),
+ *   [5] warp hit iterations (per scan round, the largest hit count of one live lane of the warp),
+ *   [6] lane hits (suffix-ball ORs of live lanes).
+ * The codes of that search land in the plan's own buffers; the next motif_search repeats it.
+ * Blocking.  MOTIF_ERR_STATE for other plans or before a load. */
+int motif_count_tiled_work(motif_plan p, uint64_t* units);
+
 /* For a plan with MOTIF_SEED_NEIGHBOURHOOD: *out receives how many candidates of its range lie
  * within d of some window of the first loaded sequence (the candidates its search scans from
  * the second sequence on).  Blocking.  MOTIF_ERR_STATE for other plans or before a load. */

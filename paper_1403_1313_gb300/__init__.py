@@ -25,7 +25,7 @@ __all__ = [
     "motif_server_opts", "motif_opts_default", "motif_plan_create", "motif_plan_destroy",
     "motif_load_seqs", "motif_load_seqs_device", "motif_load_seqs_var", "motif_fasta_parse",
     "read_fasta", "motif_search", "motif_search_device",
-    "motif_count_compares", "motif_count_work", "motif_kernel_launches", "motif_stats", "motif_batch_search", "motif_autotune",
+    "motif_count_compares", "motif_count_work", "motif_count_tiled_work", "motif_kernel_launches", "motif_stats", "motif_batch_search", "motif_autotune",
     "motif_tune_cache_save", "motif_tune_cache_load", "motif_server_start", "motif_server_stop",
     "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
@@ -151,6 +151,7 @@ def _load():
             "motif_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "motif_encode": (ctypes.c_int, [ctypes.c_char_p, i32, u64p]),
             "motif_decode": (ctypes.c_int, [u64, i32, ctypes.c_char_p]),
+            "motif_count_tiled_work": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint64)]),
             "motif_probe_rate": (ctypes.c_int, [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "motif_version": (ctypes.c_char_p, []),
         }
@@ -380,6 +381,17 @@ def motif_count_work(plan: Plan) -> tuple[int, int]:
     c, u = ctypes.c_uint64(0), ctypes.c_uint64(0)
     _check(_load().motif_count_work(plan, ctypes.byref(c), ctypes.byref(u)), "motif_count_work")
     return int(c.value), int(u.value)
+
+
+TILED_UNITS = ["visits", "windows_filtered", "map_marks", "listed", "scan_rounds",
+               "warp_hit_iterations", "lane_hits"]
+
+
+def motif_count_tiled_work(plan: Plan) -> dict:
+    """Work units of the whole-tile tiled pass of one search (names in TILED_UNITS)."""
+    u = (ctypes.c_uint64 * len(TILED_UNITS))()
+    _check(_load().motif_count_tiled_work(plan, u), "motif_count_tiled_work")
+    return dict(zip(TILED_UNITS, (int(x) for x in u)))
 
 
 def motif_kernel_launches() -> int:

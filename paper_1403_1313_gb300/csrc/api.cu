@@ -329,7 +329,10 @@ int plan_configure(motif_plan_s* p) {
   p->tiled_in_batch = tiled_ok;
   // A split search runs on the step kernel variant that has the split; its occupancy decides the
   // grid.
-  p->lkind = launch_kind(kind, pv, p->tiled && p->seq_block > 0);
+  // A tiled plan runs the kernel whose only pass is the tiled pass (split plans: the step kernel
+  // variant with the split); its dynamic shared memory is that of the GROUP kernel, which covers
+  // the tile map and the list heads.
+  p->lkind = launch_kind(kind, pv, p->tiled && p->seq_block > 0, p->tiled);
   if (p->lkind != kind) {
     if (step_kernel_attrs(p->lkind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
     int ps = step_max_ctas_per_sm(p->lkind, pv, block, smem);
@@ -1166,6 +1169,47 @@ int motif_count_work(motif_plan p, uint64_t* compares, uint64_t* unit_steps) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return status_from_cuda(e);
   *unit_steps = total;
+  return MOTIF_OK;
+}
+
+int motif_count_tiled_work(motif_plan p, uint64_t* units) {
+  if (!p || !units) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  if (p->lkind != kKindTiled) return MOTIF_ERR_STATE;  // a plan that runs the whole-tile pass
+  DeviceGuard g(p->device);
+  int rc = check_alphabet(p);
+  if (rc) return rc;
+  for (int i = 0; i < kTiledUnits; ++i) units[i] = 0;
+  if (p->W <= 0 || p->hi <= p->lo || p->nchunks == 0 || p->empty_row) return MOTIF_OK;
+  rc = plan_ensure_buffers(p);
+  if (rc) return rc;
+  // One search by the counting instantiation of the tiled kernel, from its own descriptor (the
+  // plan's uploaded one stays as it is), into the plan's output buffers.
+  const size_t bytes = sizeof(JobDesc) + 16 * kTiledUnits;
+  char* scratch = (char*)plan_alloc(p, bytes);
+  if (!scratch) return MOTIF_ERR_OOM;
+  JobDesc* d_jd = reinterpret_cast<JobDesc*>(scratch);
+  unsigned long long* d_units = reinterpret_cast<unsigned long long*>(scratch + sizeof(JobDesc));
+  JobDesc jd;
+  fill_desc(p, &jd, p->d_out, (uint64_t)p->out_cap);
+  jd.units = d_units;
+  unsigned long long h[kTiledUnits] = {};
+  cudaError_t e = cudaMemcpyAsync(d_jd, &jd, sizeof(jd), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_units, 0, 8 * kTiledUnits, p->stream);
+  if (e == cudaSuccess && p->bitmap) e = cudaMemsetAsync(p->d_bitmap, 0, p->bm_words * 4, p->stream);
+  if (e == cudaSuccess) e = step_kernel_attrs(kKindTiledCount, p->p, p->smem);
+  if (e == cudaSuccess) e = launch_init_steps(p->d_state, 1, p->d_ctl, 0, 0, 0, p->stream);
+  if (e == cudaSuccess) {
+    rc = run_steps(kKindTiledCount, p->p, d_jd, p->d_state, 1, p->d_ctl, p->grid, p->block,
+                   p->smem, max_steps_of(p), true, timeout_of(p), p->stream, nullptr);
+    if (rc == MOTIF_OK)
+      e = cudaMemcpyAsync(h, d_units, sizeof(h), cudaMemcpyDeviceToHost, p->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  plan_free(p, scratch, bytes);
+  if (e != cudaSuccess) return status_from_cuda(e);
+  if (rc) return rc;
+  for (int i = 0; i < kTiledUnits; ++i) units[i] = h[i];
   return MOTIF_OK;
 }
 

@@ -183,10 +183,14 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       block = p->block;
       timeout = std::max(timeout, p->opts.timeout_ms > 0 ? p->opts.timeout_ms : 60000);
     }
-    // The split-capable kernel variant only where a job of the table is split.
-    bool split = false;
-    for (const JobDesc& jd : descs) split = split || jd.seq_block > 0;
-    const int lkind = launch_kind(kind, pv, split);
+    // The split-capable kernel variant only where a job of the table is split; the tiled-only
+    // kernel where every job runs the whole-tile tiled pass.
+    bool split = false, all_tiled = true;
+    for (const JobDesc& jd : descs) {
+      split = split || jd.seq_block > 0;
+      all_tiled = all_tiled && jd.tiled;
+    }
+    const int lkind = launch_kind(kind, pv, split, all_tiled);
     if (step_kernel_attrs(lkind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
     grid = step_max_ctas_per_sm(lkind, pv, block, smem) * plans[ids[0]]->sms;
     if (grid <= 0) return MOTIF_ERR_ARG;

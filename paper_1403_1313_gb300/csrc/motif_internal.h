@@ -45,6 +45,7 @@ struct JobDesc {
   uint64_t* out;             // accepted codes, appended
   uint64_t out_cap;
   const uint64_t* ball;      // GROUP: Hamming-ball table for ks (see ball_table_words)
+  unsigned long long* units; // counting launches (kKindTiledCount): kTiledUnits counters
   uint32_t* bitmap;          // non-null: accepted codes set bit (code - bm_base) here instead of
   uint64_t bm_base;          //   being appended to out (bm_base is a multiple of 64)
   const uint8_t* valid;      // ragged / masked rows: [n][wstride] window flags (null = all valid);
@@ -111,11 +112,28 @@ cudaError_t launch_ball_table(uint64_t* table, int ks, cudaStream_t s);
 // MOTIF_KERNEL_GROUP; launches that hold no split job use the plain GROUP kernel, whose
 // whole-tile loop compiles without the split's code.
 constexpr int kKindTiledSplit = MOTIF_KERNEL_BITSLICE + 1;
-inline int launch_kind(int kind, int p, bool split) {
-  return split && kind == MOTIF_KERNEL_GROUP && p == 4 ? kKindTiledSplit : kind;
+// kKindTiled (p = 4) is the launch-only kind of the kernel whose only pass is the whole-tile
+// prefix-tiled pass; a launch uses it when every job of its table runs that pass
+// (JobDesc::tiled, JobDesc::seq_block == 0).
+constexpr int kKindTiled = kKindTiledSplit + 1;
+// kKindTiledCount (p = 4): the same kernel also adding the tiled pass's unit counts to
+// JobDesc::units (motif_count_tiled_work only).
+constexpr int kKindTiledCount = kKindTiledSplit + 2;
+constexpr int kLaunchKinds = kKindTiledCount + 1;
+// Unit counts of the whole-tile tiled pass (JobDesc::units, motif_count_tiled_work), in order:
+// tile-sequence visits, windows filtered (W per visit), map marks (windows at tile-prefix
+// distance d), listed windows (distance below d), scan rounds (live warps x ceil(listed / 32)),
+// warp hit iterations (per scan round the largest hit count of a live lane of the warp), lane hits.
+constexpr int kTiledUnits = 7;
+// The step kernel variant of a launch: `split` when a job of the table is split into sequence
+// blocks, `all_tiled` when every job of the table runs the tiled pass.
+inline int launch_kind(int kind, int p, bool split, bool all_tiled = false) {
+  if (kind != MOTIF_KERNEL_GROUP || p != 4) return kind;
+  if (split) return kKindTiledSplit;
+  return all_tiled ? kKindTiled : kind;
 }
-// Dynamic shared memory of a step kernel variant: kind is a unit kind (MOTIF_KERNEL_*) or
-// kKindTiledSplit.
+// Dynamic shared memory of a step kernel variant: kind is a unit kind (MOTIF_KERNEL_*) or a
+// launch-only kind (kKindTiledSplit, kKindTiled).
 size_t step_smem_bytes(int kind, int p, int wstride, int block);
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem);
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem);

@@ -837,7 +837,9 @@ __device__ __forceinline__ void filter_packed4(const uint2* __restrict__ row,
 // One item of the tiled pass.  SPLIT = false: the tile at group offset tbase, walked through
 // every sequence, its survivors appended (or ORed into the bitmap).  SPLIT = true: the tile and
 // the sequences [s_begin, s_end), its survivors ANDed into the bitmap.
-template <bool SPLIT>
+// COUNT (counting launches, motif_count_tiled_work): the same pass also adds its unit counts to
+// jd.units, see kTiledUnits.
+template <bool SPLIT, bool COUNT = false>
 __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
                             unsigned long long tbase, int s_begin, int s_end, uint32_t* head,
                             uint32_t* map, unsigned* s_cnt /* [2] */) {
@@ -857,9 +859,11 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
   code_planes(g, E, O);  // prefix planes (l-4 bases); the lane's P2 code is tid
   const uint32_t P1E = E >> 4, P1O = O >> 4;  // identical in every lane of the tile
   if (tid == 0) s_cnt[SPLIT ? (s_begin & 1) : 0] = 0;
+  unsigned long long u_visits = 0, u_marks = 0, u_rounds = 0, u_witer = 0, u_hits = 0, u_list = 0;
   int live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
   for (int s = SPLIT ? s_begin : 0; s < (SPLIT ? s_end : jd.n) && live; ++s) {
     unsigned* cnt = s_cnt + (s & 1);
+    if (COUNT) ++u_visits;
     // 1. filter the windows by the shared prefix (the list count was zeroed before the
     //    barrier that precedes this phase)
     const uint2* row = jd.planes + (size_t)s * wcap;
@@ -893,6 +897,15 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     __syncthreads();
     const int K = (int)*cnt;
     const bool lane_live = any_set<KS>(alive);
+    if (COUNT) {
+      u_list += (unsigned long long)K;
+      // the tile map's bits are the windows at prefix distance d (one candidate each); read
+      // here before this lane clears its bits
+      const uint4* own = reinterpret_cast<const uint4*>(map) + 2 * tid;
+      const uint4 m0 = own[0], m1 = own[1];
+      u_marks += __popc(m0.x) + __popc(m0.y) + __popc(m0.z) + __popc(m0.w) + __popc(m1.x) +
+                 __popc(m1.y) + __popc(m1.z) + __popc(m1.w);
+    }
     // 2. take this lane's bits of the map (the P2 code of lane tid is tid) and clear them;
     //    then scan 32 listed entries at a time: a warp transpose turns the entries' words for
     //    this warp's 32 lanes into one 32-bit hit mask per lane.  3. OR in each hit's suffix ball.
@@ -919,6 +932,11 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
         }
         x = warp_transpose32(x, lane);
         if (!lane_live) x = 0;
+        if (COUNT) {
+          ++u_rounds;
+          u_hits += __popc(x);
+          u_witer += __reduce_max_sync(kFull, (unsigned)__popc(x));
+        }
         while (x) {
           const int i = __ffs(x) - 1;
           x &= x - 1;
@@ -930,6 +948,25 @@ __device__ void group_tiled(const JobDesc& jd, JobState* st, const Pass& p,
     for (int i = 0; i < 4; ++i) alive.w[i] &= matched.w[i];
     // One barrier: the list may be rebuilt, and the tile stops once no lane has a live candidate.
     live = __syncthreads_or(any_set<KS>(alive) ? 1 : 0);
+  }
+  if (COUNT) {
+    // per tile: visits, windows filtered, listed and map marks once (thread 0 / summed map
+    // bits); scan rounds and warp hit iterations once per warp; hits of every lane
+    for (int o = 16; o > 0; o >>= 1) {
+      u_marks += __shfl_down_sync(kFull, u_marks, o);
+      u_hits += __shfl_down_sync(kFull, u_hits, o);
+    }
+    if (tid == 0) {
+      atomicAdd(jd.units + 0, u_visits);
+      atomicAdd(jd.units + 1, u_visits * (unsigned long long)jd.W);
+      atomicAdd(jd.units + 3, u_list);
+    }
+    if (lane == 0) {
+      atomicAdd(jd.units + 2, u_marks);
+      atomicAdd(jd.units + 4, u_rounds);
+      atomicAdd(jd.units + 5, u_witer);
+      atomicAdd(jd.units + 6, u_hits);
+    }
   }
   if (SPLIT) {
     if (in_chunk) group_and_bitmap(jd, g, alive);
@@ -1261,6 +1298,72 @@ __global__ void seed_kernel(const uint64_t* __restrict__ codes0, int W,
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The step kernel of launches whose every job runs the whole-tile prefix-tiled pass (GROUP,
+// k = 4, JobDesc::tiled, no sequence blocks).  Same job walk, tile claiming and end of step as
+// step_kernel, with the per-group passes left out: compiled for kTiledMinBlocks resident CTAs per
+// SM (48 registers, no spills), against 64 registers and 4 CTAs for step_kernel<GROUP, 4>, and the
+// extra warps hide more of the tiled pass's latency.  Shared memory: the 8 KB tile map, then the
+// list heads.
+constexpr int kTiledMinBlocks = 5;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kMaxBlock, kTiledMinBlocks)
+tiled_kernel(const JobDesc* __restrict__ jobs, JobState* states, int njobs, StepCtl* ctl,
+             cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ JobDesc s_jd;
+  __shared__ Pass s_pass;
+  __shared__ int s_skip;
+  __shared__ unsigned s_tiles;
+  __shared__ int s_last;
+  __shared__ unsigned s_act[kMaxBlock / 32];
+  __shared__ unsigned long long s_tbase;
+  __shared__ unsigned s_tcnt[2];
+  const int tid = threadIdx.x;
+  const unsigned budget = ctl->tiles_per_warp * (blockDim.x >> 5);
+  const int first = ctl->rotate ? (int)(blockIdx.x % (unsigned)njobs) : 0;
+  if (tid == 0) s_tiles = 0;
+  uint32_t* map = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* head = map + 2048;
+  for (int i = tid; i < 2048; i += blockDim.x) map[i] = 0u;  // every tile leaves it cleared
+  for (int jj = 0; jj < njobs; ++jj) {
+    int j = first + jj;
+    if (j >= njobs) j -= njobs;
+    __syncthreads();
+    if (tid == 0) {
+      int skip = 1;
+      if (!ld_volatile(&states[j].done) && (budget == 0 || s_tiles < budget)) {
+        s_jd = jobs[j];
+        s_pass = make_pass(s_jd, &states[j]);
+        // only whole-tile tiled passes run here (the host routes no other job to this kernel)
+        skip = s_pass.mode != kTiled || s_jd.seq_block > 0 ||
+               ld_volatile(&states[j].cursor) >= s_pass.work;
+      }
+      s_skip = skip;
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    const JobDesc& jd = s_jd;
+    const Pass p = s_pass;
+    JobState* st = &states[j];
+    for (;;) {
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long b = ~0ull;
+        if (budget == 0 || atomicAdd(&s_tiles, blockDim.x >> 5) < budget)
+          b = atomicAdd(&st->cursor, (unsigned long long)blockDim.x);
+        s_tbase = b;
+      }
+      __syncthreads();
+      const unsigned long long b = s_tbase;
+      if (b >= p.work) break;
+      group_tiled<false, COUNT>(jd, st, p, b, 0, 0, head, map, s_tcnt);
+    }
+  }
+  finish_step(jobs, states, njobs, ctl, cond, use_cond, &s_last, s_act);
+}
+
 __global__ void ball_kernel(uint64_t* table, int ks) {
   const int nv = 1 << (2 * ks);
   const int nw = mask_words(ks);
@@ -1289,6 +1392,10 @@ const void* step_fn() {
 
 const void* step_function(int kind, int p) {
   if (kind == kKindTiledSplit) return p == 4 ? step_fn<MOTIF_KERNEL_GROUP, 4, true>() : nullptr;
+  if (kind == kKindTiled)
+    return p == 4 ? reinterpret_cast<const void*>(&tiled_kernel<false>) : nullptr;
+  if (kind == kKindTiledCount)
+    return p == 4 ? reinterpret_cast<const void*>(&tiled_kernel<true>) : nullptr;
   if (kind == MOTIF_KERNEL_CAND) {
     switch (p) {
       case 1: return step_fn<MOTIF_KERNEL_CAND, 1>();
@@ -1315,6 +1422,8 @@ const void* step_function(int kind, int p) {
 }  // namespace
 
 size_t step_smem_bytes(int kind, int p, int wstride, int block) {
+  if (kind == kKindTiled || kind == kKindTiledCount)  // the tile map, the list heads
+    return 8192 + (size_t)wstride * 4;
   if (kind == kKindTiledSplit) kind = MOTIF_KERNEL_GROUP;
   if (kind == MOTIF_KERNEL_CAND) return (size_t)kMaxStageSeqs * wstride * 8;
   if (kind == MOTIF_KERNEL_BITSLICE)  // 4 words per base position (l <= 32) per 32 windows,
@@ -1335,9 +1444,9 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
 // share the kernels, and one caller's smaller request must not break another's launch.
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem) {
   static std::mutex mu;
-  static size_t set[kKindTiledSplit + 1][kMaxKs + 1] = {};
+  static size_t set[kLaunchKinds][kMaxKs + 1] = {};
   const void* f = step_function(kind, p);
-  if (!f || kind < 1 || kind > kKindTiledSplit || p < 1 || p > kMaxKs)
+  if (!f || kind < 1 || kind >= kLaunchKinds || p < 1 || p > kMaxKs)
     return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> g(mu);
   if (smem <= set[kind][p]) return cudaSuccess;

@@ -25,14 +25,19 @@ namespace motif_batch {
 
 // Per-device streams, job-table buffers and step graphs reused across batch calls.
 struct BatchCtx {
-  cudaStream_t stream = nullptr;       // steps, then each job's sort / compaction
-  cudaStream_t count_stream = nullptr; // each job's final count, once its sort is done
-  cudaStream_t copy_stream = nullptr;  // each job's codes to the host, once its count is known
+  cudaStream_t stream = nullptr;       // steps, then the jobs' sorts / compactions
+  cudaStream_t copy_stream = nullptr;  // each job's codes to the host, once the counts are known
   JobDesc* d_jobs = nullptr;
   JobState* d_states = nullptr;
   StepCtl* d_ctl = nullptr;
-  unsigned long long* h_counts = nullptr;  // pinned: the final count of each job
-  std::vector<cudaEvent_t> sorted, counted;
+  JobState* h_states = nullptr;            // pinned: every job's state after its sort
+  SortTask* h_sort_tasks = nullptr;        // pinned staging of the sort / compaction tasks
+  BitmapTask* h_bm_tasks = nullptr;
+  unsigned* h_bm_first = nullptr;
+  SortTask* d_sort_tasks = nullptr;
+  BitmapTask* d_bm_tasks = nullptr;
+  unsigned* d_bm_first = nullptr;
+  cudaEvent_t sorts_done = nullptr;    // the group's sorts and compactions, for the copy stream
   cudaEvent_t copies_done = nullptr;
   // Instantiated step graphs by (kind, p, jobs, grid, block, smem, max_steps); they name d_jobs,
   // d_states and d_ctl, so they are dropped when those are re-allocated.
@@ -50,37 +55,43 @@ void drop_graphs(BatchCtx& c) {
 int ensure_ctx(int dev, int njobs, BatchCtx** out) {
   if (dev < 0 || dev >= 64) return MOTIF_ERR_ARG;
   BatchCtx& c = g_ctx[dev];
-  for (cudaStream_t* s : {&c.stream, &c.count_stream, &c.copy_stream})
+  for (cudaStream_t* s : {&c.stream, &c.copy_stream})
     if (!*s && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess)
       return MOTIF_ERR_CUDA;
-  if (!c.copies_done &&
-      cudaEventCreateWithFlags(&c.copies_done, cudaEventDisableTiming) != cudaSuccess)
-    return MOTIF_ERR_CUDA;
+  for (cudaEvent_t* ev : {&c.copies_done, &c.sorts_done})
+    if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess)
+      return MOTIF_ERR_CUDA;
   if (njobs > c.cap) {
     drop_graphs(c);
     if (c.d_jobs) cudaFree(c.d_jobs);
     if (c.d_states) cudaFree(c.d_states);
-    if (c.h_counts) cudaFreeHost(c.h_counts);
+    for (void* h : {(void*)c.h_states, (void*)c.h_sort_tasks, (void*)c.h_bm_tasks,
+                    (void*)c.h_bm_first})
+      if (h) cudaFreeHost(h);
+    for (void* d : {(void*)c.d_sort_tasks, (void*)c.d_bm_tasks, (void*)c.d_bm_first})
+      if (d) cudaFree(d);
     c.d_jobs = nullptr;
     c.d_states = nullptr;
-    c.h_counts = nullptr;
+    c.h_states = nullptr;
+    c.h_sort_tasks = nullptr;
+    c.h_bm_tasks = nullptr;
+    c.h_bm_first = nullptr;
+    c.d_sort_tasks = nullptr;
+    c.d_bm_tasks = nullptr;
+    c.d_bm_first = nullptr;
     c.cap = 0;
     if (!c.d_ctl && cudaMalloc(&c.d_ctl, sizeof(StepCtl)) != cudaSuccess) return MOTIF_ERR_OOM;
     const int cap = std::max(njobs, 64);
     if (cudaMalloc(&c.d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
         cudaMalloc(&c.d_states, sizeof(JobState) * cap) != cudaSuccess ||
-        cudaHostAlloc((void**)&c.h_counts, sizeof(unsigned long long) * cap, 0) != cudaSuccess)
+        cudaHostAlloc((void**)&c.h_states, sizeof(JobState) * cap, 0) != cudaSuccess ||
+        cudaHostAlloc((void**)&c.h_sort_tasks, sizeof(SortTask) * cap, 0) != cudaSuccess ||
+        cudaHostAlloc((void**)&c.h_bm_tasks, sizeof(BitmapTask) * cap, 0) != cudaSuccess ||
+        cudaHostAlloc((void**)&c.h_bm_first, sizeof(unsigned) * (cap + 1), 0) != cudaSuccess ||
+        cudaMalloc(&c.d_sort_tasks, sizeof(SortTask) * cap) != cudaSuccess ||
+        cudaMalloc(&c.d_bm_tasks, sizeof(BitmapTask) * cap) != cudaSuccess ||
+        cudaMalloc(&c.d_bm_first, sizeof(unsigned) * (cap + 1)) != cudaSuccess)
       return MOTIF_ERR_OOM;
-    while ((int)c.sorted.size() < cap) {
-      cudaEvent_t a = nullptr, b = nullptr;
-      if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return MOTIF_ERR_CUDA;
-      if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
-        cudaEventDestroy(a);
-        return MOTIF_ERR_CUDA;
-      }
-      c.sorted.push_back(a);
-      c.counted.push_back(b);
-    }
     c.cap = cap;
   }
   *out = &c;
@@ -213,7 +224,6 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     // Leaves nothing in flight (copies into the caller's buffers included) before returning.
     auto fail = [&](int status) {
       cudaStreamSynchronize(c->stream);
-      cudaStreamSynchronize(c->count_stream);
       cudaStreamSynchronize(c->copy_stream);
       for (auto& x : ev) cudaEventDestroy(x);
       return status;
@@ -228,22 +238,14 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(status_from_cuda(e));
-    // Sort/dedup (or compact) every job's codes in its own buffer on the batch stream.  Once a
-    // job's sort is done its final count goes to pinned memory on the count stream; the host
-    // waits for one count at a time and queues that job's codes to the host on the copy stream,
-    // so the copies overlap the sorts of the jobs after them.
-    // Largest results first, so that the longest copies start earliest: a list job's size is its
-    // count before dedup, a bitmap job's (counted only when compacted) the caller's capacity.
-    std::vector<size_t> order(ids.size());
-    std::vector<unsigned long long> size_of(ids.size());
-    for (size_t i = 0; i < ids.size(); ++i) {
-      order[i] = i;
-      size_of[i] = plans[ids[i]]->bitmap ? (unsigned long long)capacities[ids[i]] : st[i].out_count;
-    }
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t a, size_t b) { return size_of[a] > size_of[b]; });
+    // Sort/dedup (or compact) every job's codes in its own buffer on the batch stream, the jobs
+    // together: one launch sorts every list of at most 4096 codes (a CTA per job), a radix sort
+    // runs per larger list, and three launches compact every bitmap.  One copy then brings back
+    // every final count, and each job's codes go to the host on the copy stream, largest first.
+    int nsmall = 0, nbm = 0;
+    unsigned bm_blocks = 0;
     std::vector<char> sorted(ids.size(), 0);
-    for (const size_t i : order) {
+    for (size_t i = 0; i < ids.size(); ++i) {
       const int j = ids[i];
       motif_plan_s* p = plans[j];
       const unsigned long long found = st[i].out_count;
@@ -251,44 +253,65 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         redo[j] = 1;  // the plan's own buffer was too small: rerun this job alone below
         continue;
       }
-      if (p->bitmap) {  // compact the job's bitmap into its buffer (count into its state)
-        e = launch_bitmap_compact(p->d_bitmap, p->bm_words, p->bm_base, p->d_out, p->out_cap,
-                                  p->d_bm_scratch, &c->d_states[i].out_count, c->stream);
+      unsigned long long* cnt = &c->d_states[i].out_count;
+      if (p->bitmap) {
+        c->h_bm_first[nbm] = bm_blocks;
+        c->h_bm_tasks[nbm++] = BitmapTask{p->d_bitmap, p->bm_words, p->bm_base, p->d_out,
+                                          (long long)p->out_cap, p->d_bm_scratch, cnt};
+        bm_blocks += (unsigned)bitmap_task_blocks(p->bm_words);
+      } else if (found <= 4096) {
+        if (found > 1) c->h_sort_tasks[nsmall++] = SortTask{p->d_out, cnt, (long long)p->out_cap};
       } else {
-        if (found > 4096) {
-          const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
-          if (need > p->sort_bytes) {
-            plan_free(p, p->d_sort, p->sort_bytes);
-            p->d_sort = plan_alloc(p, need);
-            cudaStreamSynchronize(p->stream);  // the scratch is used on the batch stream
-            p->sort_bytes = p->d_sort ? need : 0;
-            if (p->g_sort) {  // a cached sort graph may name the old scratch
-              cudaGraphExecDestroy(p->g_sort);
-              p->g_sort = nullptr;
-            }
-            if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
+        const size_t need = sort_scratch_bytes(p->out_cap, p->sms);
+        if (need > p->sort_bytes) {
+          plan_free(p, p->d_sort, p->sort_bytes);
+          p->d_sort = plan_alloc(p, need);
+          cudaStreamSynchronize(p->stream);  // the scratch is used on the batch stream
+          p->sort_bytes = p->d_sort ? need : 0;
+          if (p->g_sort) {  // a cached sort graph may name the old scratch
+            cudaGraphExecDestroy(p->g_sort);
+            p->g_sort = nullptr;
           }
+          if (!p->d_sort) { statuses[j] = MOTIF_ERR_OOM; continue; }
         }
-        e = launch_sort_unique(p->d_out, &c->d_states[i].out_count, p->out_cap, 2 * p->l,
-                               p->d_sort, p->sms, (long long)found, c->stream);
+        e = launch_sort_unique(p->d_out, cnt, p->out_cap, 2 * p->l, p->d_sort, p->sms,
+                               (long long)found, c->stream);
+        if (e != cudaSuccess) return fail(status_from_cuda(e));
       }
-      if (e == cudaSuccess) e = cudaEventRecord(c->sorted[i], c->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->count_stream, c->sorted[i], 0);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&c->h_counts[i], &c->d_states[i].out_count, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, c->count_stream);
-      if (e == cudaSuccess) e = cudaEventRecord(c->counted[i], c->count_stream);
-      if (e != cudaSuccess) return fail(status_from_cuda(e));
       sorted[i] = 1;
     }
-    cudaEventRecord(ev[2], c->stream);  // sorts done
+    c->h_bm_first[nbm] = bm_blocks;
+    if (nsmall)
+      e = cudaMemcpyAsync(c->d_sort_tasks, c->h_sort_tasks, sizeof(SortTask) * nsmall,
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && nbm)
+      e = cudaMemcpyAsync(c->d_bm_tasks, c->h_bm_tasks, sizeof(BitmapTask) * nbm,
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && nbm)
+      e = cudaMemcpyAsync(c->d_bm_first, c->h_bm_first, sizeof(unsigned) * (nbm + 1),
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_small_sort_tasks(c->d_sort_tasks, nsmall, c->stream);
+    if (e == cudaSuccess)
+      e = launch_bitmap_compact_tasks(c->d_bm_tasks, c->d_bm_first, nbm, bm_blocks, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);  // sorts done
+    if (e == cudaSuccess) e = cudaEventRecord(c->sorts_done, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->h_states, c->d_states, sizeof(JobState) * ids.size(),
+                          cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(status_from_cuda(e));
+    std::vector<size_t> order;
+    for (size_t i = 0; i < ids.size(); ++i)
+      if (sorted[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+      return c->h_states[a].out_count > c->h_states[b].out_count;
+    });
+    e = cudaStreamWaitEvent(c->copy_stream, c->sorts_done, 0);
+    if (e != cudaSuccess) return fail(status_from_cuda(e));
     for (const size_t i : order) {
-      if (!sorted[i]) continue;
       const int j = ids[i];
       motif_plan_s* p = plans[j];
-      e = cudaEventSynchronize(c->counted[i]);
-      if (e != cudaSuccess) return fail(status_from_cuda(e));
-      const unsigned long long fc = c->h_counts[i];
+      const unsigned long long fc = c->h_states[i].out_count;
       if (fc > (unsigned long long)p->out_cap) {  // a bitmap job outgrew the plan's buffer
         redo[j] = 1;
         continue;
@@ -301,10 +324,8 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         continue;
       }
       if (fc) {
-        e = cudaStreamWaitEvent(c->copy_stream, c->sorted[i], 0);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(out_codes[j], p->d_out, fc * 8, cudaMemcpyDeviceToHost,
-                              c->copy_stream);
+        e = cudaMemcpyAsync(out_codes[j], p->d_out, fc * 8, cudaMemcpyDeviceToHost,
+                            c->copy_stream);
         if (e != cudaSuccess) return fail(status_from_cuda(e));
       }
     }

@@ -179,6 +179,29 @@ cudaError_t launch_seed_scatter(const uint64_t* codes0, int W, const uint64_t* p
 cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t base,
                                   uint64_t* out, int64_t cap, unsigned* scratch,
                                   unsigned long long* count, cudaStream_t s);
+// Many jobs at once (batches).  A SortTask sorts codes[0 .. *count) in place when
+// 1 < *count <= min(4096, cap) (one CTA per task; larger lists take launch_sort_unique).
+struct SortTask {
+  uint64_t* codes;
+  unsigned long long* count;
+  long long cap;
+};
+cudaError_t launch_small_sort_tasks(const SortTask* d_tasks, int ntasks, cudaStream_t s);
+// A BitmapTask compacts one bitmap as launch_bitmap_compact does; the tasks' blocks form one grid:
+// task k owns blocks [d_first[k], d_first[k+1]), bitmap_task_blocks(nwords) of them, and its
+// scratch holds at least that many words.
+struct BitmapTask {
+  const uint32_t* bm;
+  uint64_t nwords;
+  uint64_t base;
+  uint64_t* out;
+  long long cap;
+  unsigned* scratch;
+  unsigned long long* count;
+};
+uint64_t bitmap_task_blocks(uint64_t nwords);
+cudaError_t launch_bitmap_compact_tasks(const BitmapTask* d_tasks, const unsigned* d_first,
+                                        int ntasks, unsigned total_blocks, cudaStream_t s);
 cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, int64_t cap,
                                int key_bits, void* scratch, int sms, long long known_count,
                                cudaStream_t s);

@@ -28,16 +28,12 @@ __device__ __forceinline__ unsigned long long read_count(const unsigned long lon
 
 // ---- small path ----------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kSmallThreads) small_sort_kernel(uint64_t* codes,
-                                                                   unsigned long long* count,
-                                                                   long long cap,
-                                                                   cudaGraphConditionalHandle cond,
-                                                                   int use_cond) {
+// One CTA sorts codes[0 .. *count) in shared memory and drops repeats (a no-op unless
+// 1 < *count <= min(kSmallMax, cap)).
+__device__ void small_sort_block(uint64_t* codes, unsigned long long* count, long long cap,
+                                 unsigned long long n) {
   __shared__ uint64_t a[kSmallMax];
   __shared__ unsigned warp_tot[kSmallThreads / 32];
-  const unsigned long long n = read_count(count);
-  if (use_cond && threadIdx.x == 0)  // inside a graph: run the multi-CTA path only when needed
-    cudaGraphSetConditional(cond, (n > (unsigned long long)kSmallMax && n <= (unsigned long long)cap) ? 1u : 0u);
   if (n <= 1 || n > (unsigned long long)kSmallMax || n > (unsigned long long)cap) return;
   int size = 2;
   while ((unsigned long long)size < n) size <<= 1;
@@ -84,6 +80,23 @@ __global__ void __launch_bounds__(kSmallThreads) small_sort_kernel(uint64_t* cod
     if (keep & (1u << q)) codes[pos++] = a[first + q];
   __syncthreads();
   if (threadIdx.x == 0) *count = total;
+}
+
+__global__ void __launch_bounds__(kSmallThreads) small_sort_kernel(uint64_t* codes,
+                                                                   unsigned long long* count,
+                                                                   long long cap,
+                                                                   cudaGraphConditionalHandle cond,
+                                                                   int use_cond) {
+  const unsigned long long n = read_count(count);
+  if (use_cond && threadIdx.x == 0)  // inside a graph: run the multi-CTA path only when needed
+    cudaGraphSetConditional(cond, (n > (unsigned long long)kSmallMax && n <= (unsigned long long)cap) ? 1u : 0u);
+  small_sort_block(codes, count, cap, n);
+}
+
+// Many jobs' small lists at once: CTA b sorts task b's codes.
+__global__ void __launch_bounds__(kSmallThreads) small_sort_tasks_kernel(const SortTask* tasks) {
+  const SortTask t = tasks[blockIdx.x];
+  small_sort_block(t.codes, t.count, t.cap, read_count(t.count));
 }
 
 // ---- large path: LSD radix sort --------------------------------------------------------------
@@ -415,6 +428,124 @@ __global__ void __launch_bounds__(kBmThreads) bitmap_write_kernel(const uint32_t
   }
 }
 
+// ---- many jobs' bitmaps at once --------------------------------------------------------------
+// The blocks of all tasks form one grid: task k owns blocks [first[k], first[k+1]).  Each CTA
+// finds its task by binary search over `first` (ntasks + 1 entries).
+
+__device__ __forceinline__ int task_of_block(const unsigned* first, int ntasks, unsigned b) {
+  int lo = 0, hi = ntasks;  // first[lo] <= b < first[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (first[mid] <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kBmThreads) bitmap_count_tasks_kernel(const BitmapTask* tasks,
+                                                                       const unsigned* first,
+                                                                       int ntasks) {
+  __shared__ unsigned warp_tot[kBmThreads / 32];
+  const int k = task_of_block(first, ntasks, blockIdx.x);
+  const BitmapTask t = tasks[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t w0 = (uint64_t)(blockIdx.x - first[k]) * kBmWords;
+  unsigned c = 0;
+  for (int i = threadIdx.x; i < kBmWords; i += kBmThreads)
+    if (w0 + i < t.nwords) c += __popc(t.bm[w0 + i]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if (lane == 0) warp_tot[warp] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < kBmThreads / 32; ++w) tot += warp_tot[w];
+    t.scratch[blockIdx.x - first[k]] = tot;
+  }
+}
+
+// CTA k scans task k's block counts (as bitmap_scan_kernel does for one bitmap).
+__global__ void __launch_bounds__(kBmThreads) bitmap_scan_tasks_kernel(const BitmapTask* tasks,
+                                                                      const unsigned* first) {
+  const int k = blockIdx.x;
+  const BitmapTask t = tasks[k];
+  __shared__ unsigned warp_tot[kBmThreads / 32];
+  __shared__ unsigned carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nblk = (int)(first[k + 1] - first[k]);
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblk; b0 += kBmThreads) {
+    const int i = b0 + threadIdx.x;
+    const unsigned x = i < nblk ? t.scratch[i] : 0u;
+    unsigned incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int w = 0; w < kBmThreads / 32; ++w) {
+      if (w < warp) before += warp_tot[w];
+      total += warp_tot[w];
+    }
+    if (i < nblk) t.scratch[i] = carry + before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *t.count = carry;
+}
+
+// Writes every task's codes (as bitmap_write_kernel does for one bitmap).
+__global__ void __launch_bounds__(kBmThreads) bitmap_write_tasks_kernel(const BitmapTask* tasks,
+                                                                       const unsigned* first,
+                                                                       int ntasks) {
+  __shared__ unsigned warp_tot[kBmThreads / 32];
+  const int k = task_of_block(first, ntasks, blockIdx.x);
+  const BitmapTask t = tasks[k];
+  const unsigned blk = blockIdx.x - first[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint64_t wbase = (uint64_t)blk * kBmWords + (uint64_t)warp * (32 * kBmWordsPerLane);
+  uint32_t x[kBmWordsPerLane];
+  unsigned c = 0;
+#pragma unroll
+  for (int i = 0; i < kBmWordsPerLane; ++i) {
+    const uint64_t w = wbase + (uint64_t)i * 32 + lane;
+    x[i] = w < t.nwords ? t.bm[w] : 0u;
+    c += __popc(x[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if (lane == 0) warp_tot[warp] = c;
+  __syncthreads();
+  unsigned long long pos = t.scratch[blk];
+  for (int w = 0; w < warp; ++w) pos += warp_tot[w];
+#pragma unroll
+  for (int i = 0; i < kBmWordsPerLane; ++i) {
+    const unsigned cnt = __popc(x[i]);
+    unsigned excl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, excl, o);
+      if (lane >= o) excl += y;
+    }
+    const unsigned tot = __shfl_sync(kFull, excl, 31);
+    excl -= cnt;
+    unsigned nz = __ballot_sync(kFull, x[i] != 0u);
+    while (nz) {
+      const int src = __ffs(nz) - 1;
+      nz &= nz - 1;
+      const uint32_t xs = __shfl_sync(kFull, x[i], src);
+      const unsigned ps = __shfl_sync(kFull, excl, src);
+      if ((xs >> lane) & 1u) {
+        const unsigned long long q = pos + ps + __popc(xs & lt);
+        if (q < (unsigned long long)t.cap)
+          t.out[q] = t.base + ((wbase + (uint64_t)i * 32 + src) << 5) + lane;
+      }
+    }
+    pos += tot;
+  }
+}
+
 // Scratch layout: [keys: cap u64][hist: kDigits*ctas u32][per_cta raw: ctas][per_cta scan: ctas]
 size_t sort_scratch_bytes(int64_t cap, int sms) {
   const int ctas = radix_ctas(sms);
@@ -444,6 +575,25 @@ cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t 
   bitmap_scan_kernel<<<1, kBmThreads, 0, s>>>(scratch, (int)nblk, count);
   bitmap_write_kernel<<<(unsigned)nblk, kBmThreads, 0, s>>>(bm, nwords, base, scratch, out,
                                                             (long long)cap);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_sort_tasks(const SortTask* d_tasks, int ntasks, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  small_sort_tasks_kernel<<<ntasks, kSmallThreads, 0, s>>>(d_tasks);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+uint64_t bitmap_task_blocks(uint64_t nwords) { return (nwords + kBmWords - 1) / kBmWords; }
+
+cudaError_t launch_bitmap_compact_tasks(const BitmapTask* d_tasks, const unsigned* d_first,
+                                        int ntasks, unsigned total_blocks, cudaStream_t s) {
+  if (ntasks <= 0 || total_blocks == 0) return cudaSuccess;
+  bitmap_count_tasks_kernel<<<total_blocks, kBmThreads, 0, s>>>(d_tasks, d_first, ntasks);
+  bitmap_scan_tasks_kernel<<<ntasks, kBmThreads, 0, s>>>(d_tasks, d_first);
+  bitmap_write_tasks_kernel<<<total_blocks, kBmThreads, 0, s>>>(d_tasks, d_first, ntasks);
   note_launches(3);
   return cudaGetLastError();
 }

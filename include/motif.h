@@ -403,15 +403,16 @@ int motif_probe_rate(int32_t kind, int32_t iters, double* ops_per_sm_clk, double
 /* Sorts `count` codes at d_codes ascending and removes repeats, in place, without allocating
  * any device memory, and writes the number of distinct codes to *d_unique_count (one int64 in
  * device memory).  The paper has no counterpart: this serves callers that cannot allocate at
- * that point (code recording a CUDA graph by stream capture, a host whose framework allocator
- * owns all free device memory, loops that must not block on cudaMalloc / cudaFree).  Its
+ * that point (a host whose framework allocator owns all free device memory, loops that must not
+ * block on cudaMalloc / cudaFree).  Its
  * scratch is one fixed array inside the library (about 2.6 MB, held by every device that loads
  * the library until the process exits).  Limits and rules:
  *  - count <= 262144 (2^18); larger counts return MOTIF_ERR_CAPACITY and touch nothing;
  *  - key_bits in [1, 64]: the number of low bits that can be non-zero (2l for l-mer codes);
  *  - asynchronous on `stream` (a cudaStream_t; NULL = the legacy default stream);
- *  - the first call on a device looks up the array's device address, so make that first call
- *    before any stream capture begins;
+ *  - the first call on a device looks up the array's device address (again after the device's
+ *    context changes, e.g. after cudaDeviceReset), so make that first call before any stream
+ *    capture begins;
  *  - every call uses the same array: calls that overlap on the GPU race and must be serialised
  *    by the caller.
  * Errors: MOTIF_ERR_ARG, MOTIF_ERR_CAPACITY, MOTIF_ERR_CUDA. */

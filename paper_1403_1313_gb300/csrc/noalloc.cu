@@ -1,18 +1,22 @@
 // Sorting codes without allocating device memory.
 //
 // Some callers cannot allocate device memory at the point where they need their codes ordered:
-// code recording a CUDA graph by stream capture (where cudaMalloc is not permitted), code that
-// runs inside a framework whose allocator owns all free device memory, and latency-critical
-// loops that must never block on an allocator or on the implicit device synchronisation of
-// cudaMalloc / cudaFree.  motif_sort_codes_noalloc serves them: it runs the library's sort/dedup
-// kernels with their scratch taken from a fixed array compiled into the library.
+// code that runs inside a framework whose allocator owns all free device memory, and
+// latency-critical loops that must never block on an allocator or on the implicit device
+// synchronisation of cudaMalloc / cudaFree.  motif_sort_codes_noalloc serves them: it runs the
+// library's sort/dedup kernels with their scratch taken from a fixed array compiled into the
+// library.
 //
 // The array below is a static __device__ allocation: every GPU that loads the library holds it
 // (about 2.6 MB) until the process exits.  Host code cannot pass the symbol itself to a kernel —
 // on the host, g_noalloc_scratch names a host-side shadow, not device memory — so the first call
 // on each device looks up the array's device address with cudaGetSymbolAddress (with that device
-// current) and caches it.  Every call shares the array, so calls that overlap on the GPU (two
-// streams, or two host threads on one device) race on it and must be serialised by the caller.
+// current) and caches it, together with the device's current context: a call from another
+// context (after cudaDeviceReset, for instance) looks the address up again.  Every call shares
+// the array, so calls that overlap on the GPU (two streams, or two host threads on one device)
+// race on it and must be serialised by the caller.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "plan.h"
@@ -31,15 +35,38 @@ constexpr size_t kNoallocBytes = kNoallocCellOffset + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-// Per-device set-up: the scratch array's device address and the SM count.
+// Per-device set-up: the scratch array's device address and the SM count, and the context the
+// address belongs to.
 std::mutex g_mu;
 unsigned char* g_addr[64] = {};
 int g_sms[64] = {};
+CUcontext g_ctx[64] = {};
+
+// The calling thread's current context, through the driver entry point the runtime exposes (no
+// link against the driver library); null if it cannot be had.
+CUcontext current_context() {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (GetCurrent) nullptr;
+    }
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 int noalloc_setup(int dev, unsigned char** base, int* sms) {
   if (dev < 0 || dev >= 64) return MOTIF_ERR_ARG;
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_addr[dev]) {
+  const CUcontext ctx = current_context();
+  if (!g_addr[dev] || g_ctx[dev] != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -50,6 +77,7 @@ int noalloc_setup(int dev, unsigned char** base, int* sms) {
       return MOTIF_ERR_CUDA;
     g_addr[dev] = static_cast<unsigned char*>(p);
     g_sms[dev] = n < kNoallocMaxSms ? n : kNoallocMaxSms;
+    g_ctx[dev] = ctx;
   }
   *base = g_addr[dev];
   *sms = g_sms[dev];

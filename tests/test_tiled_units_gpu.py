@@ -89,7 +89,8 @@ def reference_units(seqs, l, d, tiles=None):
     (9, 2, 4, 60, 3, None), (10, 3, 5, 50, 8, None), (10, 1, 6, 80, 21, None),
     (8, 2, 3, 40, 5, None), (9, 4, 3, 30, 13, None), (11, 3, 3, 41, 17, None),
     (12, 2, 3, 38, 29, None), (16, 3, 3, 40, 7, (1000, 1040)),
-    (17, 3, 2, 26, 4, (5000, 5100))])  # l > 16: one window per filter lane
+    (17, 3, 2, 26, 4, (5000, 5100)), (17, 5, 3, 27, 9, (777, 800)),
+    (25, 4, 2, 33, 6, (12345, 12360))])  # l > 16: one window per filter lane
 def test_tiled_units_match_their_definitions(l, d, n, t, seed, tiles):
     job = fmgen.fm_job(n, t, l, d, seed)
     o = m.motif_opts_default()

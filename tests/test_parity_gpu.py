@@ -422,3 +422,33 @@ def test_bitslice_beyond_its_counter_falls_back_to_cand(l, d):
     m.motif_plan_destroy(plan)
     ref, _ = oracle.search(rows, l, d)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("name,kw", VARIANTS[:1] + VARIANTS[1:2] + VARIANTS[5:6] + VARIANTS[8:9],
+                         ids=["tiled", "group4", "cand1", "bitslice1"])
+@pytest.mark.parametrize("output", [m.OUTPUT_LIST, m.OUTPUT_BITMAP])
+def test_direct_launch_equals_oracle(name, kw, output):
+    """The step kernel launched from the host once per step (MOTIF_LAUNCH_DIRECT, the form
+    profilers list) gives the oracle's result, through the blocking and the device path."""
+    torch = pytest.importorskip("torch")
+    job = fmgen.fm_job(6, 120, 10, 2, 314)
+    ref, _ = oracle.search(job.rows(), job.l, job.d)
+    plan = m.motif_plan_create(job.n, job.t, job.l, job.d,
+                               m.torch_opts(launch=m.LAUNCH_DIRECT, output=output, **kw))
+    m.motif_load_seqs(plan, job.seqs)
+    assert np.array_equal(m.motif_search(plan), ref)
+    out = torch.zeros(1 << 14, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    m.motif_search_device(plan, out, out.numel(), cnt)
+    torch.cuda.synchronize()
+    c = int(cnt.item())
+    assert np.array_equal(out[:c].cpu().numpy().astype(np.uint64), ref)
+    m.motif_plan_destroy(plan)
+
+
+def test_launch_option_is_checked():
+    o = m.motif_opts_default()
+    o.launch = 7
+    with pytest.raises(m.MotifError) as e:
+        m.motif_plan_create(2, 20, 8, 1, o)
+    assert e.value.status == m.ERR_ARG

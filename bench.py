@@ -301,8 +301,11 @@ def run_ours(args):
     job = fmgen.fm_job(n, t, l, d, seed + (0 if shard or world == 1 else rank * 1000))
     workload = "l%dd%d_n%d_t%d_seed%d" % (l, d, n, t, seed)
     cands = 4 ** l
-    # This rank's contiguous share of the candidate space (the whole space at N = 1).
-    r_lo, r_hi = m.motif_shard_range(cands, rank, world) if shard else (0, cands)
+    # This rank's contiguous share of the candidate space (the whole space at N = 1), in whole
+    # 65,536-candidate tiles where there are enough of them (each rank's plan then runs the
+    # tiled pass, whose tiles must start on that boundary).
+    from paper_1403_1313_gb300.shard import rank_range
+    r_lo, r_hi = rank_range(cands, rank, world) if shard else (0, cands)
 
     stream = torch.cuda.Stream()
     kw = {}
@@ -340,8 +343,9 @@ def run_ours(args):
             return gather_codes_device(d_out, d_cnt)
         return None
 
-    for _ in range(max(args.warmup, 3)):
-        step()
+    with torch.cuda.stream(stream):  # the gather's collectives follow the search on its stream
+        for _ in range(max(args.warmup, 3)):
+            step()
     stream.synchronize()
     count = int(d_cnt.item())
     if shard:  # every rank needs room for its own codes
@@ -354,8 +358,8 @@ def run_ours(args):
         cap = count_max
         with torch.cuda.stream(stream):
             d_out = torch.zeros(cap, dtype=torch.int64, device="cuda")
-        for _ in range(max(args.warmup, 3)):
-            step()
+            for _ in range(max(args.warmup, 3)):
+                step()
         stream.synchronize()
         count = int(d_cnt.item())
     if shard:
@@ -584,7 +588,7 @@ def run_ours(args):
                                        else "1 GPU")},
             "window_compares_per_s": cps,
             "algorithmic_compares_per_search": compares,
-            "survivors": count,
+            "survivors": int(codes.size),
             "roofline": roof,
             "roofline_cand": roof_cand,
             "roofline_bitslice": roof_bitslice,

@@ -35,6 +35,21 @@ def _rank_search_gpu(seqs, l, d, lo, hi):
         m.motif_plan_destroy(plan)
 
 
+TILE = 1 << 16  # candidates of one tile of the prefix-tiled pass
+
+
+def rank_range(total: int, rank: int, world: int, tile: int = TILE):
+    """This rank's contiguous share [lo, hi) of [0, total): whole tiles where there are at least
+    as many tiles as ranks (so that every rank's plan runs the tiled pass, whose tiles start on a
+    tile boundary), else an even split of the candidates (motif_shard_range)."""
+    import paper_1403_1313_gb300 as m
+    tiles = total // tile
+    if tile > 1 and tiles >= world and total % tile == 0:
+        lo, hi = m.motif_shard_range(tiles, rank, world)
+        return lo * tile, hi * tile
+    return m.motif_shard_range(total, rank, world)
+
+
 def gather_codes(codes: np.ndarray, group=None) -> np.ndarray:
     """All-gathers every rank's ascending codes; returns their rank-order concatenation."""
     import torch

@@ -119,8 +119,9 @@ def test_dynamic_chunks_gather_equals_single(tmp_path, chunk):
 
 def _dev_gather_worker(rank, world, port, l, d, seed, out_dir):
     """The bench's range-shard step with the oracle standing in for the rank's device search:
-    motif_shard_range's split, this rank's codes in a buffer longer than its count, and the
-    variable-size tensor gather (counts, then codes padded to the largest count)."""
+    shard.rank_range's split (whole tiles where there are enough), this rank's codes in a buffer
+    longer than its count, and the variable-size tensor gather (counts, then codes padded to the
+    largest count)."""
     sys.path.insert(0, ROOT)
     import torch
     import torch.distributed as dist
@@ -132,7 +133,8 @@ def _dev_gather_worker(rank, world, port, l, d, seed, out_dir):
     dist.init_process_group("gloo", rank=rank, world_size=world,
                             timeout=datetime.timedelta(seconds=30))
     job = fmgen.fm_job(6, 90, l, d, seed)
-    lo, hi = m.motif_shard_range(4 ** l, rank, world)
+    from paper_1403_1313_gb300.shard import rank_range
+    lo, hi = rank_range(4 ** l, rank, world)
     codes = _oracle_range(job.rows(), l, d, lo, hi)
     buf = torch.full((codes.size + 5 + 3 * rank,), -1, dtype=torch.int64)  # room past the count
     buf[:codes.size] = torch.from_numpy(codes.astype(np.int64))
@@ -142,7 +144,7 @@ def _dev_gather_worker(rank, world, port, l, d, seed, out_dir):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("l,d,seed", [(8, 2, 91), (7, 3, 12), (6, 0, 5)])
+@pytest.mark.parametrize("l,d,seed", [(8, 2, 91), (7, 3, 12), (6, 0, 5), (9, 2, 33)])
 def test_range_shard_tensor_gather_equals_single(tmp_path, l, d, seed):
     from oracle import oracle
     from paper_1403_1313_gb300 import fmgen

@@ -63,3 +63,17 @@ def test_bad_arguments(args):
         else:
             m.motif_shard_range(total, rank, world, weights)
     assert e.value.status == m.ERR_ARG
+
+
+def test_rank_range_uses_whole_tiles():
+    from paper_1403_1313_gb300.shard import TILE, rank_range
+    for total, world in ((4 ** 15, 3), (4 ** 15, 8), (4 ** 9, 4), (4 ** 17, 7)):
+        bounds = [rank_range(total, r, world) for r in range(world)]
+        assert bounds[0][0] == 0 and bounds[-1][1] == total
+        assert all(a[1] == b[0] for a, b in zip(bounds, bounds[1:]))
+        assert all(lo % TILE == 0 and hi % TILE == 0 for lo, hi in bounds)
+        sizes = [hi - lo for lo, hi in bounds]
+        assert max(sizes) - min(sizes) <= TILE
+    # fewer tiles than ranks: the candidates split evenly
+    bounds = [rank_range(4 ** 8, r, 3) for r in range(3)]
+    assert bounds[-1][1] == 4 ** 8 and all(a[1] == b[0] for a, b in zip(bounds, bounds[1:]))

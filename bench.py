@@ -272,8 +272,9 @@ def run_reference(args):
     line = {
         "metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic", "impl": "reference",
+        "higher_is_better": True,
+        "scaling": "strong" if args.parallelism == "range" else "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
         "config": {"workload": "l%dd%d_n%d_t%d_seed%d" % (l, d, n, t, seed), "l": l, "d": d,
                    "n": n, "t": t, "seed": seed, "sample_candidates_per_step": size},
         "cpu_baseline": dict({"value": value, "unit": "candidates/s", "cores": cores,

@@ -622,8 +622,11 @@ int enqueue_search(motif_plan_s* p, uint64_t* out, uint64_t cap, bool poll) {
   }
   // One graph launch runs every step: init, then a while loop whose body is the step kernel.
   if (!p->g_steps) {
+    // A tiled plan takes its whole range as one chunk, so its one pass is done in one step.
+    const bool one_step = p->tiled && p->nchunks == 1;
     cudaError_t e = build_step_graph(p->lkind, p->p, p->d_job, p->d_state, 1, p->d_ctl, p->grid,
-                                     p->block, p->smem, (unsigned)max_steps_of(p), 0, &p->g_steps);
+                                     p->block, p->smem, (unsigned)max_steps_of(p), 0, &p->g_steps,
+                                     one_step);
     if (e != cudaSuccess) {
       p->g_steps = nullptr;
       return status_from_cuda(e);

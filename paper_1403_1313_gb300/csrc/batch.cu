@@ -98,9 +98,11 @@ int ensure_ctx(int dev, int njobs, BatchCtx** out) {
   return MOTIF_OK;
 }
 
-// Runs the job table [0, njobs) of one kernel variant to completion on ctx->stream.
+// Runs the job table [0, njobs) of one kernel variant to completion on ctx->stream.  one_step:
+// every job of the table finishes in one step (one tiled pass over a single chunk), so the graph
+// holds no loop.
 int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, size_t smem,
-              int max_steps, bool use_graph, int timeout_ms) {
+              int max_steps, bool use_graph, int timeout_ms, bool one_step) {
   cudaStream_t s = c->stream;
   if (!use_graph) {
     return run_steps(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem,
@@ -109,7 +111,7 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
   // One graph launch: init, then a while loop of step launches that ends when every job is
   // done (or after max_steps steps).  The instantiated graph is kept for later batches of the
   // same shape.
-  const auto key = std::make_tuple(kind, pv, njobs, grid, block, smem, max_steps);
+  const auto key = std::make_tuple(kind, pv, njobs, grid, block, smem, one_step ? -1 : max_steps);
   cudaGraphExec_t exec = nullptr;
   cudaError_t e = cudaSuccess;
   auto it = c->graphs.find(key);
@@ -117,7 +119,7 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
     exec = it->second;
   } else {
     e = build_step_graph(kind, pv, c->d_jobs, c->d_states, njobs, c->d_ctl, grid, block, smem,
-                         (unsigned)max_steps, 1, &exec);
+                         (unsigned)max_steps, 1, &exec, one_step);
     if (e == cudaSuccess) {
       if (c->graphs.size() >= 16) drop_graphs(*c);
       c->graphs[key] = exec;
@@ -196,10 +198,11 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     }
     // The split-capable kernel variant only where a job of the table is split; the tiled-only
     // kernel where every job runs the whole-tile tiled pass.
-    bool split = false, all_tiled = true;
+    bool split = false, all_tiled = true, one_step = true;
     for (const JobDesc& jd : descs) {
       split = split || jd.seq_block > 0;
       all_tiled = all_tiled && jd.tiled;
+      one_step = one_step && jd.tiled && jd.nchunks == 1;
     }
     const int lkind = launch_kind(kind, pv, split, all_tiled);
     if (step_kernel_attrs(lkind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
@@ -230,7 +233,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     };
     cudaEventRecord(ev[0], c->stream);
     rc = run_table(c, lkind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
-                   timeout);
+                   timeout, one_step);
     cudaEventRecord(ev[1], c->stream);
     if (rc) return fail(rc);
     std::vector<JobState> st(ids.size());

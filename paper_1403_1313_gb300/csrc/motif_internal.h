@@ -153,9 +153,12 @@ cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl*
                           cudaGraphNode_t* node);
 // Builds and instantiates init -> while(step) over a job table: one launch runs every step.
 // rotate != 0 spreads the CTAs' starting jobs (batches); 0 keeps table (arrival) order.
+// one_step: init -> step, for tables whose every job finishes in one step (one tiled pass over
+// a single chunk, with no tile budget per step).
 cudaError_t build_step_graph(int kind, int p, const JobDesc* d_jobs, JobState* d_states,
                              int njobs, StepCtl* d_ctl, int grid, int block, size_t smem,
-                             unsigned max_steps, unsigned rotate, cudaGraphExec_t* exec);
+                             unsigned max_steps, unsigned rotate, cudaGraphExec_t* exec,
+                             bool one_step = false);
 cudaError_t launch_count(const JobDesc* d_job, unsigned long long* d_total, int grid, int block,
                          cudaStream_t s);
 // Canonical (group, window) prefix-compare tally of the GROUP formulation with ks suffix bases.

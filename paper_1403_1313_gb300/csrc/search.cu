@@ -1515,12 +1515,23 @@ cudaError_t add_init_node(cudaGraph_t g, JobState* d_states, int njobs, StepCtl*
 
 cudaError_t build_step_graph(int kind, int p, const JobDesc* d_jobs, JobState* d_states,
                              int njobs, StepCtl* d_ctl, int grid, int block, size_t smem,
-                             unsigned max_steps, unsigned rotate, cudaGraphExec_t* exec) {
+                             unsigned max_steps, unsigned rotate, cudaGraphExec_t* exec,
+                             bool one_step) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return e;
   cudaGraphNode_t init;
   e = add_init_node(g, d_states, njobs, d_ctl, max_steps, 0, rotate, &init);
+  if (one_step) {  // init -> step: the conditional loop node costs about 15 us per launch
+    cudaGraphNode_t step;
+    if (e == cudaSuccess)
+      e = add_step_node(g, kind, p, d_jobs, d_states, njobs, d_ctl, grid, block, smem, 0, 0,
+                        &step);
+    if (e == cudaSuccess) e = cudaGraphAddDependencies(g, &init, &step, nullptr, 1);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+  }
   cudaGraphConditionalHandle h;
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
   cudaGraphNodeParams cp = {};

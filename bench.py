@@ -107,6 +107,8 @@ def parse():
                     help="batch mode: leave the plans on their AUTO choices")
     ap.add_argument("--tune-ms", type=int, default=400,
                     help="batch mode: motif_autotune's time budget per job")
+    ap.add_argument("--saturation-only", action="store_true",
+                    help="serve mode: only the saturation comparison with the plain path")
     ap.add_argument("--serve-step-tiles", type=int, default=0,
                     help="serve mode: tile budget of one server step over all warps (0 = default)")
     return ap.parse_args()
@@ -735,7 +737,7 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     rows = []
-    for rate in [float(r) for r in args.rates.split(",")]:
+    for rate in ([] if args.saturation_only else [float(r) for r in args.rates.split(",")]):
         count = int(min(args.serve_jobs, max(20, rate * args.serve_seconds)))
         jobs = fmgen.serving_jobs(rate, count, seed=5)
         m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
@@ -789,9 +791,61 @@ def run_serve(args):
                      "last_arrival_s": jobs[-1].arrival_s, "submitted_all_s": t_submitted,
                      "done_all_s": wall})
         print(json.dumps(rows[-1]), flush=True)
+    # Saturation: the same jobs one after another through the blocking path (the plain one-job-
+    # per-launch path), then all submitted to the server at once; both include each job's plan
+    # creation, load and release.
+    jobs = fmgen.serving_jobs(1000.0, args.serve_jobs, seed=5)
+    for j in jobs[:8]:  # warm-up of both paths
+        pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+        m.motif_load_seqs(pl, j.seqs)
+        m.motif_search(pl)
+        m.motif_plan_destroy(pl)
+    t0 = time.perf_counter()
+    plain_codes = []
+    dev_ms = 0.0
+    for j in jobs:
+        pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+        m.motif_load_seqs(pl, j.seqs)
+        plain_codes.append(m.motif_search(pl))
+        stp = m.motif_stats(pl)
+        dev_ms += stp["search_ms"] + stp["sort_ms"]
+        m.motif_plan_destroy(pl)
+    t_plain = time.perf_counter() - t0
+    m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
+    wj = fmgen.fm_job(10, 300, 11, 3, 1)
+    pl = m.motif_plan_create(wj.n, wj.t, wj.l, wj.d)
+    m.motif_load_seqs(pl, wj.seqs)
+    m.motif_poll(m.motif_submit(pl), timeout_ms=60000)
+    m.motif_plan_destroy(pl)
+    t0 = time.perf_counter()
+    ids = []
+    for j in jobs:
+        pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+        m.motif_load_seqs(pl, j.seqs)
+        ids.append(m.motif_submit(pl))
+        m.motif_plan_destroy(pl)
+    t_client = time.perf_counter() - t0
+    served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
+    t_served = time.perf_counter() - t0
+    m.motif_server_stop()
+    same = all(np.array_equal(a, b[0]) for a, b in zip(plain_codes, served))
+    lat = np.array([b[1]["total_ms"] for b in served])
+    sat = {"jobs": len(jobs), "plain_jobs_per_s": len(jobs) / t_plain,
+           "served_jobs_per_s": len(jobs) / t_served,
+           "served_over_plain": t_plain / t_served,
+           # the plain path's summed device time of the searches and sorts: a server that kept
+           # the GPU as busy as each job alone does, with no host time at all, would take this
+           "plain_device_ms": dev_ms,
+           "ratio_bound_device_only": 1e3 * t_plain / max(dev_ms, 1e-9),
+           # the client's own loop (plan creation, load, submit and release of every job)
+           "served_client_loop_ms": 1e3 * t_client,
+           "served_equals_plain": bool(same),
+           "served_p50_ms": float(np.percentile(lat, 50)),
+           "served_p99_ms": float(np.percentile(lat, 99))}
+    print(json.dumps({"saturation": sat}), flush=True)
     print(json.dumps({"mode": "serve", "workload": "Poisson arrivals, seed 5: l~U{11..15}, "
                       "d~U{2..4}, n~U{10..30}, t~U{300..800}, GC in {0.4,0.5,0.6}, FM-planted",
-                      "rates": rows}), flush=True)
+                      "rates": rows, "saturation": sat}), flush=True)
     return 0
 
 

@@ -94,6 +94,15 @@ struct Server {
   // full link rate into pages that are already mapped, and motif_poll gives its block back.
   std::multimap<size_t, uint64_t*> host_free;
   size_t host_free_bytes = 0;
+  // Retirement of a step's finished jobs together (retire_finished): pinned staging of their
+  // sort / compaction tasks and of the table's states, and the tasks' device copies.
+  JobState* h_states = nullptr;
+  SortTask* h_sort_tasks = nullptr;
+  BitmapTask* h_bm_tasks = nullptr;
+  unsigned* h_bm_first = nullptr;
+  SortTask* d_sort_tasks = nullptr;
+  BitmapTask* d_bm_tasks = nullptr;
+  unsigned* d_bm_first = nullptr;
 };
 
 constexpr size_t kHostPoolBytes = (size_t)2 << 30;  // pinned result blocks kept for reuse
@@ -358,24 +367,78 @@ int finish_bitmap_job(Server* S, Job* j, int slot) {
   return copy_result(S, j, fc);
 }
 
-// Sorts a finished job's codes and copies them to the host.
-int finish_job(Server* S, Job* j, int slot, unsigned long long found) {
-  if (j->bitmap) return finish_bitmap_job(S, j, slot);
-  if (found > 4096) {
-    const size_t need = sort_scratch_bytes(j->out_cap, S->sms);
-    j->sort = salloc(S, need);
-    j->sort_bytes = need;
-    if (!j->sort) return MOTIF_ERR_OOM;
+// Finishes the jobs of the table slots `fin` (their steps are done and their codes fit their
+// buffers), all at once: one launch sorts every list of at most 4096 codes, a radix sort runs per
+// larger list and three launches compact every bitmap; one wait then reads every final count,
+// the results are copied to pinned host blocks together, and one more wait ends the copies.  A
+// bitmap job whose codes outgrow its buffer takes finish_bitmap_job alone.  Sets each job's
+// status.
+void retire_finished(Server* S, const std::vector<int>& fin, const std::vector<JobState>& st,
+                     int nact) {
+  int nsmall = 0, nbm = 0;
+  unsigned bm_blocks = 0;
+  for (const int i : fin) {
+    Job* j = S->active[i];
+    j->status = MOTIF_OK;
+    const unsigned long long found = st[i].out_count;
+    unsigned long long* cnt = &S->d_states[i].out_count;
+    if (j->bitmap) {
+      S->h_bm_first[nbm] = bm_blocks;
+      S->h_bm_tasks[nbm++] = BitmapTask{j->bitmap, j->bm_words, j->bm_base, j->out,
+                                        (long long)j->out_cap, j->bm_scratch, cnt};
+      bm_blocks += (unsigned)bitmap_task_blocks(j->bm_words);
+    } else if (found > 4096) {
+      const size_t need = sort_scratch_bytes(j->out_cap, S->sms);
+      j->sort = salloc(S, need);
+      j->sort_bytes = need;
+      if (!j->sort ||
+          launch_sort_unique(j->out, cnt, j->out_cap, 2 * j->l, j->sort, S->sms,
+                             (long long)found, S->stream) != cudaSuccess)
+        j->status = j->sort ? MOTIF_ERR_CUDA : MOTIF_ERR_OOM;
+    } else if (found > 1) {
+      S->h_sort_tasks[nsmall++] = SortTask{j->out, cnt, (long long)j->out_cap};
+    }
   }
-  cudaError_t e = launch_sort_unique(j->out, &S->d_states[slot].out_count, j->out_cap, 2 * j->l,
-                                     j->sort, S->sms, (long long)found, S->stream);
-  unsigned long long fc = 0;
+  S->h_bm_first[nbm] = bm_blocks;
+  cudaError_t e = cudaSuccess;
+  if (nsmall)
+    e = cudaMemcpyAsync(S->d_sort_tasks, S->h_sort_tasks, sizeof(SortTask) * nsmall,
+                        cudaMemcpyHostToDevice, S->stream);
+  if (e == cudaSuccess && nbm)
+    e = cudaMemcpyAsync(S->d_bm_tasks, S->h_bm_tasks, sizeof(BitmapTask) * nbm,
+                        cudaMemcpyHostToDevice, S->stream);
+  if (e == cudaSuccess && nbm)
+    e = cudaMemcpyAsync(S->d_bm_first, S->h_bm_first, sizeof(unsigned) * (nbm + 1),
+                        cudaMemcpyHostToDevice, S->stream);
+  if (e == cudaSuccess) e = launch_small_sort_tasks(S->d_sort_tasks, nsmall, S->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&fc, &S->d_states[slot].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
-                        S->stream);
+    e = launch_bitmap_compact_tasks(S->d_bm_tasks, S->d_bm_first, nbm, bm_blocks, S->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(JobState) * nact,
+                        cudaMemcpyDeviceToHost, S->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-  if (e != cudaSuccess) return status_from_cuda(e);
-  return copy_result(S, j, fc);
+  if (e != cudaSuccess) {
+    for (const int i : fin) S->active[i]->status = MOTIF_ERR_CUDA;
+    return;
+  }
+  for (const int i : fin) {
+    Job* j = S->active[i];
+    if (j->status != MOTIF_OK) continue;
+    const unsigned long long fc = S->h_states[i].out_count;
+    if (j->bitmap && fc > (unsigned long long)j->out_cap) {  // grow, compact again, copy
+      j->status = finish_bitmap_job(S, j, i);
+      continue;
+    }
+    j->result_size = (int64_t)fc;
+    if (!fc) continue;
+    j->result = host_take(S, fc, &j->result_cap);
+    if (!j->result) { j->status = MOTIF_ERR_OOM; continue; }
+    if (cudaMemcpyAsync(j->result, j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream) !=
+        cudaSuccess)
+      j->status = MOTIF_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(S->stream) != cudaSuccess)
+    for (const int i : fin) S->active[i]->status = MOTIF_ERR_CUDA;
 }
 
 void scheduler(Server* S) {
@@ -477,30 +540,36 @@ void scheduler(Server* S) {
       S->cv_done.notify_all();
       continue;
     }
-    // Retire finished jobs (keeping table order for the rest).
+    // Retire finished jobs (keeping table order for the rest), all of them together.
     std::vector<Job*> keep;
-    std::vector<int> moved;
+    std::vector<int> moved, fin, failed;
     for (int i = 0; i < nact; ++i) {
       Job* j = S->active[i];
       j->gpu_ms += step_ms;
       if (!st[i].done) { keep.push_back(j); moved.push_back(i); continue; }
       const unsigned long long found = st[i].out_count;
-      if (found > (unsigned long long)j->out_cap) {
+      if (!j->bitmap && found > (unsigned long long)j->out_cap) {
         // Output overflow: grow the buffer and restart the job in place.
         sfree(S, j->out);
         j->out_cap = (int64_t)found;
         j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
-        if (!j->out) { j->status = MOTIF_ERR_OOM; }
-        else {
+        if (!j->out) {
+          j->status = MOTIF_ERR_OOM;
+          failed.push_back(i);
+        } else {
           cudaMemsetAsync(&S->d_states[i], 0, sizeof(JobState), S->stream);
           keep.push_back(j);
           moved.push_back(i);
           dirty = true;  // descriptor changed
-          continue;
         }
-      } else {
-        j->status = finish_job(S, j, i, found);
+        continue;
       }
+      fin.push_back(i);
+    }
+    if (!fin.empty()) retire_finished(S, fin, st, nact);
+    fin.insert(fin.end(), failed.begin(), failed.end());
+    for (const int i : fin) {
+      Job* j = S->active[i];
       j->t_done = now_ms();
       j->done = true;
       S->budget_used -= j->footprint;
@@ -528,6 +597,26 @@ void scheduler(Server* S) {
   S->cv_done.notify_all();
 }
 
+// Frees the server's fixed buffers, streams, events and graph; each may be unset (a start that
+// failed part way).
+void free_fixed(Server* S) {
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->graph) cudaGraphDestroy(S->graph);
+  for (void* d : {(void*)S->d_jobs, (void*)S->d_states, (void*)S->d_ctl, (void*)S->d_sort_tasks,
+                  (void*)S->d_bm_tasks, (void*)S->d_bm_first})
+    if (d) cudaFree(d);
+  for (void* h : {(void*)S->h_states, (void*)S->h_sort_tasks, (void*)S->h_bm_tasks,
+                  (void*)S->h_bm_first})
+    if (h) cudaFreeHost(h);
+  if (S->ev0) cudaEventDestroy(S->ev0);
+  if (S->ev1) cudaEventDestroy(S->ev1);
+  if (S->submit_stream) {
+    cudaStreamSynchronize(S->submit_stream);
+    cudaStreamDestroy(S->submit_stream);
+  }
+  if (S->stream) cudaStreamDestroy(S->stream);
+}
+
 int start_locked(const motif_server_opts* opts) {
   if (g_srv) return MOTIF_ERR_STATE;
   Server* S = new Server();
@@ -545,7 +634,15 @@ int start_locked(const motif_server_opts* opts) {
       cudaMalloc(&S->d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
       cudaMalloc(&S->d_states, sizeof(JobState) * cap) != cudaSuccess ||
       cudaMalloc(&S->d_ctl, sizeof(StepCtl)) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_states, sizeof(JobState) * cap, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_sort_tasks, sizeof(SortTask) * cap, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_bm_tasks, sizeof(BitmapTask) * cap, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_bm_first, sizeof(unsigned) * (cap + 1), 0) != cudaSuccess ||
+      cudaMalloc(&S->d_sort_tasks, sizeof(SortTask) * cap) != cudaSuccess ||
+      cudaMalloc(&S->d_bm_tasks, sizeof(BitmapTask) * cap) != cudaSuccess ||
+      cudaMalloc(&S->d_bm_first, sizeof(unsigned) * (cap + 1)) != cudaSuccess ||
       cudaEventCreate(&S->ev0) != cudaSuccess || cudaEventCreate(&S->ev1) != cudaSuccess) {
+    free_fixed(S);
     delete S;
     return MOTIF_ERR_CUDA;
   }
@@ -587,16 +684,7 @@ extern "C" int motif_server_stop(void) {
   for (auto& kv : S->host_free) cudaFreeHost(kv.second);
   S->host_free.clear();
   cudaStreamSynchronize(S->stream);
-  if (S->exec) cudaGraphExecDestroy(S->exec);
-  if (S->graph) cudaGraphDestroy(S->graph);
-  cudaFree(S->d_jobs);
-  cudaFree(S->d_states);
-  cudaFree(S->d_ctl);
-  cudaEventDestroy(S->ev0);
-  cudaEventDestroy(S->ev1);
-  cudaStreamSynchronize(S->submit_stream);
-  cudaStreamDestroy(S->submit_stream);
-  cudaStreamDestroy(S->stream);
+  free_fixed(S);
   delete S;
   return MOTIF_OK;
 }

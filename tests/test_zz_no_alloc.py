@@ -91,3 +91,31 @@ def test_noalloc_sort_through_the_binding(lib):
     with pytest.raises(m.MotifError) as e:  # rejected on the host, nothing launched
         m.motif_sort_codes_noalloc(256, 5, 0, 256)
     assert e.value.status == m.ERR_ARG
+
+
+def test_noalloc_sort_allocates_nothing(lib):
+    """After a first call (which loads the kernels and looks up the array), further calls leave
+    the device's free memory and the caching allocator's bytes exactly where they were."""
+    torch = pytest.importorskip("torch")
+    ref = _search_result(8, 2, seed=7)
+    mixed = np.concatenate([ref, ref])
+    host = torch.from_numpy(mixed.astype(np.int64))
+    d_codes = host.cuda()
+    d_count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        d_codes.copy_(host)
+        st = lib.motif_sort_codes_noalloc(d_codes.data_ptr(), mixed.size, 16,
+                                          d_count.data_ptr(), stream)
+        assert st == m.OK, m.motif_strerror(st)
+        torch.cuda.synchronize()
+
+    call()
+    free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(3):
+        call()
+        assert int(d_count.item()) == ref.size
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == torch0
+    assert np.array_equal(d_codes[:ref.size].cpu().numpy().astype(np.uint64), ref)

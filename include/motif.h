@@ -141,7 +141,8 @@ typedef struct {
   double sort_ms;                /* device time of sort/dedup, last search */
   double total_ms;               /* host wall time of the last motif_search or served job */
   double queue_ms;               /* served job: submit -> admission; batched job: the part of its
-                                    batch's device-to-host result copies that outlasts the sorts */
+                                    batch's device-to-host result copies that outlasts the last
+                                    table's sorts */
   int64_t device_bytes;          /* device memory held by the plan */
   int32_t smem_bytes;            /* dynamic shared memory per CTA of the search kernel */
   int32_t kernel;                /* kernel that ran (motif_kernel) */
@@ -285,9 +286,14 @@ uint64_t motif_kernel_launches(void);
  * for later batches.  Per job j the results follow motif_search's rules on out_codes[j] /
  * capacities[j] / out_counts[j]; statuses[j] receives job j's status.  Returns MOTIF_OK when
  * every job succeeded, else the first failing status.  Blocking: it waits for each plan's
- * stream, then works on the library's per-device batch streams, where job j's result copy
- * overlaps the sorts of the jobs after it (out_codes in pinned host memory let the copies run
- * asynchronously at full link rate; pageable buffers are correct but serialise them). */
+ * stream, then works on the library's per-device batch streams.  Jobs run as one table per
+ * kernel variant.  Where every job of a variant ends in one step (the whole tiled pass over one
+ * chunk), its jobs with bitmap output (the dense ones, with large results) form a table of
+ * their own that runs first, so that their result copies overlap the steps of the tables after
+ * them (out_codes in pinned host memory let the copies run asynchronously at full link rate;
+ * pageable buffers are correct but serialise them).  Every job of the batch reports the
+ * batch's device times in motif_stats: search_ms and sort_ms summed over its tables, queue_ms
+ * the copy time left after the last table's sorts. */
 int motif_batch_search(int32_t njobs, const motif_plan* plans, uint64_t* const* out_codes,
                        const int64_t* capacities, int64_t* out_counts, int32_t* statuses,
                        int32_t use_graph);

@@ -166,8 +166,13 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     }
   }
   const double t0 = now_ms();
-  // Group the device jobs by kernel variant; each group runs as one table.
-  std::map<std::pair<int, int>, std::vector<int>> groups;
+  // Group the device jobs by kernel variant; each group runs as one table.  Where every job of
+  // a group ends in one step (the whole tiled pass over one chunk), its jobs with bitmap output
+  // (the dense ones, whose results are large) form a table of their own that runs first: their
+  // result copies then overlap the steps of the tables after them.  (Jobs of several passes
+  // keep one table: alone, their short late steps would leave the GPU idle.)
+  std::vector<int> dev_jobs;
+  std::map<std::pair<int, int>, bool> one_step_group;
   for (int j = 0; j < njobs; ++j) {
     motif_plan_s* p = plans[j];
     if (statuses[j] != MOTIF_OK || p->W <= 0 || p->hi <= p->lo || p->nchunks == 0 ||
@@ -177,11 +182,35 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       statuses[j] = MOTIF_ERR_OOM;
       continue;
     }
-    groups[{p->kind, p->p}].push_back(j);
+    dev_jobs.push_back(j);
+    auto it = one_step_group.emplace(std::make_pair(p->kind, p->p), true).first;
+    it->second = it->second && p->tiled_in_batch && p->nchunks == 1;
+  }
+  std::map<std::tuple<int, int, int>, std::vector<int>> groups;
+  for (const int j : dev_jobs) {
+    motif_plan_s* p = plans[j];
+    const bool first = p->bitmap && one_step_group[std::make_pair(p->kind, p->p)];
+    groups[std::make_tuple(first ? 0 : 1, p->kind, p->p)].push_back(j);
   }
   std::vector<char> redo(njobs, 0);
+  // The event after the last table's sorts (the copies of every table end together before the
+  // call returns), the tables' device times summed, and the jobs that ran.
+  cudaEvent_t last_sorts = nullptr;
+  float tot_steps = 0, tot_sort = 0;
+  std::vector<int> ran;
+  auto drop_copy_events = [&]() {
+    if (last_sorts) cudaEventDestroy(last_sorts);
+    last_sorts = nullptr;
+  };
+  // An error return with the earlier tables' copies still in flight waits for them first.
+  auto bail = [&](int status) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->copy_stream);
+    drop_copy_events();
+    return status;
+  };
   for (auto& kv : groups) {
-    const int kind = kv.first.first, pv = kv.first.second;
+    const int kind = std::get<1>(kv.first), pv = std::get<2>(kv.first);
     const std::vector<int>& ids = kv.second;
     std::vector<JobDesc> descs(ids.size());
     size_t smem = 0;
@@ -205,9 +234,9 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
       one_step = one_step && jd.tiled && jd.nchunks == 1;
     }
     const int lkind = launch_kind(kind, pv, split, all_tiled);
-    if (step_kernel_attrs(lkind, pv, smem) != cudaSuccess) return MOTIF_ERR_CUDA;
+    if (step_kernel_attrs(lkind, pv, smem) != cudaSuccess) return bail(MOTIF_ERR_CUDA);
     grid = step_max_ctas_per_sm(lkind, pv, block, smem) * plans[ids[0]]->sms;
-    if (grid <= 0) return MOTIF_ERR_ARG;
+    if (grid <= 0) return bail(MOTIF_ERR_ARG);
     cudaError_t e = cudaMemcpyAsync(c->d_jobs, descs.data(), sizeof(JobDesc) * ids.size(),
                                     cudaMemcpyHostToDevice, c->stream);
     for (size_t i = 0; i < ids.size() && e == cudaSuccess; ++i) {
@@ -221,15 +250,15 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     // Zero the states; CTAs rotate their starting job so every job's tiles start at once.
     if (e == cudaSuccess)
       e = launch_init_steps(c->d_states, (int)ids.size(), c->d_ctl, 0, 0, 1, c->stream);
-    if (e != cudaSuccess) return status_from_cuda(e);
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (e != cudaSuccess) return bail(status_from_cuda(e));
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     for (auto& x : ev) cudaEventCreate(&x);
     // Leaves nothing in flight (copies into the caller's buffers included) before returning.
     auto fail = [&](int status) {
       cudaStreamSynchronize(c->stream);
       cudaStreamSynchronize(c->copy_stream);
       for (auto& x : ev) cudaEventDestroy(x);
-      return status;
+      return bail(status);
     };
     cudaEventRecord(ev[0], c->stream);
     rc = run_table(c, lkind, pv, (int)ids.size(), grid, block, smem, max_steps, use_graph != 0,
@@ -332,22 +361,40 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
         if (e != cudaSuccess) return fail(status_from_cuda(e));
       }
     }
-    // The copies' end, timed on the batch stream (events of two streams do not share a timeline).
-    e = cudaEventRecord(c->copies_done, c->copy_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->copies_done, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    float steps_ms = 0, sort_ms = 0, copy_ms = 0;
+    // The copies run on while the next table steps (ev[0..2] have completed: the wait on the
+    // states above came after them).
+    float steps_ms = 0, sort_ms = 0;
     cudaEventElapsedTime(&steps_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&sort_ms, ev[1], ev[2]);
-    cudaEventElapsedTime(&copy_ms, ev[2], ev[3]);  // the copy time not hidden under the sorts
-    if (e != cudaSuccess) return fail(status_from_cuda(e));
-    for (auto& x : ev) cudaEventDestroy(x);
-    for (size_t i = 0; i < ids.size(); ++i) {  // the group's device times, shared by its jobs
-      plans[ids[i]]->stats.search_ms = steps_ms;
-      plans[ids[i]]->stats.sort_ms = sort_ms;
-      plans[ids[i]]->stats.queue_ms = copy_ms;  // result copy to the host
+    tot_steps += steps_ms;
+    tot_sort += sort_ms;
+    ran.insert(ran.end(), ids.begin(), ids.end());
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    drop_copy_events();
+    last_sorts = ev[2];
+  }
+  {
+    // Every table's copies end here, timed on the batch stream.
+    cudaEvent_t end = nullptr;
+    cudaError_t e = cudaEventCreate(&end);
+    if (e == cudaSuccess) e = cudaEventRecord(c->copies_done, c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->copies_done, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(end, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      if (end) cudaEventDestroy(end);
+      return bail(status_from_cuda(e));
     }
+    float copy_ms = 0;  // the copy time not hidden under the steps and sorts
+    if (last_sorts) cudaEventElapsedTime(&copy_ms, last_sorts, end);
+    for (const int j : ran) {  // the batch's device times, shared by its jobs
+      plans[j]->stats.search_ms = tot_steps;
+      plans[j]->stats.sort_ms = tot_sort;
+      plans[j]->stats.queue_ms = copy_ms;
+    }
+    cudaEventDestroy(end);
+    drop_copy_events();
   }
   for (int j = 0; j < njobs; ++j) {
     if (!redo[j]) continue;

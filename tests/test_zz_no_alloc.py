@@ -10,6 +10,7 @@ collected last and needs nothing from the other test files, so it runs alone in 
 as well as after them.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -95,7 +96,7 @@ def test_noalloc_sort_through_the_binding(lib):
 
 def test_noalloc_sort_allocates_nothing(lib):
     """After a first call (which loads the kernels and looks up the array), further calls leave
-    the device's free memory and the caching allocator's bytes exactly where they were."""
+    the device's free memory exactly where it was and take nothing from torch's allocator."""
     torch = pytest.importorskip("torch")
     ref = _search_result(8, 2, seed=7)
     mixed = np.concatenate([ref, ref])
@@ -112,10 +113,11 @@ def test_noalloc_sort_allocates_nothing(lib):
         torch.cuda.synchronize()
 
     call()
+    gc.collect()  # tensors left by earlier tests go back to torch's cache before the baseline
     free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
     for _ in range(3):
         call()
         assert int(d_count.item()) == ref.size
     assert torch.cuda.mem_get_info()[0] == free0
-    assert torch.cuda.memory_allocated() == torch0
+    assert torch.cuda.memory_allocated() <= torch0
     assert np.array_equal(d_codes[:ref.size].cpu().numpy().astype(np.uint64), ref)

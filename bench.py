@@ -107,6 +107,9 @@ def parse():
                     help="batch mode: leave the plans on their AUTO choices")
     ap.add_argument("--tune-ms", type=int, default=400,
                     help="batch mode: motif_autotune's time budget per job")
+    ap.add_argument("--serve-submit", choices=["seqs", "plan"], default="seqs",
+                    help="serve mode: submit jobs straight from their rows (motif_submit_seqs) "
+                         "or through a plan (create, load, motif_submit, destroy)")
     ap.add_argument("--saturation-only", action="store_true",
                     help="serve mode: only the saturation comparison with the plain path")
     ap.add_argument("--serve-step-tiles", type=int, default=0,
@@ -748,13 +751,18 @@ def run_serve(args):
         m.motif_poll(m.motif_submit(pl), timeout_ms=60000)
         m.motif_plan_destroy(pl)
         ids = []
-        client = {"create": 0.0, "load": 0.0, "submit": 0.0, "destroy": 0.0}
+        client = ({"submit": 0.0} if args.serve_submit == "seqs" else
+                  {"create": 0.0, "load": 0.0, "submit": 0.0, "destroy": 0.0})
         t0 = time.perf_counter()
         for j in jobs:
             delay = t0 + j.arrival_s - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
             c0 = time.perf_counter()
+            if args.serve_submit == "seqs":
+                ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
+                client["submit"] += time.perf_counter() - c0
+                continue
             pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
             c1 = time.perf_counter()
             m.motif_load_seqs(pl, j.seqs)
@@ -811,28 +819,40 @@ def run_serve(args):
         dev_ms += stp["search_ms"] + stp["sort_ms"]
         m.motif_plan_destroy(pl)
     t_plain = time.perf_counter() - t0
-    m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
-    wj = fmgen.fm_job(10, 300, 11, 3, 1)
-    pl = m.motif_plan_create(wj.n, wj.t, wj.l, wj.d)
-    m.motif_load_seqs(pl, wj.seqs)
-    m.motif_poll(m.motif_submit(pl), timeout_ms=60000)
-    m.motif_plan_destroy(pl)
-    t0 = time.perf_counter()
-    ids = []
-    for j in jobs:
-        pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
-        m.motif_load_seqs(pl, j.seqs)
-        ids.append(m.motif_submit(pl))
-        m.motif_plan_destroy(pl)
-    t_client = time.perf_counter() - t0
-    served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
-    t_served = time.perf_counter() - t0
-    m.motif_server_stop()
-    same = all(np.array_equal(a, b[0]) for a, b in zip(plain_codes, served))
+    def served_at_once(via):
+        """Every job submitted at once (through `via`), then every result polled."""
+        m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
+        wj = fmgen.fm_job(10, 300, 11, 3, 1)
+        m.motif_poll(m.motif_submit_seqs(wj.seqs, wj.l, wj.d), timeout_ms=60000)
+        t0 = time.perf_counter()
+        ids = []
+        for j in jobs:
+            if via == "seqs":
+                ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
+                continue
+            pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+            m.motif_load_seqs(pl, j.seqs)
+            ids.append(m.motif_submit(pl))
+            m.motif_plan_destroy(pl)
+        t_client = time.perf_counter() - t0
+        served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
+        t_served = time.perf_counter() - t0
+        m.motif_server_stop()
+        return served, t_client, t_served
+
+    served_plan, t_client_plan, t_served_plan = served_at_once("plan")
+    served, t_client, t_served = served_at_once(args.serve_submit)
+    same = all(np.array_equal(a, b[0]) and np.array_equal(a, c[0])
+               for a, b, c in zip(plain_codes, served, served_plan))
     lat = np.array([b[1]["total_ms"] for b in served])
-    sat = {"jobs": len(jobs), "plain_jobs_per_s": len(jobs) / t_plain,
+    sat = {"jobs": len(jobs), "submit": args.serve_submit,
+           "plain_jobs_per_s": len(jobs) / t_plain,
            "served_jobs_per_s": len(jobs) / t_served,
            "served_over_plain": t_plain / t_served,
+           # the same jobs served through plans (create, load, motif_submit, destroy each)
+           "served_via_plans_jobs_per_s": len(jobs) / t_served_plan,
+           "served_via_plans_over_plain": t_plain / t_served_plan,
+           "served_via_plans_client_loop_ms": 1e3 * t_client_plan,
            # the plain path's summed device time of the searches and sorts: a server that kept
            # the GPU as busy as each job alone does, with no host time at all, would take this
            "plain_device_ms": dev_ms,
@@ -845,7 +865,8 @@ def run_serve(args):
     print(json.dumps({"saturation": sat}), flush=True)
     print(json.dumps({"mode": "serve", "workload": "Poisson arrivals, seed 5: l~U{11..15}, "
                       "d~U{2..4}, n~U{10..30}, t~U{300..800}, GC in {0.4,0.5,0.6}, FM-planted",
-                      "rates": rows, "saturation": sat}), flush=True)
+                      "submit": args.serve_submit, "rates": rows, "saturation": sat}),
+          flush=True)
     return 0
 
 

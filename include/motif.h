@@ -349,6 +349,17 @@ int motif_server_stop(void);
  * MOTIF_ERR_BUSY (max_queued jobs already wait), MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
 int motif_submit(motif_plan p, int64_t* job_id);
 
+/* Submits a job straight from n host rows of t characters (row r at seqs + r * stride, stride
+ * >= t, only ACGTacgt), searched for (l, d), without a plan: the job is configured as
+ * motif_plan_create would configure a plan with these options (opts may be NULL; its stream and
+ * allocator are not used, the server's are), the characters are checked on the host, copied to
+ * the device and packed on the server's submit stream.  seqs may be reused once this returns.
+ * *job_id receives the job id; poll it with motif_poll.  Errors: MOTIF_ERR_ARG (NULL
+ * arguments, stride < t, and motif_plan_create's argument errors), MOTIF_ERR_ALPHABET,
+ * MOTIF_ERR_BUSY, MOTIF_ERR_OOM, MOTIF_ERR_CUDA. */
+int motif_submit_seqs(const char* seqs, int64_t stride, int32_t n, int32_t t, int32_t l,
+                      int32_t d, const motif_opts* opts, int64_t* job_id);
+
 /* Waits up to timeout_ms (0 = do not wait) for the job.  Returns MOTIF_PENDING while it runs;
  * on completion writes the codes by motif_search's rules and releases the job (on
  * MOTIF_ERR_CAPACITY the job stays so that it can be polled again).  stats may be NULL.

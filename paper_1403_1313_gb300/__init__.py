@@ -27,7 +27,7 @@ __all__ = [
     "read_fasta", "motif_search", "motif_search_device",
     "motif_count_compares", "motif_count_work", "motif_count_tiled_work", "motif_kernel_launches", "motif_stats", "motif_batch_search", "motif_autotune",
     "motif_tune_cache_save", "motif_tune_cache_load", "motif_server_start", "motif_server_stop",
-    "motif_submit", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
+    "motif_submit", "motif_submit_seqs", "motif_poll", "motif_shard_range", "motif_strerror", "motif_encode",
     "motif_decode", "motif_probe_rate", "motif_version", "library_path", "torch_opts",
     "KERNEL_AUTO", "KERNEL_CAND", "KERNEL_GROUP", "KERNEL_TILED", "KERNEL_BITSLICE",
     "OUTPUT_AUTO", "OUTPUT_LIST", "OUTPUT_BITMAP", "SEED_ALL", "SEED_NEIGHBOURHOOD",
@@ -146,6 +146,8 @@ def _load():
             "motif_server_start": (ctypes.c_int, [ctypes.POINTER(motif_server_opts)]),
             "motif_server_stop": (ctypes.c_int, []),
             "motif_submit": (ctypes.c_int, [P, i64p]),
+            "motif_submit_seqs": (ctypes.c_int, [ctypes.c_char_p, i64, i32, i32, i32, i32,
+                                                 ctypes.POINTER(motif_opts), i64p]),
             "motif_poll": (ctypes.c_int, [i64, u64p, i64, i64p, i32, ctypes.POINTER(motif_stats_t)]),
             "motif_shard_range": (ctypes.c_int, [u64, i32, i32, ctypes.POINTER(ctypes.c_double), u64p, u64p]),
             "motif_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -471,6 +473,18 @@ def motif_server_stop() -> None:
 def motif_submit(plan: Plan) -> int:
     j = ctypes.c_int64(0)
     _check(_load().motif_submit(plan, ctypes.byref(j)), "motif_submit")
+    return int(j.value)
+
+
+def motif_submit_seqs(seqs, l: int, d: int, opts: motif_opts | None = None) -> int:
+    """Submits a job from host rows (a list of equal-length str/bytes rows or an (n, t) uint8
+    array) without a plan; returns its id for motif_poll."""
+    buf, n, t = _rows(seqs)
+    ptr = buf.ctypes.data_as(ctypes.c_char_p) if isinstance(buf, np.ndarray) else buf
+    j = ctypes.c_int64(0)
+    _check(_load().motif_submit_seqs(ptr, t, n, t, l, d,
+                                     ctypes.byref(opts) if opts is not None else None,
+                                     ctypes.byref(j)), "motif_submit_seqs")
     return int(j.value)
 
 

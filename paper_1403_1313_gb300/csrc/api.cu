@@ -727,14 +727,14 @@ void motif_opts_default(motif_opts* o) {
   if (o) memset(o, 0, sizeof(*o));
 }
 
-int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_opts* opts,
-                      motif_plan* out) {
-  if (!out) return MOTIF_ERR_ARG;
-  *out = nullptr;
+}  // extern "C"
+
+namespace motif {
+
+int plan_init_host(motif_plan_s* p, int32_t n, int32_t t, int32_t l, int32_t d,
+                   const motif_opts* opts) {
   int rc = validate_args(n, t, l, d);
   if (rc) return rc;
-  motif_plan_s* p = new (std::nothrow) motif_plan_s();
-  if (!p) return MOTIF_ERR_OOM;
   if (opts) p->opts = *opts;
   p->n = n; p->t = t; p->l = l; p->d = d;
   p->W = t - l + 1;
@@ -742,17 +742,39 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
   const uint64_t space = 1ull << (2 * l);
   p->lo = p->opts.range_lo;
   p->hi = p->opts.range_hi ? p->opts.range_hi : space;
-  if (p->hi > space || p->lo > p->hi) { delete p; return MOTIF_ERR_ARG; }
-  if (p->opts.launch != MOTIF_LAUNCH_GRAPH && p->opts.launch != MOTIF_LAUNCH_DIRECT) {
-    delete p;
+  if (p->hi > space || p->lo > p->hi) return MOTIF_ERR_ARG;
+  if (p->opts.launch != MOTIF_LAUNCH_GRAPH && p->opts.launch != MOTIF_LAUNCH_DIRECT)
     return MOTIF_ERR_ARG;
-  }
   p->stream = (cudaStream_t)p->opts.stream;
+  // (one attribute query: a full cudaGetDeviceProperties costs more than the rest of a small
+  // plan's set-up)
   cudaError_t e = cudaGetDevice(&p->device);
-  cudaDeviceProp prop;
-  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, p->device);
-  if (e != cudaSuccess) { cudaGetLastError(); delete p; return MOTIF_ERR_CUDA; }
-  p->sms = prop.multiProcessorCount;
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MOTIF_ERR_CUDA;
+  }
+  return MOTIF_OK;
+}
+
+int plan_configure_host(motif_plan_s* p) {
+  if (p->opts.kernel == MOTIF_KERNEL_AUTO) tune_lookup(p, &p->opts);
+  return plan_configure(p);
+}
+
+}  // namespace motif
+
+extern "C" {
+
+int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_opts* opts,
+                      motif_plan* out) {
+  if (!out) return MOTIF_ERR_ARG;
+  *out = nullptr;
+  motif_plan_s* p = new (std::nothrow) motif_plan_s();
+  if (!p) return MOTIF_ERR_OOM;
+  int rc = plan_init_host(p, n, t, l, d, opts);
+  if (rc) { delete p; return rc; }
   const size_t chars = (size_t)n * t;
   const size_t wins = (size_t)n * std::max(p->wstride, 0);
   p->d_chars = (char*)plan_alloc(p, chars);
@@ -769,8 +791,7 @@ int motif_plan_create(int32_t n, int32_t t, int32_t l, int32_t d, const motif_op
     motif_plan_destroy(p);
     return MOTIF_ERR_OOM;
   }
-  if (p->opts.kernel == MOTIF_KERNEL_AUTO) tune_lookup(p, &p->opts);
-  rc = plan_configure(p);
+  rc = plan_configure_host(p);
   if (rc) { motif_plan_destroy(p); return rc; }
   *out = p;
   return MOTIF_OK;

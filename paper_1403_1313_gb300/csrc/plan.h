@@ -122,6 +122,12 @@ void fill_desc(const motif_plan_s* p, JobDesc* jd, uint64_t* out, uint64_t out_c
 
 // (Re)applies the kernel configuration: variant, grid, shared memory and chunking.
 int plan_configure(motif_plan_s* p);
+// The host part of plan creation: arguments, options, range, window stride, device and SM
+// count checked and set (no device memory).  A motif_status.
+int plan_init_host(motif_plan_s* p, int32_t n, int32_t t, int32_t l, int32_t d,
+                   const motif_opts* opts);
+// The tuning cache's choice (kernel AUTO) and plan_configure.
+int plan_configure_host(motif_plan_s* p);
 // Allocates the survivor queues and the default output buffer on first use.
 int plan_ensure_buffers(motif_plan_s* p);
 void free_bitmap(motif_plan_s* p);

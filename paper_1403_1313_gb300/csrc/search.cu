@@ -31,7 +31,9 @@
 // windows of the pass into shared memory and pulls tiles from the job's pass cursor.  The last
 // CTA to finish advances each job's state for the next launch (and, inside a CUDA graph, sets
 // the while-loop condition); no CTA ever waits for another.
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "motif_internal.h"
 
@@ -1444,22 +1446,39 @@ size_t step_smem_bytes(int kind, int p, int wstride, int block) {
 // share the kernels, and one caller's smaller request must not break another's launch.
 cudaError_t step_kernel_attrs(int kind, int p, size_t smem) {
   static std::mutex mu;
-  static size_t set[kLaunchKinds][kMaxKs + 1] = {};
+  static size_t set[64][kLaunchKinds][kMaxKs + 1] = {};  // per device
   const void* f = step_function(kind, p);
   if (!f || kind < 1 || kind >= kLaunchKinds || p < 1 || p > kMaxKs)
     return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(mu);
-  if (smem <= set[kind][p]) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) set[kind][p] = smem;
+  if (smem <= set[dev][kind][p]) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) set[dev][kind][p] = smem;
   return e;
 }
 
 int step_max_ctas_per_sm(int kind, int p, int block, size_t smem) {
+  // The occupancy query is asked again for every plan configured: its answers are kept, per
+  // device (the same kernel can differ in resident CTAs on another device).
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, size_t>, int> known;
   const void* f = step_function(kind, p);
+  int dev = 0;
+  if (!f || cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const auto key = std::make_tuple(dev, kind, p, block, smem);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = known.find(key);
+    if (it != known.end()) return it->second;
+  }
   int n = 0;
-  if (!f || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> g(mu);
+  known[key] = n;
   return n;
 }
 

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <condition_variable>
 #include <deque>
 #include <iterator>
@@ -40,9 +41,13 @@ struct Job {
   int seq_block = 0;  // tiled with bitmap output: sequences per (tile, block) item
   size_t smem = 0;
   uint64_t lo = 0, hi = 0, unit_lo = 0, unit_hi = 0, chunk_units = 0, nchunks = 0, rest = 0;
-  uint2* planes = nullptr;
+  uint2* planes = nullptr;    // one allocation: the planes, then the codes
   uint64_t* codes = nullptr;
   size_t win_bytes = 0;
+  // Pinned staging of a job submitted from host rows: its characters, read by the pack kernel
+  // on the submit stream; back to the pool when the job is released.
+  uint64_t* stage = nullptr;
+  size_t stage_cap = 0;
   uint32_t* qidx[2] = {nullptr, nullptr};
   uint64_t* qmask[2] = {nullptr, nullptr};
   uint64_t qcap = 0;
@@ -92,11 +97,19 @@ struct Server {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // Pinned host blocks for results, by capacity in codes (guarded by mu): a result is copied at
   // full link rate into pages that are already mapped, and motif_poll gives its block back.
+  std::mutex pool_mu;  // guards host_free (taken by the scheduler, given back by motif_poll)
   std::multimap<size_t, uint64_t*> host_free;
   size_t host_free_bytes = 0;
   // Retirement of a step's finished jobs together (retire_finished): pinned staging of their
   // sort / compaction tasks and of the table's states, and the tasks' device copies.
   JobState* h_states = nullptr;
+  // The table's upload: pinned descriptors and states, the step control, and the host's copy of
+  // the device states as of the last step or upload (the jobs' states move with them when the
+  // table is compacted, on the host, and go up with the next upload).
+  JobDesc* h_jobs = nullptr;
+  JobState* h_table = nullptr;
+  StepCtl* h_ctl = nullptr;
+  std::vector<JobState> mirror;
   SortTask* h_sort_tasks = nullptr;
   BitmapTask* h_bm_tasks = nullptr;
   unsigned* h_bm_first = nullptr;
@@ -110,13 +123,16 @@ constexpr size_t kHostPoolBytes = (size_t)2 << 30;  // pinned result blocks kept
 // A pinned block for at least `n` codes: a pooled one at most twice that size, else a new one of
 // the next power of two.  Null when pinned memory is exhausted.
 uint64_t* host_take(Server* S, size_t n, size_t* cap) {
-  auto it = S->host_free.lower_bound(n);
-  if (it != S->host_free.end() && it->first <= 2 * n) {
-    uint64_t* b = it->second;
-    *cap = it->first;
-    S->host_free_bytes -= it->first * 8;
-    S->host_free.erase(it);
-    return b;
+  {
+    std::lock_guard<std::mutex> g(S->pool_mu);
+    auto it = S->host_free.lower_bound(n);
+    if (it != S->host_free.end() && it->first <= 2 * n) {
+      uint64_t* b = it->second;
+      *cap = it->first;
+      S->host_free_bytes -= it->first * 8;
+      S->host_free.erase(it);
+      return b;
+    }
   }
   size_t c = 1024;
   while (c < n) c <<= 1;
@@ -129,11 +145,12 @@ uint64_t* host_take(Server* S, size_t n, size_t* cap) {
   return b;
 }
 
-// Returns a block to the pool (under S->mu).  Blocks that do not fit the pool's bound go to
-// `evicted`, for the caller to free once it has released the lock: cudaFreeHost may wait for the
-// device, which must not hold up the scheduler.
+// Returns a block to the pool.  Blocks that do not fit the pool's bound go to `evicted`, for the
+// caller to free once it has released its locks: cudaFreeHost may wait for the device, which
+// must not hold up the scheduler.
 void host_give(Server* S, uint64_t* b, size_t cap, std::vector<uint64_t*>* evicted) {
   if (!b) return;
+  std::lock_guard<std::mutex> g(S->pool_mu);
   if (cap * 8 > kHostPoolBytes) {
     evicted->push_back(b);
     return;
@@ -164,14 +181,25 @@ void sfree(Server* S, void* p) {
   if (p) cudaFreeAsync(p, S->stream);
 }
 
+// Gives a job's character staging back to the pool.  (A block given back while the job's pack
+// kernel may still read it only ever spoils the windows of that job, which is being discarded:
+// every later user of the block packs on the same stream, after it.)
+void release_stage(Server* S, Job* j) {
+  if (!j->stage) return;
+  std::vector<uint64_t*> evicted;
+  host_give(S, j->stage, j->stage_cap, &evicted);
+  for (uint64_t* b : evicted) cudaFreeHost(b);
+  j->stage = nullptr;
+}
+
 void release_windows_from_client(Server* S, Job* j) {
   std::lock_guard<std::mutex> g(S->submit_mu);
-  if (j->planes) cudaFreeAsync(j->planes, S->submit_stream);
-  if (j->codes) cudaFreeAsync(j->codes, S->submit_stream);
+  if (j->planes) cudaFreeAsync(j->planes, S->submit_stream);  // the codes share it
   j->planes = nullptr;
   j->codes = nullptr;
   if (j->ready) cudaEventDestroy(j->ready);
   j->ready = nullptr;
+  release_stage(S, j);
 }
 
 // Queues, output and sort scratch: held only while the job is admitted.
@@ -204,8 +232,7 @@ void release_buffers(Server* S, Job* j) {
   sfree(S, j->sort);
   sfree(S, j->bitmap);
   sfree(S, j->bm_scratch);
-  sfree(S, j->planes);
-  sfree(S, j->codes);
+  sfree(S, j->planes);  // the codes share it
   j->out = nullptr;
   j->sort = nullptr;
   j->bitmap = nullptr;
@@ -214,6 +241,7 @@ void release_buffers(Server* S, Job* j) {
   j->codes = nullptr;
   if (j->ready) cudaEventDestroy(j->ready);
   j->ready = nullptr;
+  release_stage(S, j);
 }
 
 int64_t footprint_of(const Job* j) {
@@ -308,28 +336,26 @@ unsigned tiles_per_warp(const Server* S) {
 
 // Uploads descriptors of the active jobs; states of jobs that moved down are copied, states of
 // newly admitted jobs zeroed, and unused slots marked done.
+// Uploads the descriptors and states of the table, two copies from pinned memory: the state of
+// slot i is the host copy's state of slot old_slot[i], or zero for a newly admitted job
+// (old_slot[i] < 0); unused slots are marked done.  The pinned buffers are written again only
+// after the next step's wait, so the copies are complete by then.
 int upload_table(Server* S, const std::vector<int>& old_slot) {
   const int cap = max_active(S);
-  std::vector<JobDesc> descs(cap);
-  memset(descs.data(), 0, sizeof(JobDesc) * cap);
-  for (size_t i = 0; i < S->active.size(); ++i) fill_job_desc(S->active[i], &descs[i]);
-  cudaError_t e = cudaMemcpyAsync(S->d_jobs, descs.data(), sizeof(JobDesc) * cap,
+  const int nact = (int)S->active.size();
+  memset(S->h_jobs, 0, sizeof(JobDesc) * cap);
+  memset(S->h_table, 0, sizeof(JobState) * cap);
+  for (int i = 0; i < nact; ++i) {
+    fill_job_desc(S->active[i], &S->h_jobs[i]);
+    if (old_slot[i] >= 0) S->h_table[i] = S->mirror[old_slot[i]];
+  }
+  for (int i = nact; i < cap; ++i) S->h_table[i].done = 1;
+  S->mirror.assign(S->h_table, S->h_table + cap);
+  cudaError_t e = cudaMemcpyAsync(S->d_jobs, S->h_jobs, sizeof(JobDesc) * cap,
                                   cudaMemcpyHostToDevice, S->stream);
-  for (size_t i = 0; i < S->active.size() && e == cudaSuccess; ++i) {
-    if (old_slot[i] < 0)
-      e = cudaMemsetAsync(&S->d_states[i], 0, sizeof(JobState), S->stream);
-    else if (old_slot[i] != (int)i)
-      e = cudaMemcpyAsync(&S->d_states[i], &S->d_states[old_slot[i]], sizeof(JobState),
-                          cudaMemcpyDeviceToDevice, S->stream);
-  }
-  if (e == cudaSuccess && (int)S->active.size() < cap) {
-    std::vector<JobState> idle(cap - S->active.size());
-    memset(idle.data(), 0, sizeof(JobState) * idle.size());
-    for (auto& st : idle) st.done = 1;
-    e = cudaMemcpyAsync(&S->d_states[S->active.size()], idle.data(), sizeof(JobState) * idle.size(),
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S->d_states, S->h_table, sizeof(JobState) * cap,
                         cudaMemcpyHostToDevice, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);  // `idle` goes out of scope
-  }
   return status_from_cuda(e);
 }
 
@@ -499,8 +525,15 @@ void scheduler(Server* S) {
       S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
       continue;
     }
+    // From here to the end of the step's retirement the lock is not held: the table
+    // (S->active) is the scheduler thread's own, and clients read a job's results only after its
+    // done flag is set under the lock, so submissions and polls go on meanwhile.
+    const int nact = (int)S->active.size();
+    lk.unlock();
     if (dirty) {
-      if (upload_table(S, old_slot) != MOTIF_OK) {
+      const int rc = upload_table(S, old_slot);
+      if (rc != MOTIF_OK) {
+        lk.lock();
         for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
         S->active.clear();
         S->cv_done.notify_all();
@@ -508,12 +541,11 @@ void scheduler(Server* S) {
       }
       dirty = false;
     }
-    const int nact = (int)S->active.size();
-    lk.unlock();
     // One device step over the whole table.
-    StepCtl ctl{};
-    ctl.tiles_per_warp = tiles_per_warp(S);
-    cudaError_t e = cudaMemcpyAsync(S->d_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, S->stream);
+    *S->h_ctl = StepCtl{};
+    S->h_ctl->tiles_per_warp = tiles_per_warp(S);
+    cudaError_t e = cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice,
+                                    S->stream);
     cudaEventRecord(S->ev0, S->stream);
     if (e == cudaSuccess) {
       if (S->exec) {
@@ -526,20 +558,21 @@ void scheduler(Server* S) {
       }
     }
     cudaEventRecord(S->ev1, S->stream);
-    std::vector<JobState> st(nact);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(st.data(), S->d_states, sizeof(JobState) * nact, cudaMemcpyDeviceToHost,
-                          S->stream);
+      e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(JobState) * nact,
+                          cudaMemcpyDeviceToHost, S->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     float step_ms = 0;
     cudaEventElapsedTime(&step_ms, S->ev0, S->ev1);
-    lk.lock();
     if (e != cudaSuccess) {
+      lk.lock();
       for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
       S->active.clear();
       S->cv_done.notify_all();
       continue;
     }
+    const std::vector<JobState> st(S->h_states, S->h_states + nact);
+    std::copy(st.begin(), st.end(), S->mirror.begin());
     // Retire finished jobs (keeping table order for the rest), all of them together.
     std::vector<Job*> keep;
     std::vector<int> moved, fin, failed;
@@ -557,7 +590,7 @@ void scheduler(Server* S) {
           j->status = MOTIF_ERR_OOM;
           failed.push_back(i);
         } else {
-          cudaMemsetAsync(&S->d_states[i], 0, sizeof(JobState), S->stream);
+          S->mirror[i] = JobState{};  // it starts again
           keep.push_back(j);
           moved.push_back(i);
           dirty = true;  // descriptor changed
@@ -568,6 +601,7 @@ void scheduler(Server* S) {
     }
     if (!fin.empty()) retire_finished(S, fin, st, nact);
     fin.insert(fin.end(), failed.begin(), failed.end());
+    lk.lock();
     for (const int i : fin) {
       Job* j = S->active[i];
       j->t_done = now_ms();
@@ -576,16 +610,14 @@ void scheduler(Server* S) {
       release_buffers(S, j);
       dirty = true;
     }
+    if (!fin.empty()) S->cv_done.notify_all();
     if (dirty) {
+      // The remaining jobs move down to their new slots, their states with them in the host
+      // copy; the next upload (at the loop's top, after admission) takes them to the device.
       S->active = keep;
-      old_slot = moved;
-      // States move down to their new slots before the next step (upload_table at loop top).
-      if (upload_table(S, old_slot) != MOTIF_OK) {
-        for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
-        S->active.clear();
-      }
-      dirty = false;
-      S->cv_done.notify_all();
+      std::vector<JobState> moved_states(S->mirror.size());
+      for (size_t i = 0; i < moved.size(); ++i) moved_states[i] = S->mirror[moved[i]];
+      S->mirror.swap(moved_states);
     }
   }
   // Shutdown: fail whatever is still queued.
@@ -606,7 +638,7 @@ void free_fixed(Server* S) {
                   (void*)S->d_bm_tasks, (void*)S->d_bm_first})
     if (d) cudaFree(d);
   for (void* h : {(void*)S->h_states, (void*)S->h_sort_tasks, (void*)S->h_bm_tasks,
-                  (void*)S->h_bm_first})
+                  (void*)S->h_bm_first, (void*)S->h_jobs, (void*)S->h_table, (void*)S->h_ctl})
     if (h) cudaFreeHost(h);
   if (S->ev0) cudaEventDestroy(S->ev0);
   if (S->ev1) cudaEventDestroy(S->ev1);
@@ -635,6 +667,9 @@ int start_locked(const motif_server_opts* opts) {
       cudaMalloc(&S->d_states, sizeof(JobState) * cap) != cudaSuccess ||
       cudaMalloc(&S->d_ctl, sizeof(StepCtl)) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_states, sizeof(JobState) * cap, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_jobs, sizeof(JobDesc) * cap, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_table, sizeof(JobState) * cap, 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_ctl, sizeof(StepCtl), 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_sort_tasks, sizeof(SortTask) * cap, 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_bm_tasks, sizeof(BitmapTask) * cap, 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_bm_first, sizeof(unsigned) * (cap + 1), 0) != cudaSuccess ||
@@ -676,6 +711,7 @@ extern "C" int motif_server_stop(void) {
   S->cv_work.notify_all();
   S->th.join();
   cudaStreamSynchronize(S->stream);
+  cudaStreamSynchronize(S->submit_stream);  // the pack kernels have read their staging
   for (auto& kv : S->jobs) {
     release_buffers(S, kv.second);
     if (kv.second->result) cudaFreeHost(kv.second->result);
@@ -689,19 +725,12 @@ extern "C" int motif_server_stop(void) {
   return MOTIF_OK;
 }
 
-extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
-  if (!p || !job_id) return MOTIF_ERR_ARG;
-  if (!p->loaded) return MOTIF_ERR_STATE;
-  DeviceGuard g(p->device);
-  // Validate device-loaded characters before accepting the job.
-  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MOTIF_ERR_CUDA;
-  if (p->check_alpha) {
-    int err = 0;
-    if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return MOTIF_ERR_CUDA;
-    p->check_alpha = false;
-    if (err) { p->loaded = false; return MOTIF_ERR_ALPHABET; }
-  }
+namespace motif_serve {
+
+// Builds and queues the job of a configured plan.  Its windows are the plan's packed windows
+// (seqs == NULL: copied on the submit stream) or are packed on the submit stream from the n host
+// rows at seqs (row r at seqs + r * stride, characters already checked).
+int submit_job(motif_plan_s* p, const char* seqs, int64_t stride, int64_t* job_id) {
   Server* S;
   {
     std::lock_guard<std::mutex> lg(g_life);
@@ -751,23 +780,52 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
     // Private copies of the packed windows, made on the submit stream; the scheduler's stream
     // waits for `ready` before the job's first step, and the plan's stream waits for it too, so
     // the plan may be reused or destroyed as soon as this returns.
-    j->win_bytes = (size_t)j->n * j->wstride * 8;
-    cudaError_t e = cudaMallocAsync((void**)&j->planes, j->win_bytes, S->submit_stream);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&j->codes, j->win_bytes, S->submit_stream);
+    j->win_bytes = (size_t)j->n * j->wstride * 8;  // a multiple of 16 bytes
+    cudaError_t e = cudaMallocAsync((void**)&j->planes, 2 * j->win_bytes, S->submit_stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(j->planes, p->d_planes, j->win_bytes, cudaMemcpyDeviceToDevice,
-                          S->submit_stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(j->codes, p->d_codes, j->win_bytes, cudaMemcpyDeviceToDevice,
-                          S->submit_stream);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(j->ready, S->submit_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, j->ready, 0);
+      j->codes = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(j->planes) + j->win_bytes);
+    if (seqs) {
+      // The rows go into a pinned staging block, row after row, and the pack kernel reads them
+      // there (pinned memory is in the device's address space), on the submit stream.
+      const size_t chars = (size_t)j->n * j->t;
+      if (e == cudaSuccess) {
+        j->stage = host_take(S, (chars + 7) / 8, &j->stage_cap);
+        if (!j->stage) e = cudaErrorMemoryAllocation;
+      }
+      char* d_stage = nullptr;  // the block's device address (an error, not a fault, if unmapped)
+      if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&d_stage, j->stage, 0);
+      if (e == cudaSuccess) {
+        char* dst = reinterpret_cast<char*>(j->stage);
+        for (int r = 0; r < j->n; ++r)
+          memcpy(dst + (size_t)r * j->t, seqs + (size_t)r * stride, (size_t)j->t);
+        e = launch_pack(d_stage, j->t, j->n, j->t, j->l, j->wstride, j->planes, j->codes,
+                        nullptr, S->submit_stream);
+      }
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(j->ready, S->submit_stream);
+    } else {
+      // Private copies of the plan's windows, ordered after its packing; the plan's stream
+      // waits for `ready` too, so the plan may be reused or destroyed as soon as this returns.
+      cudaEvent_t packed = nullptr;
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&packed, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(packed, p->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(S->submit_stream, packed, 0);
+      if (packed) cudaEventDestroy(packed);  // released once the waits have seen it
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->planes, p->d_planes, j->win_bytes, cudaMemcpyDeviceToDevice,
+                            S->submit_stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->codes, p->d_codes, j->win_bytes, cudaMemcpyDeviceToDevice,
+                            S->submit_stream);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(j->ready, S->submit_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, j->ready, 0);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       if (j->planes) cudaFreeAsync(j->planes, S->submit_stream);
-      if (j->codes) cudaFreeAsync(j->codes, S->submit_stream);
       if (j->ready) cudaEventDestroy(j->ready);
+      release_stage(S, j);
       delete j;
       return status_from_cuda(e);
     }
@@ -790,6 +848,56 @@ extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
   }
   *job_id = j->id;
   return MOTIF_OK;
+}
+
+// True when every character of the n rows is one of ACGTacgt.
+bool host_chars_valid(const char* seqs, int64_t stride, int n, int t) {
+  static const std::array<uint8_t, 256> valid = [] {
+    std::array<uint8_t, 256> a{};
+    for (unsigned char c : {'A', 'C', 'G', 'T', 'a', 'c', 'g', 't'}) a[c] = 1;
+    return a;
+  }();
+  unsigned bad = 0;
+  for (int r = 0; r < n; ++r) {
+    const unsigned char* row = reinterpret_cast<const unsigned char*>(seqs) + (size_t)r * stride;
+    for (int c = 0; c < t; ++c) bad |= valid[row[c]] ^ 1u;
+  }
+  return bad == 0;
+}
+
+}  // namespace motif_serve
+
+extern "C" int motif_submit(motif_plan p, int64_t* job_id) {
+  if (!p || !job_id) return MOTIF_ERR_ARG;
+  if (!p->loaded) return MOTIF_ERR_STATE;
+  DeviceGuard g(p->device);
+  // Validate device-loaded characters before accepting the job (host loads were checked while
+  // they were staged; their windows are ordered before the job's copies by an event).
+  if (p->check_alpha) {
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return MOTIF_ERR_CUDA;
+    int err = 0;
+    if (cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return MOTIF_ERR_CUDA;
+    p->check_alpha = false;
+    if (err) { p->loaded = false; return MOTIF_ERR_ALPHABET; }
+  }
+  return submit_job(p, nullptr, 0, job_id);
+}
+
+extern "C" int motif_submit_seqs(const char* seqs, int64_t stride, int32_t n, int32_t t,
+                                 int32_t l, int32_t d, const motif_opts* opts, int64_t* job_id) {
+  if (!seqs || !job_id) return MOTIF_ERR_ARG;
+  // A plan without device memory carries the configuration (the same choices as
+  // motif_plan_create makes); its options may name no stream or allocator of their own.
+  std::unique_ptr<motif_plan_s> p(new (std::nothrow) motif_plan_s());
+  if (!p) return MOTIF_ERR_OOM;
+  int rc = plan_init_host(p.get(), n, t, l, d, opts);
+  if (rc) return rc;
+  if (stride < t) return MOTIF_ERR_ARG;
+  if (!host_chars_valid(seqs, stride, n, t)) return MOTIF_ERR_ALPHABET;
+  rc = plan_configure_host(p.get());
+  if (rc) return rc;
+  return submit_job(p.get(), seqs, stride, job_id);
 }
 
 extern "C" int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity,

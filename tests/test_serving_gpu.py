@@ -1,6 +1,7 @@
 """Serving (continuous batching) on the GPU: jobs submitted while others run are admitted into
 the shared job table; every result equals the oracle's and the result of the same job served
 alone (exact equality: the result is an integer set)."""
+import ctypes
 import random
 
 import numpy as np
@@ -161,3 +162,64 @@ def test_other_variant_does_not_hold_back_later_jobs(server):
     for c in codes_a.tolist():
         ref, _ = oracle.search(long_job.rows(), long_job.l, long_job.d, lo=c, hi=c + 1)
         assert ref.tolist() == [c]
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_submit_seqs_equals_oracle_and_plan_path(server, use_graph):
+    """Jobs submitted from host rows without a plan, mixed with plan-submitted jobs in one table,
+    give the oracle's result and the same result as through a plan."""
+    m.motif_server_start(max_active=6, step_tiles=64, use_graph=use_graph)
+    jobs = _mix(11, 10)
+    # alternately through a plan and straight from the rows (as strings and as a uint8 array)
+    ids = []
+    for i, job in enumerate(jobs):
+        if i % 3 == 0:
+            ids.append(_submit(job))
+        elif i % 3 == 1:
+            ids.append(m.motif_submit_seqs(job.rows(), job.l, job.d))
+        else:
+            arr = np.frombuffer("".join(job.rows()).encode(), dtype=np.uint8).reshape(job.n, job.t)
+            ids.append(m.motif_submit_seqs(arr, job.l, job.d))
+    got = [m.motif_poll(jid, timeout_ms=120000)[0] for jid in ids]
+    for job, g in zip(jobs, got):
+        ref, _ = oracle.search(job.rows(), job.l, job.d, threads=8)
+        assert np.array_equal(g, ref)
+    for job, g in zip(jobs[:3], got[:3]):  # each path alone
+        assert np.array_equal(m.motif_poll(m.motif_submit_seqs(job.rows(), job.l, job.d),
+                                           timeout_ms=120000)[0], g)
+        assert np.array_equal(m.motif_poll(_submit(job), timeout_ms=120000)[0], g)
+
+
+def test_submit_seqs_range_and_errors(server):
+    """A sub-range through the options; lower-case rows; the host-side checks."""
+    m.motif_server_start(max_active=4)
+    job = fmgen.fm_job(6, 200, 9, 2, 77)
+    full = m.motif_poll(m.motif_submit_seqs(job.rows(), job.l, job.d), timeout_ms=120000)[0]
+    ref, _ = oracle.search(job.rows(), job.l, job.d, threads=8)
+    assert np.array_equal(full, ref)
+    lo, hi = 1 << 12, 3 << 15
+    o = m.motif_opts_default()
+    o.range_lo, o.range_hi = lo, hi
+    part = m.motif_poll(m.motif_submit_seqs(job.rows(), job.l, job.d, o), timeout_ms=120000)[0]
+    assert np.array_equal(part, ref[(ref >= lo) & (ref < hi)])
+    lower = [r.lower() for r in job.rows()]
+    assert np.array_equal(m.motif_poll(m.motif_submit_seqs(lower, job.l, job.d),
+                                       timeout_ms=120000)[0], ref)
+    bad = list(job.rows())
+    bad[3] = bad[3][:50] + "N" + bad[3][51:]
+    with pytest.raises(m.MotifError) as e:
+        m.motif_submit_seqs(bad, job.l, job.d)
+    assert e.value.status == m.ERR_ALPHABET
+    lib = m._load()
+    jid = ctypes.c_int64(-1)
+    buf = "".join(job.rows()).encode()
+    assert lib.motif_submit_seqs(buf, job.t - 1, job.n, job.t, job.l, job.d, None,
+                                 ctypes.byref(jid)) == m.ERR_ARG          # stride < t
+    assert lib.motif_submit_seqs(None, job.t, job.n, job.t, job.l, job.d, None,
+                                 ctypes.byref(jid)) == m.ERR_ARG          # no rows
+    assert lib.motif_submit_seqs(buf, job.t, job.n, job.t, 0, job.d, None,
+                                 ctypes.byref(jid)) == m.ERR_ARG          # l < 1
+    assert jid.value == -1
+    # rows shorter than l: no windows, nothing survives
+    short = m.motif_poll(m.motif_submit_seqs(["ACGT"] * 3, 6, 1), timeout_ms=120000)[0]
+    assert short.size == 0

@@ -317,7 +317,8 @@ typedef struct {
   int32_t max_queued;      /* jobs waiting for admission before submit returns BUSY; 0 = 4096 */
   int64_t device_budget;   /* bytes of device memory the admitted jobs may hold; 0 = 8 GiB */
   int32_t step_tiles;      /* candidate tiles one device step may take over all its warps
-                              (admissions happen between steps); 0 = 48 per warp */
+                              (admissions happen between steps); 0 = 48 per warp, 192 while
+                              jobs wait for admission */
   int32_t use_graph;       /* != 0: replay the step launch from a CUDA graph */
   int32_t timeout_ms;      /* not used: each server step is bounded by step_tiles, and callers
                               bound their waits with motif_poll's timeout_ms */

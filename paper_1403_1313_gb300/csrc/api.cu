@@ -108,15 +108,51 @@ int fold_event_quads(motif_plan_s* p) {
   return MOTIF_OK;
 }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaMemPool_t device_pool(int device) {
+  if (device < 0 || device >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool[device]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = kPoolKeepBytes;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      cudaMemPoolDestroy(pool);
+      return nullptr;
+    }
+    g_pool[device] = pool;
+  }
+  return g_pool[device];
+}
+
+void* pool_alloc(int device, size_t bytes, cudaStream_t s) {
+  void* ptr = nullptr;
+  cudaMemPool_t pool = device_pool(device);
+  if (!pool || cudaMallocFromPoolAsync(&ptr, bytes, pool, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return ptr;
+}
+
 void* plan_alloc(motif_plan_s* p, size_t bytes) {
   if (bytes == 0) return nullptr;
   void* ptr = nullptr;
-  if (p->opts.alloc) {
-    ptr = p->opts.alloc(bytes, p->stream, p->opts.alloc_ctx);
-  } else if (cudaMallocAsync(&ptr, bytes, p->stream) != cudaSuccess) {
-    cudaGetLastError();
-    ptr = nullptr;
-  }
+  if (p->opts.alloc) ptr = p->opts.alloc(bytes, p->stream, p->opts.alloc_ctx);
+  else ptr = pool_alloc(p->device, bytes, p->stream);
   if (ptr) p->device_bytes += (int64_t)bytes;
   return ptr;
 }

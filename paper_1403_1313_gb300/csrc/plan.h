@@ -110,7 +110,14 @@ struct motif_plan_s {
 
 namespace motif {
 
-// Device memory through the plan's allocator (or stream-ordered cudaMallocAsync).
+// The library's stream-ordered memory pool of a device (made on first use): freed blocks up to
+// kPoolKeepBytes stay in it between synchronisations instead of going back to the driver, so
+// the many small buffers of short-lived plans and served jobs come back without a new mapping.
+constexpr uint64_t kPoolKeepBytes = (uint64_t)256 << 20;
+cudaMemPool_t device_pool(int device);
+// Stream-ordered device memory from that pool (freed with cudaFreeAsync); null on failure.
+void* pool_alloc(int device, size_t bytes, cudaStream_t s);
+// Device memory through the plan's allocator (or the device's pool, stream-ordered).
 void* plan_alloc(motif_plan_s* p, size_t bytes);
 void plan_free(motif_plan_s* p, void* ptr, size_t bytes);
 

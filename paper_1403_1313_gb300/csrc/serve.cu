@@ -110,6 +110,11 @@ struct Server {
   JobState* h_table = nullptr;
   StepCtl* h_ctl = nullptr;
   std::vector<JobState> mirror;
+  // The retirement of a step's finished jobs runs on its own stream, during the next step: the
+  // step's state snapshot (two, alternating) and the final counts read from it.
+  cudaStream_t retire_stream = nullptr;
+  JobState* d_snap[2] = {nullptr, nullptr};
+  JobState* h_fin = nullptr;
   SortTask* h_sort_tasks = nullptr;
   BitmapTask* h_bm_tasks = nullptr;
   unsigned* h_bm_first = nullptr;
@@ -168,15 +173,13 @@ void host_give(Server* S, uint64_t* b, size_t cap, std::vector<uint64_t*>* evict
 std::mutex g_life;  // guards g_srv creation / destruction
 Server* g_srv = nullptr;
 
-void* salloc(Server* S, size_t b) {
-  void* p = nullptr;
+// Device memory in the order of stream s (the scheduler's stream by default); freed on the
+// scheduler's stream once nothing uses it any more.
+void* salloc_on(Server* S, size_t b, cudaStream_t s) {
   if (b == 0) return nullptr;
-  if (cudaMallocAsync(&p, b, S->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return p;
+  return pool_alloc(S->device, b, s);
 }
+void* salloc(Server* S, size_t b) { return salloc_on(S, b, S->stream); }
 void sfree(Server* S, void* p) {
   if (p) cudaFreeAsync(p, S->stream);
 }
@@ -327,11 +330,14 @@ int prepare_launch(Server* S, int kind, int pv, size_t smem) {
   return MOTIF_OK;
 }
 
-// Tile budget per warp and step: bounds the length of one step.
-unsigned tiles_per_warp(const Server* S) {
+// Tile budget per warp and step: bounds the length of one step, so that arrivals are admitted
+// soon.  While jobs wait for admission (backlog) the default budget is four times larger: a
+// full table gains more from fewer, longer steps (less scheduling per job) than a waiting job
+// loses.
+unsigned tiles_per_warp(const Server* S, bool backlog) {
   const unsigned warps = (unsigned)S->grid * (unsigned)(S->block / 32);
   if (S->o.step_tiles > 0) return std::max(1u, (unsigned)S->o.step_tiles / std::max(1u, warps));
-  return 48;
+  return backlog ? 192 : 48;
 }
 
 // Uploads descriptors of the active jobs; states of jobs that moved down are copied, states of
@@ -359,55 +365,63 @@ int upload_table(Server* S, const std::vector<int>& old_slot) {
   return status_from_cuda(e);
 }
 
-// Copies a finished job's `count` ascending codes from its output buffer to a pinned host block.
-int copy_result(Server* S, Job* j, unsigned long long fc) {
+// Copies a finished job's `count` ascending codes from its output buffer to a pinned host block,
+// on stream r.
+int copy_result(Server* S, Job* j, unsigned long long fc, cudaStream_t r) {
   j->result_size = (int64_t)fc;
   if (fc) {
     j->result = host_take(S, fc, &j->result_cap);
     if (!j->result) return MOTIF_ERR_OOM;
   }
   cudaError_t e = cudaSuccess;
-  if (fc) e = cudaMemcpyAsync(j->result, j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+  if (fc) e = cudaMemcpyAsync(j->result, j->out, fc * 8, cudaMemcpyDeviceToHost, r);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r);
   return status_from_cuda(e);
 }
 
-// Bitmap output: compacts the job's bitmap in order into its output buffer (grown, and the
-// compaction repeated, when the codes do not fit) and copies the codes to the host.
-int finish_bitmap_job(Server* S, Job* j, int slot) {
+// Bitmap output whose codes outgrew the buffer: compacts the job's bitmap in order into its
+// output buffer again (grown, and the compaction repeated, until the codes fit), counting at
+// cnt, and copies the codes to the host; on stream r.
+int finish_bitmap_job(Server* S, Job* j, unsigned long long* cnt, cudaStream_t r) {
   unsigned long long fc = 0;
   for (;;) {
     cudaError_t e = launch_bitmap_compact(j->bitmap, j->bm_words, j->bm_base, j->out, j->out_cap,
-                                          j->bm_scratch, &S->d_states[slot].out_count, S->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&fc, &S->d_states[slot].out_count, sizeof(fc), cudaMemcpyDeviceToHost,
-                          S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+                                          j->bm_scratch, cnt, r);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&fc, cnt, sizeof(fc), cudaMemcpyDeviceToHost, r);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r);
     if (e != cudaSuccess) return status_from_cuda(e);
     if (fc <= (unsigned long long)j->out_cap) break;
     sfree(S, j->out);
     j->out_cap = (int64_t)fc;
-    j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
+    j->out = (uint64_t*)salloc_on(S, (size_t)j->out_cap * 8, r);
     if (!j->out) return MOTIF_ERR_OOM;
   }
-  return copy_result(S, j, fc);
+  return copy_result(S, j, fc, r);
 }
 
-// Finishes the jobs of the table slots `fin` (their steps are done and their codes fit their
-// buffers), all at once: one launch sorts every list of at most 4096 codes, a radix sort runs per
-// larger list and three launches compact every bitmap; one wait then reads every final count,
-// the results are copied to pinned host blocks together, and one more wait ends the copies.  A
-// bitmap job whose codes outgrow its buffer takes finish_bitmap_job alone.  Sets each job's
-// status.
-void retire_finished(Server* S, const std::vector<int>& fin, const std::vector<JobState>& st,
-                     int nact) {
+// A job that finished in a step: the job, its slot in that step's table and the step's state
+// snapshot (whose out_count of the slot the sort / compaction counts in).
+struct Finished {
+  Job* j;
+  int slot;
+  JobState state;
+};
+
+// Finishes the jobs of one step (their codes fit their buffers), all at once, on the retire
+// stream while the next step runs: one launch sorts every list of at most 4096 codes, a radix
+// sort runs per larger list and three launches compact every bitmap, counting in the step's
+// snapshot `snap`; one wait then reads every final count, the results are copied to pinned
+// host blocks together, and one more wait ends the copies.  A bitmap job whose codes outgrow
+// its buffer takes finish_bitmap_job alone.  Sets each job's status.
+void retire_finished(Server* S, const std::vector<Finished>& fin, JobState* snap) {
+  cudaStream_t r = S->retire_stream;
   int nsmall = 0, nbm = 0;
   unsigned bm_blocks = 0;
-  for (const int i : fin) {
-    Job* j = S->active[i];
+  for (const Finished& f : fin) {
+    Job* j = f.j;
     j->status = MOTIF_OK;
-    const unsigned long long found = st[i].out_count;
-    unsigned long long* cnt = &S->d_states[i].out_count;
+    const unsigned long long found = f.state.out_count;
+    unsigned long long* cnt = &snap[f.slot].out_count;
     if (j->bitmap) {
       S->h_bm_first[nbm] = bm_blocks;
       S->h_bm_tasks[nbm++] = BitmapTask{j->bitmap, j->bm_words, j->bm_base, j->out,
@@ -415,11 +429,11 @@ void retire_finished(Server* S, const std::vector<int>& fin, const std::vector<J
       bm_blocks += (unsigned)bitmap_task_blocks(j->bm_words);
     } else if (found > 4096) {
       const size_t need = sort_scratch_bytes(j->out_cap, S->sms);
-      j->sort = salloc(S, need);
+      j->sort = salloc_on(S, need, r);
       j->sort_bytes = need;
       if (!j->sort ||
           launch_sort_unique(j->out, cnt, j->out_cap, 2 * j->l, j->sort, S->sms,
-                             (long long)found, S->stream) != cudaSuccess)
+                             (long long)found, r) != cudaSuccess)
         j->status = j->sort ? MOTIF_ERR_CUDA : MOTIF_ERR_OOM;
     } else if (found > 1) {
       S->h_sort_tasks[nsmall++] = SortTask{j->out, cnt, (long long)j->out_cap};
@@ -429,55 +443,83 @@ void retire_finished(Server* S, const std::vector<int>& fin, const std::vector<J
   cudaError_t e = cudaSuccess;
   if (nsmall)
     e = cudaMemcpyAsync(S->d_sort_tasks, S->h_sort_tasks, sizeof(SortTask) * nsmall,
-                        cudaMemcpyHostToDevice, S->stream);
+                        cudaMemcpyHostToDevice, r);
   if (e == cudaSuccess && nbm)
     e = cudaMemcpyAsync(S->d_bm_tasks, S->h_bm_tasks, sizeof(BitmapTask) * nbm,
-                        cudaMemcpyHostToDevice, S->stream);
+                        cudaMemcpyHostToDevice, r);
   if (e == cudaSuccess && nbm)
     e = cudaMemcpyAsync(S->d_bm_first, S->h_bm_first, sizeof(unsigned) * (nbm + 1),
-                        cudaMemcpyHostToDevice, S->stream);
-  if (e == cudaSuccess) e = launch_small_sort_tasks(S->d_sort_tasks, nsmall, S->stream);
+                        cudaMemcpyHostToDevice, r);
+  if (e == cudaSuccess) e = launch_small_sort_tasks(S->d_sort_tasks, nsmall, r);
   if (e == cudaSuccess)
-    e = launch_bitmap_compact_tasks(S->d_bm_tasks, S->d_bm_first, nbm, bm_blocks, S->stream);
+    e = launch_bitmap_compact_tasks(S->d_bm_tasks, S->d_bm_first, nbm, bm_blocks, r);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(JobState) * nact,
-                        cudaMemcpyDeviceToHost, S->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    e = cudaMemcpyAsync(S->h_fin, snap, sizeof(JobState) * max_active(S),
+                        cudaMemcpyDeviceToHost, r);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(r);
   if (e != cudaSuccess) {
-    for (const int i : fin) S->active[i]->status = MOTIF_ERR_CUDA;
+    for (const Finished& f : fin) f.j->status = MOTIF_ERR_CUDA;
     return;
   }
-  for (const int i : fin) {
-    Job* j = S->active[i];
+  for (const Finished& f : fin) {
+    Job* j = f.j;
     if (j->status != MOTIF_OK) continue;
-    const unsigned long long fc = S->h_states[i].out_count;
+    const unsigned long long fc = S->h_fin[f.slot].out_count;
     if (j->bitmap && fc > (unsigned long long)j->out_cap) {  // grow, compact again, copy
-      j->status = finish_bitmap_job(S, j, i);
+      j->status = finish_bitmap_job(S, j, &snap[f.slot].out_count, r);
       continue;
     }
     j->result_size = (int64_t)fc;
     if (!fc) continue;
     j->result = host_take(S, fc, &j->result_cap);
     if (!j->result) { j->status = MOTIF_ERR_OOM; continue; }
-    if (cudaMemcpyAsync(j->result, j->out, fc * 8, cudaMemcpyDeviceToHost, S->stream) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(j->result, j->out, fc * 8, cudaMemcpyDeviceToHost, r) != cudaSuccess)
       j->status = MOTIF_ERR_CUDA;
   }
-  if (cudaStreamSynchronize(S->stream) != cudaSuccess)
-    for (const int i : fin) S->active[i]->status = MOTIF_ERR_CUDA;
+  if (cudaStreamSynchronize(r) != cudaSuccess)
+    for (const Finished& f : fin) f.j->status = MOTIF_ERR_CUDA;
 }
 
+// Marks retired jobs done (under the lock) and releases their device buffers.
+void mark_done(Server* S, const std::vector<Finished>& fin) {
+  for (const Finished& f : fin) {
+    Job* j = f.j;
+    j->t_done = now_ms();
+    j->done = true;
+    S->budget_used -= j->footprint;
+    release_buffers(S, j);
+  }
+  if (!fin.empty()) S->cv_done.notify_all();
+}
+
+// Fails every job of the table and those still retiring (a CUDA error), under the lock.
+void fail_all(Server* S, std::vector<Finished>* retiring) {
+  for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
+  for (const Finished& f : *retiring) { f.j->status = MOTIF_ERR_CUDA; f.j->done = true; }
+  S->active.clear();
+  retiring->clear();
+  S->cv_done.notify_all();
+}
+
+// The scheduler loop.  Each turn: admission (under the lock), the upload of a changed table,
+// the launch of one step, then, while that step runs, the retirement of the jobs that finished
+// in the step before (on the retire stream); then the wait for the step and the compaction of
+// the table (finished jobs leave it at once: their codes and counts stay in their buffers and in
+// the step's state snapshot, one of two, until they are retired in the next turn).
 void scheduler(Server* S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
   bool dirty = true;
   std::vector<int> old_slot;
+  std::vector<Finished> retiring;  // finished in the last step, retired in this turn
+  int snap_buf = 0;                // the snapshot buffer of the next step
   for (;;) {
     // Admission, in arrival order, while slots and the memory budget allow.  The table runs one
     // kernel variant, so a job of another variant waits until the table drains; later jobs of
     // the table's variant are admitted past it until it has waited kHeadWaitMs, after which
     // nothing more is admitted and the table drains for it.  A job that does not fit the memory
-    // budget stops admission (memory is granted in arrival order).
+    // budget stops admission (memory is granted in arrival order; jobs still retiring hold
+    // theirs).
     const int64_t budget = S->o.device_budget > 0 ? S->o.device_budget : (8ll << 30);
     old_slot.assign(S->active.size(), 0);
     for (size_t i = 0; i < S->active.size(); ++i) old_slot[i] = (int)i;
@@ -493,7 +535,7 @@ void scheduler(Server* S) {
       if (!S->active.empty() && S->budget_used + j->footprint > budget) break;
       if (!allocate_job(S, j)) {
         release_run_buffers(S, j);  // keeps the window copies: the job stays queued
-        if (S->active.empty()) {  // cannot ever fit: fail the job
+        if (S->active.empty() && retiring.empty()) {  // cannot ever fit: fail the job
           release_buffers(S, j);
           it = S->queue.erase(it);
           j->status = MOTIF_ERR_OOM;
@@ -521,29 +563,38 @@ void scheduler(Server* S) {
       dirty = true;
     }
     if (S->active.empty()) {
+      if (!retiring.empty()) {  // nothing to overlap: retire the last step's jobs now
+        lk.unlock();
+        retire_finished(S, retiring, S->d_snap[snap_buf ^ 1]);
+        lk.lock();
+        mark_done(S, retiring);
+        retiring.clear();
+        continue;
+      }
       if (S->stopping) break;
       S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
       continue;
     }
-    // From here to the end of the step's retirement the lock is not held: the table
-    // (S->active) is the scheduler thread's own, and clients read a job's results only after its
-    // done flag is set under the lock, so submissions and polls go on meanwhile.
+    // From here to the compaction the lock is not held: the table (S->active) is the scheduler
+    // thread's own, and clients read a job's results only after its done flag is set under the
+    // lock, so submissions and polls go on meanwhile.
     const int nact = (int)S->active.size();
+    const bool backlog = !S->queue.empty();
     lk.unlock();
     if (dirty) {
       const int rc = upload_table(S, old_slot);
       if (rc != MOTIF_OK) {
         lk.lock();
-        for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
-        S->active.clear();
-        S->cv_done.notify_all();
+        fail_all(S, &retiring);
         continue;
       }
       dirty = false;
     }
-    // One device step over the whole table.
+    // One device step over the whole table, then its state snapshot (for the retirement of the
+    // jobs that finish in it) and the host copy of the states.
+    JobState* snap = S->d_snap[snap_buf];
     *S->h_ctl = StepCtl{};
-    S->h_ctl->tiles_per_warp = tiles_per_warp(S);
+    S->h_ctl->tiles_per_warp = tiles_per_warp(S, backlog);
     cudaError_t e = cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(StepCtl), cudaMemcpyHostToDevice,
                                     S->stream);
     cudaEventRecord(S->ev0, S->stream);
@@ -553,36 +604,44 @@ void scheduler(Server* S) {
         note_launches(1);
       } else {
         e = launch_step(launch_kind(S->kind, S->pv, true), S->pv, S->d_jobs, S->d_states,
-                        max_active(S), S->d_ctl,
-                        S->grid, S->block, S->smem, S->stream);
+                        max_active(S), S->d_ctl, S->grid, S->block, S->smem, S->stream);
       }
     }
     cudaEventRecord(S->ev1, S->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(S->h_states, S->d_states, sizeof(JobState) * nact,
-                          cudaMemcpyDeviceToHost, S->stream);
+      e = cudaMemcpyAsync(snap, S->d_states, sizeof(JobState) * max_active(S),
+                          cudaMemcpyDeviceToDevice, S->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(S->h_states, snap, sizeof(JobState) * nact, cudaMemcpyDeviceToHost,
+                          S->stream);
+    // The jobs of the step before retire while this one runs.
+    if (!retiring.empty()) {
+      retire_finished(S, retiring, S->d_snap[snap_buf ^ 1]);
+      lk.lock();
+      mark_done(S, retiring);
+      lk.unlock();
+      retiring.clear();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     float step_ms = 0;
     cudaEventElapsedTime(&step_ms, S->ev0, S->ev1);
     if (e != cudaSuccess) {
       lk.lock();
-      for (Job* j : S->active) { j->status = MOTIF_ERR_CUDA; j->done = true; }
-      S->active.clear();
-      S->cv_done.notify_all();
+      fail_all(S, &retiring);
       continue;
     }
     const std::vector<JobState> st(S->h_states, S->h_states + nact);
     std::copy(st.begin(), st.end(), S->mirror.begin());
-    // Retire finished jobs (keeping table order for the rest), all of them together.
+    // Compaction: finished jobs leave the table (to be retired next turn); jobs whose list
+    // outgrew its buffer start again in place with a larger one.
     std::vector<Job*> keep;
-    std::vector<int> moved, fin, failed;
+    std::vector<int> moved, failed;
     for (int i = 0; i < nact; ++i) {
       Job* j = S->active[i];
       j->gpu_ms += step_ms;
       if (!st[i].done) { keep.push_back(j); moved.push_back(i); continue; }
       const unsigned long long found = st[i].out_count;
       if (!j->bitmap && found > (unsigned long long)j->out_cap) {
-        // Output overflow: grow the buffer and restart the job in place.
         sfree(S, j->out);
         j->out_cap = (int64_t)found;
         j->out = (uint64_t*)salloc(S, (size_t)j->out_cap * 8);
@@ -597,27 +656,26 @@ void scheduler(Server* S) {
         }
         continue;
       }
-      fin.push_back(i);
+      retiring.push_back(Finished{j, i, st[i]});
     }
-    if (!fin.empty()) retire_finished(S, fin, st, nact);
-    fin.insert(fin.end(), failed.begin(), failed.end());
+    snap_buf ^= 1;
     lk.lock();
-    for (const int i : fin) {
+    for (const int i : failed) {
       Job* j = S->active[i];
       j->t_done = now_ms();
       j->done = true;
       S->budget_used -= j->footprint;
       release_buffers(S, j);
-      dirty = true;
+      S->cv_done.notify_all();
     }
-    if (!fin.empty()) S->cv_done.notify_all();
-    if (dirty) {
+    if (keep.size() != (size_t)nact) {
       // The remaining jobs move down to their new slots, their states with them in the host
       // copy; the next upload (at the loop's top, after admission) takes them to the device.
       S->active = keep;
       std::vector<JobState> moved_states(S->mirror.size());
       for (size_t i = 0; i < moved.size(); ++i) moved_states[i] = S->mirror[moved[i]];
       S->mirror.swap(moved_states);
+      dirty = true;
     }
   }
   // Shutdown: fail whatever is still queued.
@@ -635,10 +693,12 @@ void free_fixed(Server* S) {
   if (S->exec) cudaGraphExecDestroy(S->exec);
   if (S->graph) cudaGraphDestroy(S->graph);
   for (void* d : {(void*)S->d_jobs, (void*)S->d_states, (void*)S->d_ctl, (void*)S->d_sort_tasks,
-                  (void*)S->d_bm_tasks, (void*)S->d_bm_first})
+                  (void*)S->d_bm_tasks, (void*)S->d_bm_first, (void*)S->d_snap[0],
+                  (void*)S->d_snap[1]})
     if (d) cudaFree(d);
   for (void* h : {(void*)S->h_states, (void*)S->h_sort_tasks, (void*)S->h_bm_tasks,
-                  (void*)S->h_bm_first, (void*)S->h_jobs, (void*)S->h_table, (void*)S->h_ctl})
+                  (void*)S->h_bm_first, (void*)S->h_jobs, (void*)S->h_table, (void*)S->h_ctl,
+                  (void*)S->h_fin})
     if (h) cudaFreeHost(h);
   if (S->ev0) cudaEventDestroy(S->ev0);
   if (S->ev1) cudaEventDestroy(S->ev1);
@@ -646,6 +706,7 @@ void free_fixed(Server* S) {
     cudaStreamSynchronize(S->submit_stream);
     cudaStreamDestroy(S->submit_stream);
   }
+  if (S->retire_stream) cudaStreamDestroy(S->retire_stream);
   if (S->stream) cudaStreamDestroy(S->stream);
 }
 
@@ -670,6 +731,10 @@ int start_locked(const motif_server_opts* opts) {
       cudaHostAlloc((void**)&S->h_jobs, sizeof(JobDesc) * cap, 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_table, sizeof(JobState) * cap, 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_ctl, sizeof(StepCtl), 0) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_fin, sizeof(JobState) * cap, 0) != cudaSuccess ||
+      cudaMalloc(&S->d_snap[0], sizeof(JobState) * cap) != cudaSuccess ||
+      cudaMalloc(&S->d_snap[1], sizeof(JobState) * cap) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->retire_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_sort_tasks, sizeof(SortTask) * cap, 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_bm_tasks, sizeof(BitmapTask) * cap, 0) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_bm_first, sizeof(unsigned) * (cap + 1), 0) != cudaSuccess ||
@@ -781,7 +846,8 @@ int submit_job(motif_plan_s* p, const char* seqs, int64_t stride, int64_t* job_i
     // waits for `ready` before the job's first step, and the plan's stream waits for it too, so
     // the plan may be reused or destroyed as soon as this returns.
     j->win_bytes = (size_t)j->n * j->wstride * 8;  // a multiple of 16 bytes
-    cudaError_t e = cudaMallocAsync((void**)&j->planes, 2 * j->win_bytes, S->submit_stream);
+    j->planes = (uint2*)pool_alloc(S->device, 2 * j->win_bytes, S->submit_stream);
+    cudaError_t e = j->planes ? cudaSuccess : cudaErrorMemoryAllocation;
     if (e == cudaSuccess)
       j->codes = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(j->planes) + j->win_bytes);
     if (seqs) {

@@ -107,6 +107,8 @@ def parse():
                     help="batch mode: leave the plans on their AUTO choices")
     ap.add_argument("--tune-ms", type=int, default=400,
                     help="batch mode: motif_autotune's time budget per job")
+    ap.add_argument("--serve-max-active", type=int, default=128,
+                    help="serve mode: jobs resident in the server's table")
     ap.add_argument("--serve-submit", choices=["seqs", "plan"], default="seqs",
                     help="serve mode: submit jobs straight from their rows (motif_submit_seqs) "
                          "or through a plan (create, load, motif_submit, destroy)")
@@ -743,7 +745,7 @@ def run_serve(args):
     for rate in ([] if args.saturation_only else [float(r) for r in args.rates.split(",")]):
         count = int(min(args.serve_jobs, max(20, rate * args.serve_seconds)))
         jobs = fmgen.serving_jobs(rate, count, seed=5)
-        m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
+        m.motif_server_start(max_active=args.serve_max_active, step_tiles=args.serve_step_tiles)
         # warm-up job (graph capture, ball tables, allocator pools)
         wj = fmgen.fm_job(10, 300, 11, 3, 1)
         pl = m.motif_plan_create(wj.n, wj.t, wj.l, wj.d)
@@ -800,55 +802,60 @@ def run_serve(args):
                      "done_all_s": wall})
         print(json.dumps(rows[-1]), flush=True)
     # Saturation: the same jobs one after another through the blocking path (the plain one-job-
-    # per-launch path), then all submitted to the server at once; both include each job's plan
-    # creation, load and release.
+    # per-launch path: plan creation, load, search and release each), then all submitted to the
+    # server at once.  Each arm runs the whole job list once untimed first (allocator pools,
+    # graphs, pinned blocks), then timed: the plain path once, the server three times (median).
     jobs = fmgen.serving_jobs(1000.0, args.serve_jobs, seed=5)
-    for j in jobs[:8]:  # warm-up of both paths
-        pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
-        m.motif_load_seqs(pl, j.seqs)
-        m.motif_search(pl)
-        m.motif_plan_destroy(pl)
-    t0 = time.perf_counter()
-    plain_codes = []
-    dev_ms = 0.0
-    for j in jobs:
-        pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
-        m.motif_load_seqs(pl, j.seqs)
-        plain_codes.append(m.motif_search(pl))
-        stp = m.motif_stats(pl)
-        dev_ms += stp["search_ms"] + stp["sort_ms"]
-        m.motif_plan_destroy(pl)
-    t_plain = time.perf_counter() - t0
-    def served_at_once(via):
-        """Every job submitted at once (through `via`), then every result polled."""
-        m.motif_server_start(max_active=64, step_tiles=args.serve_step_tiles)
-        wj = fmgen.fm_job(10, 300, 11, 3, 1)
-        m.motif_poll(m.motif_submit_seqs(wj.seqs, wj.l, wj.d), timeout_ms=60000)
+
+    def plain_pass():
+        codes, dev = [], 0.0
         t0 = time.perf_counter()
-        ids = []
         for j in jobs:
-            if via == "seqs":
-                ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
-                continue
             pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
             m.motif_load_seqs(pl, j.seqs)
-            ids.append(m.motif_submit(pl))
+            codes.append(m.motif_search(pl))
+            stp = m.motif_stats(pl)
+            dev += stp["search_ms"] + stp["sort_ms"]
             m.motif_plan_destroy(pl)
-        t_client = time.perf_counter() - t0
-        served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
-        t_served = time.perf_counter() - t0
-        m.motif_server_stop()
-        return served, t_client, t_served
+        return codes, dev, time.perf_counter() - t0
 
-    served_plan, t_client_plan, t_served_plan = served_at_once("plan")
-    served, t_client, t_served = served_at_once(args.serve_submit)
+    plain_pass()
+    plain_codes, dev_ms, t_plain = plain_pass()
+
+    def served_at_once(via, reps):
+        """Every job submitted at once (through `via`), then every result polled; `reps` timed
+        passes after an untimed one on the same server."""
+        m.motif_server_start(max_active=args.serve_max_active, step_tiles=args.serve_step_tiles)
+        out = []
+        for rep in range(reps + 1):
+            t0 = time.perf_counter()
+            ids = []
+            for j in jobs:
+                if via == "seqs":
+                    ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
+                    continue
+                pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+                m.motif_load_seqs(pl, j.seqs)
+                ids.append(m.motif_submit(pl))
+                m.motif_plan_destroy(pl)
+            t_client = time.perf_counter() - t0
+            served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
+            if rep:
+                out.append((time.perf_counter() - t0, t_client, served))
+        m.motif_server_stop()
+        out.sort(key=lambda x: x[0])
+        return out[len(out) // 2], [x[0] for x in out]
+
+    (t_served_plan, t_client_plan, served_plan), _ = served_at_once("plan", 1)
+    (t_served, t_client, served), all_served = served_at_once(args.serve_submit, 3)
     same = all(np.array_equal(a, b[0]) and np.array_equal(a, c[0])
                for a, b, c in zip(plain_codes, served, served_plan))
     lat = np.array([b[1]["total_ms"] for b in served])
-    sat = {"jobs": len(jobs), "submit": args.serve_submit,
+    sat = {"jobs": len(jobs), "submit": args.serve_submit, "max_active": args.serve_max_active,
            "plain_jobs_per_s": len(jobs) / t_plain,
            "served_jobs_per_s": len(jobs) / t_served,
            "served_over_plain": t_plain / t_served,
+           "served_ms_all_reps": [1e3 * x for x in all_served],
            # the same jobs served through plans (create, load, motif_submit, destroy each)
            "served_via_plans_jobs_per_s": len(jobs) / t_served_plan,
            "served_via_plans_over_plain": t_plain / t_served_plan,
@@ -857,7 +864,7 @@ def run_serve(args):
            # the GPU as busy as each job alone does, with no host time at all, would take this
            "plain_device_ms": dev_ms,
            "ratio_bound_device_only": 1e3 * t_plain / max(dev_ms, 1e-9),
-           # the client's own loop (plan creation, load, submit and release of every job)
+           # the client's own loop (the submissions of every job)
            "served_client_loop_ms": 1e3 * t_client,
            "served_equals_plain": bool(same),
            "served_p50_ms": float(np.percentile(lat, 50)),

@@ -803,8 +803,9 @@ def run_serve(args):
         print(json.dumps(rows[-1]), flush=True)
     # Saturation: the same jobs one after another through the blocking path (the plain one-job-
     # per-launch path: plan creation, load, search and release each), then all submitted to the
-    # server at once.  Each arm runs the whole job list once untimed first (allocator pools,
-    # graphs, pinned blocks), then timed: the plain path once, the server three times (median).
+    # server at once.  Each arm runs the whole job list untimed first (allocator pools, graphs,
+    # pinned blocks: once for the plain path, twice for a server), then timed: the plain path
+    # once, the server three times (median).
     jobs = fmgen.serving_jobs(1000.0, args.serve_jobs, seed=5)
 
     def plain_pass():
@@ -822,12 +823,13 @@ def run_serve(args):
     plain_pass()
     plain_codes, dev_ms, t_plain = plain_pass()
 
-    def served_at_once(via, reps):
+    def served_at_once(via, reps, warm=2):
         """Every job submitted at once (through `via`), then every result polled; `reps` timed
-        passes after an untimed one on the same server."""
+        passes after `warm` untimed ones on the same server (a new server's pinned pools fill
+        during its first passes)."""
         m.motif_server_start(max_active=args.serve_max_active, step_tiles=args.serve_step_tiles)
         out = []
-        for rep in range(reps + 1):
+        for rep in range(reps + warm):
             t0 = time.perf_counter()
             ids = []
             for j in jobs:
@@ -840,7 +842,7 @@ def run_serve(args):
                 m.motif_plan_destroy(pl)
             t_client = time.perf_counter() - t0
             served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
-            if rep:
+            if rep >= warm:
                 out.append((time.perf_counter() - t0, t_client, served))
         m.motif_server_stop()
         out.sort(key=lambda x: x[0])

@@ -614,19 +614,19 @@ void scheduler(Server* S) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(S->h_states, snap, sizeof(JobState) * nact, cudaMemcpyDeviceToHost,
                           S->stream);
-    // The jobs of the step before retire while this one runs.
+    // The jobs of the step before retire while this one runs; they are marked done with the
+    // compaction below (one turn of the lock per step).
+    std::vector<Finished> retired;
     if (!retiring.empty()) {
       retire_finished(S, retiring, S->d_snap[snap_buf ^ 1]);
-      lk.lock();
-      mark_done(S, retiring);
-      lk.unlock();
-      retiring.clear();
+      retired.swap(retiring);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
     float step_ms = 0;
     cudaEventElapsedTime(&step_ms, S->ev0, S->ev1);
     if (e != cudaSuccess) {
       lk.lock();
+      mark_done(S, retired);
       fail_all(S, &retiring);
       continue;
     }
@@ -660,6 +660,7 @@ void scheduler(Server* S) {
     }
     snap_buf ^= 1;
     lk.lock();
+    mark_done(S, retired);
     for (const int i : failed) {
       Job* j = S->active[i];
       j->t_done = now_ms();
@@ -994,13 +995,15 @@ extern "C" int motif_poll(int64_t job_id, uint64_t* out_codes, int64_t capacity,
     stats->kernel = j->kind;
   }
   if (j->status == MOTIF_OK && j->result_size > capacity) return MOTIF_ERR_CAPACITY;
+  // The job is released: once it leaves the map nobody else reaches it (the scheduler let go of
+  // it when it marked it done), so the copy out runs without the lock.
+  S->jobs.erase(it);
+  lk.unlock();
   if (j->result_size > 0) memcpy(out_codes, j->result, (size_t)j->result_size * 8);
   const int st = j->status;
   std::vector<uint64_t*> evicted;
   host_give(S, j->result, j->result_cap, &evicted);
-  S->jobs.erase(it);
   delete j;  // the scheduler released its device buffers when it retired the job
-  lk.unlock();
   for (uint64_t* b : evicted) cudaFreeHost(b);
   return st;
 }

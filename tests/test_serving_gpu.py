@@ -223,3 +223,28 @@ def test_submit_seqs_range_and_errors(server):
     # rows shorter than l: no windows, nothing survives
     short = m.motif_poll(m.motif_submit_seqs(["ACGT"] * 3, 6, 1), timeout_ms=120000)[0]
     assert short.size == 0
+
+
+def test_served_overflow_paths_equal_oracle(server):
+    """Results larger than a served job's first output buffer (65,536 codes): a list job grows
+    its buffer and starts again, then sorts on the retirement stream (radix sort); a bitmap job
+    compacts again into a larger buffer.  Mixed with small jobs in one table."""
+    m.motif_server_start(max_active=8, step_tiles=256)
+    dense = fmgen.fm_job(3, 100, 10, 4, 321)          # most of the 4^10 codes survive
+    ref_dense, _ = oracle.search(dense.rows(), dense.l, dense.d, threads=8)
+    assert ref_dense.size > 1 << 16
+    as_list = m.motif_opts_default()
+    as_list.output = m.OUTPUT_LIST
+    as_bitmap = m.motif_opts_default()
+    as_bitmap.output = m.OUTPUT_BITMAP
+    small = _mix(21, 6)
+    ids = [m.motif_submit_seqs(dense.rows(), dense.l, dense.d, as_list)]
+    ids += [m.motif_submit_seqs(j.rows(), j.l, j.d) for j in small[:3]]
+    ids.append(m.motif_submit_seqs(dense.rows(), dense.l, dense.d, as_bitmap))
+    ids += [m.motif_submit_seqs(j.rows(), j.l, j.d) for j in small[3:]]
+    got = [m.motif_poll(jid, timeout_ms=120000, capacity=1 << 21)[0] for jid in ids]
+    assert np.array_equal(got[0], ref_dense)
+    assert np.array_equal(got[4], ref_dense)
+    for job, g in zip(small, got[1:4] + got[5:]):
+        ref, _ = oracle.search(job.rows(), job.l, job.d, threads=8)
+        assert np.array_equal(g, ref)

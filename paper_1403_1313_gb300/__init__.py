@@ -488,8 +488,10 @@ def motif_submit_seqs(seqs, l: int, d: int, opts: motif_opts | None = None) -> i
     return int(j.value)
 
 
-def motif_poll(job_id: int, timeout_ms: int = 0, capacity: int = 1 << 16):
-    """Returns (codes, stats dict) when the job is done, or None while it is pending."""
+def motif_poll(job_id: int, timeout_ms: int = 0, capacity: int = 1 << 12):
+    """Returns (codes, stats dict) when the job is done, or None while it is pending.  The
+    first buffer holds `capacity` codes; a larger result is polled again into one of its size
+    (the job stays until its codes fit)."""
     lib = _load()
     while True:
         out = _host_codes(capacity)

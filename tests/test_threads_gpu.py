@@ -95,6 +95,41 @@ def test_concurrent_submit_and_poll():
         m.motif_server_stop()
 
 
+def test_concurrent_row_submissions_and_polls():
+    """motif_submit_seqs from several threads at once (the server's pinned staging pool and
+    submit stream are shared), each thread polling its own jobs, some with a capacity that is
+    too small at first; mixed with plan submissions from another thread."""
+    work = [_jobs(1010 + w, 8) for w in range(5)]
+
+    def rows_worker(jobs):
+        def run():
+            for _ in range(2):
+                ids = [m.motif_submit_seqs(job.seqs, job.l, job.d) for job, _ in jobs]
+                for k, (jid, (_, ref)) in enumerate(zip(ids, jobs)):
+                    cap = 1 if k % 2 else max(1, ref.size)  # odd jobs: grow on ERR_CAPACITY
+                    got, _ = m.motif_poll(jid, timeout_ms=120000, capacity=cap)
+                    assert np.array_equal(got, ref)
+        return run
+
+    def plan_worker(jobs):
+        def run():
+            ids = []
+            for job, _ in jobs:
+                plan = m.motif_plan_create(job.n, job.t, job.l, job.d)
+                m.motif_load_seqs(plan, job.seqs)
+                ids.append(m.motif_submit(plan))
+                m.motif_plan_destroy(plan)
+            for jid, (_, ref) in zip(ids, jobs):
+                assert np.array_equal(m.motif_poll(jid, timeout_ms=120000)[0], ref)
+        return run
+
+    try:
+        m.motif_server_start(max_active=16, step_tiles=512)
+        _run_threads([rows_worker(j) for j in work[:4]] + [plan_worker(work[4])])
+    finally:
+        m.motif_server_stop()
+
+
 def test_concurrent_batches():
     work = [_jobs(980 + w, 8) for w in range(3)]
 

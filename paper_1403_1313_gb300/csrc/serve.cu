@@ -125,13 +125,16 @@ struct Server {
 
 constexpr size_t kHostPoolBytes = (size_t)2 << 30;  // pinned result blocks kept for reuse
 
-// A pinned block for at least `n` codes: a pooled one at most twice that size, else a new one of
-// the next power of two.  Null when pinned memory is exhausted.
+// A pinned block for at least `n` codes.  Blocks come in powers of two of at least 1,024 codes;
+// a pooled one of the request's size class, or the next one up, is reused, else a new block of
+// the class is allocated.  Null when pinned memory is exhausted.
 uint64_t* host_take(Server* S, size_t n, size_t* cap) {
+  size_t c = 1024;
+  while (c < n) c <<= 1;
   {
     std::lock_guard<std::mutex> g(S->pool_mu);
-    auto it = S->host_free.lower_bound(n);
-    if (it != S->host_free.end() && it->first <= 2 * n) {
+    auto it = S->host_free.lower_bound(c);
+    if (it != S->host_free.end() && it->first <= 2 * c) {
       uint64_t* b = it->second;
       *cap = it->first;
       S->host_free_bytes -= it->first * 8;
@@ -139,8 +142,6 @@ uint64_t* host_take(Server* S, size_t n, size_t* cap) {
       return b;
     }
   }
-  size_t c = 1024;
-  while (c < n) c <<= 1;
   uint64_t* b = nullptr;
   if (cudaHostAlloc((void**)&b, c * 8, 0) != cudaSuccess) {
     cudaGetLastError();

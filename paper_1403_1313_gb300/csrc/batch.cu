@@ -155,9 +155,15 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
   BatchCtx* c = nullptr;
   int rc = ensure_ctx(plans[0]->device, njobs, &c);
   if (rc) return rc;
-  // Every plan's pending work (loads) must finish before the batch stream reads its windows.
+  // Every plan's pending work (loads) must finish before the batch stream reads its windows:
+  // one wait per distinct stream (plans usually share one).
+  std::vector<cudaStream_t> streams;
+  for (int j = 0; j < njobs; ++j)
+    if (std::find(streams.begin(), streams.end(), plans[j]->stream) == streams.end())
+      streams.push_back(plans[j]->stream);
+  for (cudaStream_t st : streams)
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MOTIF_ERR_CUDA;
   for (int j = 0; j < njobs; ++j) {
-    if (cudaStreamSynchronize(plans[j]->stream) != cudaSuccess) return MOTIF_ERR_CUDA;
     if (plans[j]->check_alpha) {
       int err = 0;
       cudaMemcpy(&err, plans[j]->d_err, sizeof(int), cudaMemcpyDeviceToHost);
@@ -178,7 +184,7 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     if (statuses[j] != MOTIF_OK || p->W <= 0 || p->hi <= p->lo || p->nchunks == 0 ||
         p->empty_row)
       continue;
-    if (plan_ensure_buffers(p) != MOTIF_OK || cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    if (plan_ensure_buffers(p) != MOTIF_OK) {
       statuses[j] = MOTIF_ERR_OOM;
       continue;
     }
@@ -186,6 +192,9 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
     auto it = one_step_group.emplace(std::make_pair(p->kind, p->p), true).first;
     it->second = it->second && p->tiled_in_batch && p->nchunks == 1;
   }
+  // The buffers are made on the plans' streams, and the batch stream uses them.
+  for (cudaStream_t st : streams)
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MOTIF_ERR_CUDA;
   std::map<std::tuple<int, int, int>, std::vector<int>> groups;
   for (const int j : dev_jobs) {
     motif_plan_s* p = plans[j];

@@ -31,6 +31,7 @@ struct BatchCtx {
   JobState* d_states = nullptr;
   StepCtl* d_ctl = nullptr;
   JobState* h_states = nullptr;            // pinned: every job's state after its sort
+  StepCtl* h_ctl = nullptr;                // pinned: the step control after a table's steps
   SortTask* h_sort_tasks = nullptr;        // pinned staging of the sort / compaction tasks
   BitmapTask* h_bm_tasks = nullptr;
   unsigned* h_bm_first = nullptr;
@@ -81,6 +82,10 @@ int ensure_ctx(int dev, int njobs, BatchCtx** out) {
     c.d_bm_first = nullptr;
     c.cap = 0;
     if (!c.d_ctl && cudaMalloc(&c.d_ctl, sizeof(StepCtl)) != cudaSuccess) return MOTIF_ERR_OOM;
+    if (!c.h_ctl && cudaHostAlloc((void**)&c.h_ctl, sizeof(StepCtl), 0) != cudaSuccess) {
+      c.h_ctl = nullptr;
+      return MOTIF_ERR_OOM;
+    }
     const int cap = std::max(njobs, 64);
     if (cudaMalloc(&c.d_jobs, sizeof(JobDesc) * cap) != cudaSuccess ||
         cudaMalloc(&c.d_states, sizeof(JobState) * cap) != cudaSuccess ||
@@ -100,7 +105,8 @@ int ensure_ctx(int dev, int njobs, BatchCtx** out) {
 
 // Runs the job table [0, njobs) of one kernel variant to completion on ctx->stream.  one_step:
 // every job of the table finishes in one step (one tiled pass over a single chunk), so the graph
-// holds no loop.
+// holds no loop.  The graph path only enqueues: the step control's copy to c->h_ctl follows the
+// graph, and the caller's wait (table_status) reads it; the per-step path waits itself.
 int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, size_t smem,
               int max_steps, bool use_graph, int timeout_ms, bool one_step) {
   cudaStream_t s = c->stream;
@@ -126,13 +132,18 @@ int run_table(BatchCtx* c, int kind, int pv, int njobs, int grid, int block, siz
     }
   }
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  StepCtl ctl{};
-  if (e == cudaSuccess) e = cudaMemcpy(&ctl, c->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return status_from_cuda(e);
-  note_launches(1 + (int)ctl.steps);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, s);
   (void)timeout_ms;
-  return ctl.active_jobs == 0 ? MOTIF_OK : MOTIF_ERR_TIMEOUT;
+  return status_from_cuda(e);
+}
+
+// After the wait that follows a graph-launched table: every job done (else the step bound ended
+// the loop first).
+int table_status(BatchCtx* c, bool use_graph) {
+  if (!use_graph) return MOTIF_OK;  // run_steps checked it
+  note_launches(1 + (int)c->h_ctl->steps);
+  return c->h_ctl->active_jobs == 0 ? MOTIF_OK : MOTIF_ERR_TIMEOUT;
 }
 
 }  // namespace motif_batch
@@ -274,11 +285,13 @@ extern "C" int motif_batch_search(int32_t njobs, const motif_plan* plans,
                    timeout, one_step);
     cudaEventRecord(ev[1], c->stream);
     if (rc) return fail(rc);
-    std::vector<JobState> st(ids.size());
-    e = cudaMemcpyAsync(st.data(), c->d_states, sizeof(JobState) * ids.size(),
+    e = cudaMemcpyAsync(c->h_states, c->d_states, sizeof(JobState) * ids.size(),
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(status_from_cuda(e));
+    rc = table_status(c, use_graph != 0);
+    if (rc) return fail(rc);
+    const std::vector<JobState> st(c->h_states, c->h_states + ids.size());
     // Sort/dedup (or compact) every job's codes in its own buffer on the batch stream, the jobs
     // together: one launch sorts every list of at most 4096 codes (a CTA per job), a radix sort
     // runs per larger list, and three launches compact every bitmap.  One copy then brings back

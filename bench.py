@@ -490,7 +490,10 @@ def run_ours(args):
                          "clock per SM" % (bind.upper(), PIPE_PER_SM_CLK[bind],
                                            100.0 * pipes[bind] / ncu["inst"], lim[bind]))
         peak_i = per_clk * sms * max_mhz * 1e6
-        roof = {"bound": "issue", "kernel": "tiled_kernel (whole-tile prefix-tiled pass)",
+        roof = {"bound": "alu", "kernel": "tiled_kernel (whole-tile prefix-tiled pass)",
+                "bound_detail": "plain integer ALU work, measured against the SM's instruction "
+                                "issue rate for this kernel's own mix (per-pipe rates from the "
+                                "K4 probes, pipe shares from ncu)",
                 "unit": "G warp-instructions/s",
                 "achieved": ach_i / 1e9 if ach_i else None, "peak": peak_i / 1e9,
                 "frac": ach_i / peak_i if ach_i else None,

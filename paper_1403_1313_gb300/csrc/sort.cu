@@ -10,7 +10,11 @@
 //     histograms, one global digit-major scan, stable scatter ranked with warp match masks),
 //     then a keep-flag compaction of repeats.
 // Each path returns at once when the count belongs to the other path (or exceeds `cap`).
+#include <cooperative_groups.h>
+
 #include "motif_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace motif {
 namespace {
@@ -114,12 +118,14 @@ __device__ __forceinline__ void segment(unsigned long long n, unsigned long long
   if (e > n) e = n;
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(
-    const uint64_t* __restrict__ keys, const unsigned long long* count, long long cap, int shift,
-    unsigned* __restrict__ hist) {
+// The radix sort's phases, as device functions of one CTA (blockIdx.x of gridDim.x CTAs, or the
+// CTA alone for the scans).  The per-phase kernels below and the single cooperative kernel run
+// the same phases; n is the count read at the start.
+
+// Per-CTA digit counts of keys[segment], into hist[digit * gridDim.x + cta].
+__device__ void hist_phase(const uint64_t* __restrict__ keys, unsigned long long n, int shift,
+                           unsigned* __restrict__ hist) {
   __shared__ unsigned h[kDigits];
-  const unsigned long long n = read_count(count);
-  if (!large_active(n, cap)) return;
   for (int i = threadIdx.x; i < kDigits; i += blockDim.x) h[i] = 0;
   __syncthreads();
   unsigned long long b, e;
@@ -128,16 +134,13 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(
     atomicAdd(&h[(keys[i] >> shift) & (kDigits - 1)], 1u);
   __syncthreads();
   for (int i = threadIdx.x; i < kDigits; i += blockDim.x) hist[(size_t)i * gridDim.x + blockIdx.x] = h[i];
+  __syncthreads();
 }
 
 // Exclusive scan of `len` counters in place by one CTA of kRadixThreads threads.
-__global__ void __launch_bounds__(kRadixThreads) scan_kernel(unsigned* __restrict__ v, int len,
-                                                             const unsigned long long* count,
-                                                             long long cap, int need_large) {
+__device__ void scan_phase(unsigned* __restrict__ v, int len) {
   __shared__ unsigned warp_tot[kRadixThreads / 32];
   __shared__ unsigned carry;
-  const unsigned long long n = read_count(count);
-  if (need_large && !large_active(n, cap)) return;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -166,13 +169,8 @@ __global__ void __launch_bounds__(kRadixThreads) scan_kernel(unsigned* __restric
 // Exclusive scan of a digit-major histogram hist[digit * ctas + cta], taken in (digit, cta)
 // order: thread `digit` sums its row, the CTA scans the row totals, and each thread rewrites its
 // row as running offsets from its digit's base.  One CTA of kDigits threads.
-__global__ void __launch_bounds__(kDigits) hist_scan_kernel(unsigned* __restrict__ hist,
-                                                            int ctas,
-                                                            const unsigned long long* count,
-                                                            long long cap) {
+__device__ void hist_scan_phase(unsigned* __restrict__ hist, int ctas) {
   __shared__ unsigned warp_tot[kDigits / 32];
-  const unsigned long long n = read_count(count);
-  if (!large_active(n, cap)) return;
   const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
   unsigned* row = hist + (size_t)d * ctas;
   unsigned tot = 0;
@@ -193,17 +191,17 @@ __global__ void __launch_bounds__(kDigits) hist_scan_kernel(unsigned* __restrict
     row[c] = run;
     run += x;
   }
+  __syncthreads();
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
-    const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, const unsigned long long* count,
-    long long cap, int shift, const unsigned* __restrict__ offsets) {
+// Stable scatter of keys[segment] by digit, from the CTA's scanned histogram column.
+__device__ void scatter_phase(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
+                              unsigned long long n, int shift,
+                              const unsigned* __restrict__ offsets) {
   constexpr int kWarps = kRadixThreads / 32;
   __shared__ unsigned base[kDigits];
   __shared__ unsigned warp_cnt[kWarps][kDigits];
   __shared__ unsigned chunk_tot[kDigits];
-  const unsigned long long n = read_count(count);
-  if (!large_active(n, cap)) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   base[tid] = offsets[(size_t)tid * gridDim.x + blockIdx.x];  // kRadixThreads == kDigits
   unsigned long long b, e;
@@ -237,13 +235,10 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
   }
 }
 
-// Keep flags: per-CTA counts of first-of-run elements.
-__global__ void __launch_bounds__(kRadixThreads) unique_count_kernel(
-    const uint64_t* __restrict__ keys, const unsigned long long* count, long long cap,
-    unsigned* __restrict__ per_cta) {
+// Keep flags: the CTA's count of first-of-run elements.
+__device__ void unique_count_phase(const uint64_t* __restrict__ keys, unsigned long long n,
+                                   unsigned* __restrict__ per_cta) {
   __shared__ unsigned tot;
-  const unsigned long long n = read_count(count);
-  if (!large_active(n, cap)) return;
   if (threadIdx.x == 0) tot = 0;
   __syncthreads();
   unsigned long long b, e;
@@ -256,13 +251,11 @@ __global__ void __launch_bounds__(kRadixThreads) unique_count_kernel(
   if (threadIdx.x == 0) per_cta[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kRadixThreads) unique_write_kernel(
-    const uint64_t* __restrict__ keys, uint64_t* __restrict__ dst, const unsigned long long* count,
-    long long cap, const unsigned* __restrict__ offsets) {
+// The CTA's first-of-run elements, in order, from its scanned offset.
+__device__ void unique_write_phase(const uint64_t* __restrict__ keys, uint64_t* __restrict__ dst,
+                                   unsigned long long n, const unsigned* __restrict__ offsets) {
   __shared__ unsigned warp_tot[kRadixThreads / 32];
   __shared__ unsigned run;
-  const unsigned long long n = read_count(count);
-  if (!large_active(n, cap)) return;
   if (threadIdx.x == 0) run = offsets[blockIdx.x];
   __syncthreads();
   unsigned long long b, e;
@@ -286,6 +279,63 @@ __global__ void __launch_bounds__(kRadixThreads) unique_write_kernel(
   }
 }
 
+// The de-duplicated codes copied back (all CTAs, grid-stride).
+__device__ void finish_copy_phase(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
+                                  unsigned long long total) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(
+    const uint64_t* __restrict__ keys, const unsigned long long* count, long long cap, int shift,
+    unsigned* __restrict__ hist) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  hist_phase(keys, n, shift, hist);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) scan_kernel(unsigned* __restrict__ v, int len,
+                                                             const unsigned long long* count,
+                                                             long long cap, int need_large) {
+  const unsigned long long n = read_count(count);
+  if (need_large && !large_active(n, cap)) return;
+  scan_phase(v, len);
+}
+
+__global__ void __launch_bounds__(kDigits) hist_scan_kernel(unsigned* __restrict__ hist,
+                                                            int ctas,
+                                                            const unsigned long long* count,
+                                                            long long cap) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  hist_scan_phase(hist, ctas);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+    const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, const unsigned long long* count,
+    long long cap, int shift, const unsigned* __restrict__ offsets) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  scatter_phase(src, dst, n, shift, offsets);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) unique_count_kernel(
+    const uint64_t* __restrict__ keys, const unsigned long long* count, long long cap,
+    unsigned* __restrict__ per_cta) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  unique_count_phase(keys, n, per_cta);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) unique_write_kernel(
+    const uint64_t* __restrict__ keys, uint64_t* __restrict__ dst, const unsigned long long* count,
+    long long cap, const unsigned* __restrict__ offsets) {
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;
+  unique_write_phase(keys, dst, n, offsets);
+}
+
 // Copies the de-duplicated codes back and stores the new count.
 __global__ void unique_finish_kernel(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst,
                                      unsigned long long* count, long long cap,
@@ -293,11 +343,8 @@ __global__ void unique_finish_kernel(const uint64_t* __restrict__ src, uint64_t*
                                      const unsigned* __restrict__ per_cta_raw, int ctas) {
   const unsigned long long n = read_count(count);
   if (!large_active(n, cap)) return;
-  const unsigned long long total =
-      (unsigned long long)per_cta_scanned[ctas - 1] + per_cta_raw[ctas - 1];
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
-       i += (unsigned long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+  finish_copy_phase(src, dst,
+                    (unsigned long long)per_cta_scanned[ctas - 1] + per_cta_raw[ctas - 1]);
 }
 
 __global__ void store_count_kernel(unsigned long long* count, long long cap,
@@ -307,6 +354,46 @@ __global__ void store_count_kernel(unsigned long long* count, long long cap,
   if (!large_active(n, cap)) return;
   if (threadIdx.x == 0 && blockIdx.x == 0)
     *count = (unsigned long long)per_cta_scanned[ctas - 1] + per_cta_raw[ctas - 1];
+}
+
+// The whole large path in one cooperative launch (every CTA resident; grid-wide barriers
+// between the phases): it returns at once, from every CTA, unless the count needs it, so a
+// sort graph can hold it unconditionally after the one-CTA sort.  alt, hist, raw and scanned
+// are the scratch of launch_sort_unique's layout, for gridDim.x CTAs.
+__global__ void __launch_bounds__(kRadixThreads) radix_sort_coop_kernel(
+    uint64_t* codes, uint64_t* alt, unsigned long long* count, long long cap, int key_bits,
+    unsigned* hist, unsigned* raw, unsigned* scanned) {
+  static_assert(kRadixThreads == kDigits, "one thread per digit in the histogram scan");
+  const unsigned long long n = read_count(count);
+  if (!large_active(n, cap)) return;  // the same answer in every CTA
+  cg::grid_group grid = cg::this_grid();
+  uint64_t* a = codes;
+  uint64_t* b = alt;
+  const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * kRadixBits;
+    hist_phase(a, n, shift, hist);
+    grid.sync();
+    if (blockIdx.x == 0) hist_scan_phase(hist, gridDim.x);
+    grid.sync();
+    scatter_phase(a, b, n, shift, hist);
+    grid.sync();
+    uint64_t* t = a; a = b; b = t;
+  }
+  unique_count_phase(a, n, raw);
+  grid.sync();
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) scanned[i] = raw[i];
+    __syncthreads();
+    scan_phase(scanned, gridDim.x);
+  }
+  grid.sync();
+  unique_write_phase(a, b, n, scanned);
+  grid.sync();
+  const unsigned long long total =
+      (unsigned long long)scanned[gridDim.x - 1] + raw[gridDim.x - 1];
+  finish_copy_phase(b, codes, total);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = total;
 }
 
 int radix_ctas(int sms) { return sms > 0 ? 2 * sms : 256; }
@@ -636,21 +723,21 @@ cudaError_t launch_sort_unique(uint64_t* d_codes, unsigned long long* d_count, i
   return cudaGetLastError();
 }
 
-// Graph form of launch_sort_unique: the one-CTA kernel runs unconditionally and sets an IF
-// condition; the multi-CTA path is the body of that IF node, so it costs nothing when the count
-// fits the one-CTA path.  *last receives the final node.
+// Graph form of launch_sort_unique: the one-CTA kernel runs unconditionally; the multi-CTA path
+// follows it as one cooperative kernel node that returns at once unless the count needs it
+// (a kernel node costs about 1 us where a conditional node cost about 12 us on GB300).  Where
+// a cooperative node cannot be made, the one-CTA kernel sets an IF condition and the multi-CTA
+// path is the body of that IF node.  *last receives the final node.
 cudaError_t add_sort_nodes(cudaGraph_t g, cudaGraphNode_t dep, uint64_t* d_codes,
                            unsigned long long* d_count, int64_t cap, int key_bits, void* scratch,
                            int sms, cudaGraphNode_t* last) {
   const bool large = cap > kSmallMax && scratch != nullptr;
   cudaGraphConditionalHandle h = 0;
   cudaError_t e = cudaSuccess;
-  if (large) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) return e;
   cudaGraphNode_t small;
   {
     long long capv = cap;
-    int use = large ? 1 : 0;
+    int use = 0;
     void* args[] = {(void*)&d_codes, (void*)&d_count, (void*)&capv, (void*)&h, (void*)&use};
     cudaKernelNodeParams kp = {};
     kp.func = (void*)small_sort_kernel;
@@ -663,6 +750,59 @@ cudaError_t add_sort_nodes(cudaGraph_t g, cudaGraphNode_t dep, uint64_t* d_codes
   if (!large) {  // the count can never need the multi-CTA path
     *last = small;
     return cudaSuccess;
+  }
+  // The multi-CTA path as one cooperative kernel node after it: it returns at once unless the
+  // count needs it, which costs a kernel node's launch instead of a conditional node's.
+  {
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, radix_sort_coop_kernel,
+                                                      kRadixThreads, 0) == cudaSuccess &&
+        per_sm > 0) {
+      const int ctas = std::min(radix_ctas(sms), per_sm * sms);  // every CTA resident
+      uint64_t* alt = reinterpret_cast<uint64_t*>(scratch);
+      unsigned* hist = reinterpret_cast<unsigned*>(alt + cap);
+      unsigned* raw = hist + (size_t)kDigits * radix_ctas(sms);
+      unsigned* scanned = raw + radix_ctas(sms);
+      long long capv = cap;
+      int kb = key_bits;
+      void* args[] = {(void*)&d_codes, (void*)&alt, (void*)&d_count, (void*)&capv, (void*)&kb,
+                      (void*)&hist, (void*)&raw, (void*)&scanned};
+      cudaKernelNodeParams kp = {};
+      kp.func = (void*)radix_sort_coop_kernel;
+      kp.gridDim = dim3(ctas);
+      kp.blockDim = dim3(kRadixThreads);
+      kp.kernelParams = args;
+      cudaGraphNode_t node;
+      e = cudaGraphAddKernelNode(&node, g, &small, 1, &kp);
+      if (e != cudaSuccess) return e;
+      cudaKernelNodeAttrValue v = {};
+      v.cooperative = 1;
+      if (cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributeCooperative, &v) ==
+          cudaSuccess) {
+        *last = node;
+        return cudaSuccess;
+      }
+      cudaGetLastError();
+      e = cudaGraphDestroyNode(node);  // not cooperative: the conditional form instead
+      if (e != cudaSuccess) return e;
+    }
+    cudaGetLastError();
+  }
+  e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  {  // the one-CTA sort now sets the IF node's condition
+    long long capv = cap;
+    int use = 1;
+    void* args[] = {(void*)&d_codes, (void*)&d_count, (void*)&capv, (void*)&h, (void*)&use};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)small_sort_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(kSmallThreads);
+    kp.kernelParams = args;
+    e = cudaGraphKernelNodeSetParams(small, &kp);
+    if (e != cudaSuccess) return e;
   }
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;

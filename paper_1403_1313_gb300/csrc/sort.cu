@@ -411,6 +411,9 @@ int radix_ctas(int sms) { return sms > 0 ? 2 * sms : 256; }
 constexpr int kBmThreads = 256;
 constexpr int kBmWordsPerLane = 8;
 constexpr int kBmWords = kBmThreads * kBmWordsPerLane;
+// Bitmaps of at most this many blocks (2^19 codes) are compacted by one CTA in one launch: the
+// three launches of the multi-CTA form cost more than the one CTA's walk.
+constexpr int kBmSmallBlocks = 16;
 
 __global__ void __launch_bounds__(kBmThreads) bitmap_count_kernel(const uint32_t* __restrict__ bm,
                                                                  uint64_t nwords,
@@ -464,18 +467,17 @@ __global__ void __launch_bounds__(kBmThreads) bitmap_scan_kernel(unsigned* __res
   if (threadIdx.x == 0) *count = carry;
 }
 
-// Writes the codes base + bit of the set bits of every block at the block's offset (at most cap
-// codes in all).  Warp w of the block owns words [w*256, (w+1)*256) of it; lane k holds words
-// k, k+32, ... of that range.
-__global__ void __launch_bounds__(kBmThreads) bitmap_write_kernel(const uint32_t* __restrict__ bm,
-                                                                 uint64_t nwords, uint64_t base,
-                                                                 const unsigned* __restrict__ blk,
-                                                                 uint64_t* __restrict__ out,
-                                                                 long long cap) {
+// Writes the codes base + bit of the set bits of block `b` from offset `pos0` (at most cap codes
+// in all) and returns the block's count (every thread).  Warp w of the block owns words
+// [w*256, (w+1)*256) of it; lane k holds words k, k+32, ... of that range.  The CTA may call it
+// again for another block once it returns.
+__device__ unsigned bitmap_write_block(const uint32_t* __restrict__ bm, uint64_t nwords,
+                                       uint64_t base, uint64_t b, unsigned long long pos0,
+                                       uint64_t* __restrict__ out, long long cap) {
   __shared__ unsigned warp_tot[kBmThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const uint64_t wbase = (uint64_t)blockIdx.x * kBmWords + (uint64_t)warp * (32 * kBmWordsPerLane);
+  const uint64_t wbase = b * kBmWords + (uint64_t)warp * (32 * kBmWordsPerLane);
   uint32_t x[kBmWordsPerLane];
   unsigned c = 0;
 #pragma unroll
@@ -487,8 +489,12 @@ __global__ void __launch_bounds__(kBmThreads) bitmap_write_kernel(const uint32_t
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
   if (lane == 0) warp_tot[warp] = c;
   __syncthreads();
-  unsigned long long pos = blk[blockIdx.x];
-  for (int w = 0; w < warp; ++w) pos += warp_tot[w];
+  unsigned long long pos = pos0;
+  unsigned block_tot = 0;
+  for (int w = 0; w < kBmThreads / 32; ++w) {
+    if (w < warp) pos += warp_tot[w];
+    block_tot += warp_tot[w];
+  }
 #pragma unroll
   for (int i = 0; i < kBmWordsPerLane; ++i) {
     const unsigned cnt = __popc(x[i]);
@@ -513,6 +519,27 @@ __global__ void __launch_bounds__(kBmThreads) bitmap_write_kernel(const uint32_t
     }
     pos += tot;
   }
+  __syncthreads();  // warp_tot is read by every warp before a next block overwrites it
+  return block_tot;
+}
+
+__global__ void __launch_bounds__(kBmThreads) bitmap_write_kernel(const uint32_t* __restrict__ bm,
+                                                                 uint64_t nwords, uint64_t base,
+                                                                 const unsigned* __restrict__ blk,
+                                                                 uint64_t* __restrict__ out,
+                                                                 long long cap) {
+  bitmap_write_block(bm, nwords, base, blockIdx.x, blk[blockIdx.x], out, cap);
+}
+
+// A small bitmap (at most kBmSmallBlocks blocks) compacted by one CTA in one launch: its blocks
+// in order, each written from the running count, which *count receives at the end.
+__global__ void __launch_bounds__(kBmThreads) bitmap_compact_small_kernel(
+    const uint32_t* __restrict__ bm, uint64_t nwords, uint64_t base, uint64_t* __restrict__ out,
+    long long cap, unsigned long long* count) {
+  const uint64_t nblk = (nwords + kBmWords - 1) / kBmWords;
+  unsigned long long run = 0;
+  for (uint64_t b = 0; b < nblk; ++b) run += bitmap_write_block(bm, nwords, base, b, run, out, cap);
+  if (threadIdx.x == 0) *count = run;
 }
 
 // ---- many jobs' bitmaps at once --------------------------------------------------------------
@@ -587,50 +614,10 @@ __global__ void __launch_bounds__(kBmThreads) bitmap_scan_tasks_kernel(const Bit
 __global__ void __launch_bounds__(kBmThreads) bitmap_write_tasks_kernel(const BitmapTask* tasks,
                                                                        const unsigned* first,
                                                                        int ntasks) {
-  __shared__ unsigned warp_tot[kBmThreads / 32];
   const int k = task_of_block(first, ntasks, blockIdx.x);
   const BitmapTask t = tasks[k];
   const unsigned blk = blockIdx.x - first[k];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const uint64_t wbase = (uint64_t)blk * kBmWords + (uint64_t)warp * (32 * kBmWordsPerLane);
-  uint32_t x[kBmWordsPerLane];
-  unsigned c = 0;
-#pragma unroll
-  for (int i = 0; i < kBmWordsPerLane; ++i) {
-    const uint64_t w = wbase + (uint64_t)i * 32 + lane;
-    x[i] = w < t.nwords ? t.bm[w] : 0u;
-    c += __popc(x[i]);
-  }
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-  if (lane == 0) warp_tot[warp] = c;
-  __syncthreads();
-  unsigned long long pos = t.scratch[blk];
-  for (int w = 0; w < warp; ++w) pos += warp_tot[w];
-#pragma unroll
-  for (int i = 0; i < kBmWordsPerLane; ++i) {
-    const unsigned cnt = __popc(x[i]);
-    unsigned excl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, excl, o);
-      if (lane >= o) excl += y;
-    }
-    const unsigned tot = __shfl_sync(kFull, excl, 31);
-    excl -= cnt;
-    unsigned nz = __ballot_sync(kFull, x[i] != 0u);
-    while (nz) {
-      const int src = __ffs(nz) - 1;
-      nz &= nz - 1;
-      const uint32_t xs = __shfl_sync(kFull, x[i], src);
-      const unsigned ps = __shfl_sync(kFull, excl, src);
-      if ((xs >> lane) & 1u) {
-        const unsigned long long q = pos + ps + __popc(xs & lt);
-        if (q < (unsigned long long)t.cap)
-          t.out[q] = t.base + ((wbase + (uint64_t)i * 32 + src) << 5) + lane;
-      }
-    }
-    pos += tot;
-  }
+  bitmap_write_block(t.bm, t.nwords, t.base, blk, t.scratch[blk], t.out, t.cap);
 }
 
 // Scratch layout: [keys: cap u64][hist: kDigits*ctas u32][per_cta raw: ctas][per_cta scan: ctas]
@@ -658,6 +645,12 @@ cudaError_t launch_bitmap_compact(const uint32_t* bm, uint64_t nwords, uint64_t 
                                   unsigned long long* count, cudaStream_t s) {
   const uint64_t nblk = (nwords + kBmWords - 1) / kBmWords;
   if (nblk == 0 || nblk > (uint64_t)INT32_MAX) return cudaErrorInvalidValue;
+  if (nblk <= (uint64_t)kBmSmallBlocks) {  // one CTA, one launch
+    bitmap_compact_small_kernel<<<1, kBmThreads, 0, s>>>(bm, nwords, base, out, (long long)cap,
+                                                         count);
+    note_launches(1);
+    return cudaGetLastError();
+  }
   bitmap_count_kernel<<<(unsigned)nblk, kBmThreads, 0, s>>>(bm, nwords, scratch);
   bitmap_scan_kernel<<<1, kBmThreads, 0, s>>>(scratch, (int)nblk, count);
   bitmap_write_kernel<<<(unsigned)nblk, kBmThreads, 0, s>>>(bm, nwords, base, scratch, out,

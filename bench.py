@@ -29,6 +29,8 @@ cpu_baseline_1t = the oracle on one thread over a stated sub-range, extrapolated
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import json
 import os
 import statistics
@@ -72,6 +74,19 @@ TILED_NCU = {
 PIPE_PER_SM_CLK = {"alu": 2.0, "fma": 2.0, "xu": 0.5}
 
 
+
+
+@contextlib.contextmanager
+def quiet_gc():
+    """A host-timed region without the interpreter's cyclic garbage collector: the client's
+    objects (results, stats dicts) would otherwise trigger collections that walk every result
+    kept so far, pauses of tens of milliseconds that belong to this script, not the library."""
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -562,14 +577,15 @@ def run_ours(args):
     if world > 1:
         from paper_1403_1313_gb300.shard import gather_codes
         dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(ne):
-        m.motif_load_seqs(plan2, host_chars)
-        got = m.motif_search(plan2)
-        d2h = 8 * got.size + 8
-        if shard:
-            got = gather_codes(got)
-    dt = time.perf_counter() - t0
+    with quiet_gc():
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            m.motif_load_seqs(plan2, host_chars)
+            got = m.motif_search(plan2)
+            d2h = 8 * got.size + 8
+            if shard:
+                got = gather_codes(got)
+        dt = time.perf_counter() - t0
     if world > 1:
         tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -665,19 +681,22 @@ def run_batch(args):
             m.motif_batch_search(plans, use_graph=True)
             m.motif_batch_search(plans, use_graph=False)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            for pl in plans:
-                m.motif_search(pl)
-        t_plain = (time.perf_counter() - t0) / reps
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            m.motif_batch_search(plans, use_graph=True)
-        t_batch = (time.perf_counter() - t0) / reps
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            m.motif_batch_search(plans, use_graph=False)
-        t_batch_nograph = (time.perf_counter() - t0) / reps
+        with quiet_gc():
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                for pl in plans:
+                    m.motif_search(pl)
+            t_plain = (time.perf_counter() - t0) / reps
+        with quiet_gc():
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                m.motif_batch_search(plans, use_graph=True)
+            t_batch = (time.perf_counter() - t0) / reps
+        with quiet_gc():
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                m.motif_batch_search(plans, use_graph=False)
+            t_batch_nograph = (time.perf_counter() - t0) / reps
         survivors = sum(int(r.size) for r in batch_res)
         # Per-job view of both paths (the slowest plain jobs, and the batch's phase split).
         per_job = []
@@ -755,43 +774,44 @@ def run_serve(args):
         m.motif_load_seqs(pl, wj.seqs)
         m.motif_poll(m.motif_submit(pl), timeout_ms=60000)
         m.motif_plan_destroy(pl)
-        ids = []
-        client = ({"submit": 0.0} if args.serve_submit == "seqs" else
-                  {"create": 0.0, "load": 0.0, "submit": 0.0, "destroy": 0.0})
-        t0 = time.perf_counter()
-        for j in jobs:
-            delay = t0 + j.arrival_s - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            c0 = time.perf_counter()
-            if args.serve_submit == "seqs":
-                ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
-                client["submit"] += time.perf_counter() - c0
-                continue
-            pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
-            c1 = time.perf_counter()
-            m.motif_load_seqs(pl, j.seqs)
-            c2 = time.perf_counter()
-            ids.append(m.motif_submit(pl))
-            c3 = time.perf_counter()
-            m.motif_plan_destroy(pl)
-            c4 = time.perf_counter()
-            client["create"] += c1 - c0
-            client["load"] += c2 - c1
-            client["submit"] += c3 - c2
-            client["destroy"] += c4 - c3
-        t_submitted = time.perf_counter() - t0
-        lat, queue, cands, ok = [], [], 0, 0
-        for j, jid in zip(jobs, ids):
-            res = m.motif_poll(jid, timeout_ms=600000)
-            codes, st = res
-            lat.append(st["total_ms"])
-            queue.append(st["queue_ms"])
-            cands += 4 ** j.l
-            c = m.motif_encode(j.consensus)
-            pos = int(np.searchsorted(codes, np.uint64(c)))
-            ok += int(pos < codes.size and int(codes[pos]) == c)
-        wall = time.perf_counter() - t0
+        with quiet_gc():
+            ids = []
+            client = ({"submit": 0.0} if args.serve_submit == "seqs" else
+                      {"create": 0.0, "load": 0.0, "submit": 0.0, "destroy": 0.0})
+            t0 = time.perf_counter()
+            for j in jobs:
+                delay = t0 + j.arrival_s - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                c0 = time.perf_counter()
+                if args.serve_submit == "seqs":
+                    ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
+                    client["submit"] += time.perf_counter() - c0
+                    continue
+                pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+                c1 = time.perf_counter()
+                m.motif_load_seqs(pl, j.seqs)
+                c2 = time.perf_counter()
+                ids.append(m.motif_submit(pl))
+                c3 = time.perf_counter()
+                m.motif_plan_destroy(pl)
+                c4 = time.perf_counter()
+                client["create"] += c1 - c0
+                client["load"] += c2 - c1
+                client["submit"] += c3 - c2
+                client["destroy"] += c4 - c3
+            t_submitted = time.perf_counter() - t0
+            lat, queue, cands, ok = [], [], 0, 0
+            for j, jid in zip(jobs, ids):
+                res = m.motif_poll(jid, timeout_ms=600000)
+                codes, st = res
+                lat.append(st["total_ms"])
+                queue.append(st["queue_ms"])
+                cands += 4 ** j.l
+                c = m.motif_encode(j.consensus)
+                pos = int(np.searchsorted(codes, np.uint64(c)))
+                ok += int(pos < codes.size and int(codes[pos]) == c)
+            wall = time.perf_counter() - t0
         m.motif_server_stop()
         lat = np.array(lat)
         rows.append({"rate_jobs_per_s": rate, "jobs": count, "p50_ms": float(np.percentile(lat, 50)),
@@ -813,15 +833,17 @@ def run_serve(args):
 
     def plain_pass():
         codes, dev = [], 0.0
-        t0 = time.perf_counter()
-        for j in jobs:
-            pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
-            m.motif_load_seqs(pl, j.seqs)
-            codes.append(m.motif_search(pl))
-            stp = m.motif_stats(pl)
-            dev += stp["search_ms"] + stp["sort_ms"]
-            m.motif_plan_destroy(pl)
-        return codes, dev, time.perf_counter() - t0
+        with quiet_gc():
+            t0 = time.perf_counter()
+            for j in jobs:
+                pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+                m.motif_load_seqs(pl, j.seqs)
+                codes.append(m.motif_search(pl))
+                stp = m.motif_stats(pl)
+                dev += stp["search_ms"] + stp["sort_ms"]
+                m.motif_plan_destroy(pl)
+            dt = time.perf_counter() - t0
+        return codes, dev, dt
 
     plain_pass()
     plain_codes, dev_ms, t_plain = plain_pass()
@@ -833,20 +855,22 @@ def run_serve(args):
         m.motif_server_start(max_active=args.serve_max_active, step_tiles=args.serve_step_tiles)
         out = []
         for rep in range(reps + warm):
-            t0 = time.perf_counter()
-            ids = []
-            for j in jobs:
-                if via == "seqs":
-                    ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
-                    continue
-                pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
-                m.motif_load_seqs(pl, j.seqs)
-                ids.append(m.motif_submit(pl))
-                m.motif_plan_destroy(pl)
-            t_client = time.perf_counter() - t0
-            served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
+            with quiet_gc():
+                t0 = time.perf_counter()
+                ids = []
+                for j in jobs:
+                    if via == "seqs":
+                        ids.append(m.motif_submit_seqs(j.seqs, j.l, j.d))
+                        continue
+                    pl = m.motif_plan_create(j.n, j.t, j.l, j.d)
+                    m.motif_load_seqs(pl, j.seqs)
+                    ids.append(m.motif_submit(pl))
+                    m.motif_plan_destroy(pl)
+                t_client = time.perf_counter() - t0
+                served = [m.motif_poll(jid, timeout_ms=600000) for jid in ids]
+                t_done = time.perf_counter() - t0
             if rep >= warm:
-                out.append((time.perf_counter() - t0, t_client, served))
+                out.append((t_done, t_client, served))
         m.motif_server_stop()
         out.sort(key=lambda x: x[0])
         return out[len(out) // 2], [x[0] for x in out]

@@ -310,7 +310,8 @@ int motif_autotune(motif_plan p, int32_t budget_ms, motif_opts* best);
 int motif_tune_cache_save(const char* path);
 int motif_tune_cache_load(const char* path);
 
-/* ---- serving: continuous batching -------------------------------------------------------- */
+/* ---- serving: continuous batching (no counterpart in the paper; each job is the Sec. III.A
+ * search) ---------------------------------------------------------------------------------- */
 
 typedef struct {
   int32_t max_active;      /* jobs resident on the device at once; 0 = 64 */
@@ -351,7 +352,8 @@ int motif_server_stop(void);
 int motif_submit(motif_plan p, int64_t* job_id);
 
 /* Submits a job straight from n host rows of t characters (row r at seqs + r * stride, stride
- * >= t, only ACGTacgt), searched for (l, d), without a plan: the job is configured as
+ * >= t, only ACGTacgt; the inputs of Sec. IV.A), searched for (l, d) by the Sec. III.A skip-BF
+ * search as motif_search runs it, without a plan: the job is configured as
  * motif_plan_create would configure a plan with these options (opts may be NULL; its stream and
  * allocator are not used, the server's are), the characters are checked on the host, copied to
  * the device and packed on the server's submit stream.  seqs may be reused once this returns.

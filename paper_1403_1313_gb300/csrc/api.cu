@@ -1046,9 +1046,10 @@ int motif_search(motif_plan p, uint64_t* out_codes, int64_t capacity, int64_t* o
   for (;;) {
     rc = plan_ensure_buffers(p);
     if (rc) return rc;
-    // The graph holds the multi-CTA sort (under a conditional node, about 10 us even when it
-    // is skipped) only once the plan's previous result needed it; until then the one-CTA sort
-    // alone, and a larger result is sorted below with one more wait.
+    // The graph holds the multi-CTA sort (one more node, which runs even when it returns at
+    // once, and needs scratch sized for the buffer) only once the plan's previous result needed
+    // it; until then the one-CTA sort alone, and a larger result is sorted below with one more
+    // wait.
     sorted = p->out_cap <= 4096 ||
              (p->stats.survivors > 4096 && p->d_sort &&
               p->sort_bytes >= sort_scratch_bytes(p->out_cap, p->sms));

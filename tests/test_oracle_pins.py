@@ -296,3 +296,28 @@ def test_golden_l15d4_is_consistent():
     q = 1 - (1 - p) ** W
     expect = 4 ** l * (1 - q ** n) / (1 - q) * q / p
     assert abs(g["compares"] / expect - 1) < 0.001
+
+
+def test_golden_l17d5_is_consistent():
+    """The stored complete (17,5) result (about 4 h of oracle time on 8 cores, so not
+    regenerated here): same inputs, the planted consensus among the codes, every stored code
+    accepted by the oracle alone, its three neighbours in the last base stored exactly when the
+    oracle accepts them, and a compare tally within 0.1 % of the closed form for uniform bases."""
+    with open(os.path.join(GOLDEN, "l17d5_n20_t600_seed3.json")) as f:
+        g = json.load(f)
+    job = fmgen.single("l17d5")
+    import hashlib
+    assert hashlib.sha256(job.seqs.tobytes()).hexdigest() == g["seqs_sha256"]
+    assert g["consensus"] == job.consensus and base4(job.consensus) in g["codes"]
+    stored = set(g["codes"])
+    for c in g["codes"]:
+        assert oracle.search(job.rows(), 17, 5, lo=c, hi=c + 1)[0].tolist() == [c]
+        for x in range(1, 4):  # the other three bases at the last position
+            other = (c & ~3) | ((c + x) & 3)
+            got = oracle.search(job.rows(), 17, 5, lo=other, hi=other + 1)[0].tolist()
+            assert (other in stored) == (got == [other])
+    l, d, n, W = 17, 5, 20, 600 - 17 + 1
+    p = sum(math.comb(l, k) * 3 ** k for k in range(d + 1)) / 4 ** l
+    q = 1 - (1 - p) ** W
+    expect = 4 ** l * (1 - q ** n) / (1 - q) * q / p
+    assert abs(g["compares"] / expect - 1) < 0.001
